@@ -1,0 +1,98 @@
+"""Planted mistakes in the oracle must be caught by its pins.
+
+Each test patches one plausible mistake into the oracle (on the CPU) and
+checks that the pin meant to catch it fails.
+"""
+import dataclasses
+
+import numpy as np
+import pytest
+
+import stokes_synth as synth
+from oracle import OracleMesh, stokes
+
+H = 1e-30
+
+
+@pytest.fixture(scope="module")
+def cmesh():
+    return OracleMesh(synth.workload("cforest_3x3x2_q2p1"))
+
+
+def _rigid_residual(m):
+    rng = np.random.default_rng(1)
+    a, w = rng.normal(size=3), rng.normal(size=3)
+    u = a + np.cross(w, m.node_coords())
+    phys = dataclasses.replace(m.wl.phys, robin=False)
+    rv, _ = stokes.element_residual(m, phys, stokes.gather(m, u), np.zeros((m.E, m.npr)),
+                                    np.zeros(m.Nb), body=False)
+    ur = rng.uniform(-1, 1, size=u.shape)
+    rr, _ = stokes.element_residual(m, phys, stokes.gather(m, ur), np.zeros((m.E, m.npr)),
+                                    np.zeros(m.Nb), body=False)
+    return np.abs(stokes.scatter(m, rv)).max() / np.abs(stokes.scatter(m, rr)).max()
+
+
+def _cs_error(m):
+    lb = m.wl.phys.logbeta(*m.basal_coords()[:, :2].T)
+    up = synth.uniform_vector(1, m.ndof)
+    x = synth.uniform_vector(1, m.ndof, stream=1)
+    y = stokes.jacobian_apply(m, m.wl.phys, up, x, lb)
+    yc = stokes.residual(m, m.wl.phys, up + 1j * H * x, lb).imag / H
+    return np.linalg.norm(y - yc) / np.linalg.norm(yc)
+
+
+def _dot_asym(m):
+    lb = m.wl.phys.logbeta(*m.basal_coords()[:, :2].T)
+    up = synth.uniform_vector(4, m.ndof)
+    x = synth.uniform_vector(4, m.ndof, stream=1)
+    y = synth.uniform_vector(4, m.ndof, stream=2)
+    a = np.dot(y, stokes.jacobian_apply(m, m.wl.phys, up, x, lb))
+    b = np.dot(x, stokes.jacobian_apply(m, m.wl.phys, up, y, lb))
+    return abs(a - b) / (abs(a) + abs(b))
+
+
+def test_baseline_pins_hold(cmesh):
+    assert _rigid_residual(cmesh) < 1e-10
+    assert _cs_error(cmesh) < 1e-13
+    assert _dot_asym(cmesh) < 1e-12
+
+
+def test_transposed_inverse_jacobian_is_caught(cmesh, monkeypatch):
+    orig = stokes._grad
+    def bad(mesh, ue, sl):
+        G = np.einsum("mqa,eac->eqcm", mesh.dphi, ue)
+        return np.einsum("eqcm,eqdm->eqcd", G, mesh.Jinv[sl])
+    monkeypatch.setattr(stokes, "_grad", bad)
+    assert _rigid_residual(cmesh) > 1e-6
+
+
+def test_dropped_newton_term_is_caught(cmesh, monkeypatch):
+    monkeypatch.setattr(stokes, "_pexp", lambda phys: 0.0 * phys.n)
+    # residual still uses p_n through _viscosity: restore it there only
+    orig_visc = stokes._viscosity
+    monkeypatch.setattr(stokes, "_viscosity",
+                        lambda phys, DD: phys.viscosity_prefactor()
+                        * (phys.gamma * DD + phys.delta) ** ((1.0 - phys.n) / (2.0 * phys.n)))
+    assert _cs_error(cmesh) > 1e-6
+
+
+def test_pressure_sign_error_is_caught(cmesh, monkeypatch):
+    orig = stokes.element_jacobian
+    def bad(*a, **k):
+        yv, yp = orig(*a, **k)
+        return yv, -yp
+    monkeypatch.setattr(stokes, "element_jacobian", bad)
+    assert _dot_asym(cmesh) > 1e-6
+
+
+def test_wrong_energy_constant_is_caught(cmesh, monkeypatch):
+    m = cmesh
+    lb = m.wl.phys.logbeta(*m.basal_coords()[:, :2].T)
+    u = synth.uniform_vector(3, 3 * m.Nv).reshape(m.Nv, 3)
+    w = synth.uniform_vector(3, 3 * m.Nv, stream=1).reshape(m.Nv, 3)
+    phys = m.wl.phys
+    rv, _ = stokes.element_residual(m, phys, stokes.gather(m, u), np.zeros((m.E, m.npr)), lb)
+    ref = np.sum(stokes.scatter(m, rv) * w)
+    bad = dataclasses.replace(phys, gamma=2.0 * phys.gamma)   # energy with the wrong gamma
+    dE = stokes.energy(m, bad, u + 1j * H * w, lb).imag / H
+    assert abs(dE - ref) > 1e-6 * abs(ref)
