@@ -1,0 +1,185 @@
+/*
+ * stokes.h -- C-ABI of the GB300 matrix-free high-order nonlinear Stokes operator.
+ *
+ * The library evaluates, on one GPU, the discrete operator of the paper
+ * "Solution of nonlinear Stokes equations discretized by high-order finite
+ * elements on nonconforming and anisotropic meshes, with application to ice
+ * sheet dynamics" (Isaac, Stadler, Ghattas):
+ *
+ *   residual  r(u, p)    of the weak form, Eq. 2.5 (Section 2.2), Glen flow
+ *                        law Eq. 2.2 with basal Robin sliding and no
+ *                        penetration, Eq. 2.4;
+ *   Jacobian  J(u)[w, q] Newton linearisation, Eqs. 2.6-2.7 (Section 2.3);
+ *   J^T                  transpose action (Section 4.1: A(u) is symmetric);
+ *   gradients            adjoint products with d r / d log(beta) and d r / d A
+ *                        (the "adjoint equations" of Section 2.3 and 8.3).
+ *
+ * Discretisation (Section 3.2): isoparametric Q_k velocity on GLL nodes, tensor
+ * Gauss quadrature with k+1 points per direction, discontinuous P_{k-1} or
+ * Q_{k-2} pressure, hexahedral meshes with one level of 2:1 refinement and
+ * hanging-node restriction R_i (hanging-node figure of Section 3.2.1).  The
+ * operator is applied matrix-free with sum-factorised tensor contractions
+ * (Section 3.3).
+ *
+ * Conventions shared by every entry point
+ *   - All vector arguments are CALLER-OWNED DEVICE pointers on the mesh's
+ *     device, contiguous, of the element type given by `prec`
+ *     (STOKES_F64: double, STOKES_F32: float) unless stated otherwise.
+ *   - A state vector "up" has length 3*Nv + Np: the velocity node-major and
+ *     interleaved (u_x, u_y, u_z of node 0, then node 1, ...), followed by the
+ *     discontinuous pressure, element-major ([E][npr]).
+ *   - Global nodes are ordered by reference position (Z, then Y, then X,
+ *     X and Y wrapped on periodic meshes); elements by coarse cell (x fastest,
+ *     then y, then z) with a refined cell replaced by its 8 children in the
+ *     order bx + 2 by + 4 bz.
+ *   - Every call is asynchronous on `stream` (a cudaStream_t passed as void*;
+ *     NULL = legacy default stream).  Nothing is allocated per call: the mesh
+ *     handle owns its device metadata and workspaces, which is why calls that
+ *     share a mesh must not run concurrently on different streams.
+ *   - Return value: STOKES_OK or a negative error code; stokes_last_error()
+ *     returns a message for the calling thread's last failure.  No exception
+ *     crosses the ABI.
+ *   - Constraints: basal nodes carry the nodal projector P (P = 0 for no-slip;
+ *     P = I - n n^T for u . n = 0, n the normalised area-weighted nodal normal).
+ *     The residual evaluated is r_c(u) = P r(P u) + (I - P) u and the Jacobian
+ *     P J(P u) P + (I - P), its exact derivative.
+ */
+#ifndef STOKES_GB300_H
+#define STOKES_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes -------------------------------------------------------- */
+#define STOKES_OK            0
+#define STOKES_E_INVAL      -1   /* bad argument: NULL pointer, size, enum     */
+#define STOKES_E_MESH       -2   /* invalid mesh: inverted element, bad mask   */
+#define STOKES_E_NOMEM      -3   /* device or host allocation failed           */
+#define STOKES_E_CUDA       -4   /* a CUDA runtime call or launch failed       */
+#define STOKES_E_NONFINITE  -5   /* a non-finite value was produced            */
+#define STOKES_E_NOCONV     -6   /* solver did not reach its tolerance         */
+
+/* ---- enums ---------------------------------------------------------------- */
+#define STOKES_F64 0
+#define STOKES_F32 1
+
+#define STOKES_PRESSURE_P 0      /* P_{k-1}^disc: Legendre products, degree <= k-1 */
+#define STOKES_PRESSURE_Q 1      /* Q_{k-2}^disc: Lagrange on (k-1)^3 Gauss points */
+
+#define STOKES_BASE_NOSLIP 0     /* u = 0 on the base                           */
+#define STOKES_BASE_SLIP   1     /* u . n = 0 on the base (plus Robin if enabled) */
+
+/* A smooth periodic field f(x,y) = mean + sum_m amp[m] cos(kx[m] x + ky[m] y
+ * + phase[m]).  Host pointers, read during stokes_mesh_create only. */
+typedef struct {
+    double mean;
+    int n_modes;
+    const double* amp;
+    const double* kx;
+    const double* ky;
+    const double* phase;
+} stokes_field;
+
+/* Mesh description (all host memory, read during stokes_mesh_create only).
+ * Geometry: x = Lx X / nx, y = Ly Y / ny, z = bed + (Z / nz)(surface - bed),
+ * evaluated at the GLL nodes of each coarse cell (isoparametric map); refined
+ * children inherit the parent map (Section 3.1). */
+typedef struct {
+    int nx, ny, nz;               /* coarse hexahedral grid                     */
+    int k;                        /* velocity degree, 1 <= k <= 5                */
+    int pressure_space;           /* STOKES_PRESSURE_P or STOKES_PRESSURE_Q      */
+    int periodic_xy;              /* 1: periodic in x and y                      */
+    double Lx, Ly;                /* horizontal extent                           */
+    stokes_field bed, surface;
+    const uint8_t* refine;        /* [nx*ny*nz] 1 = split once into 8, or NULL   */
+    int basal_bc;                 /* STOKES_BASE_NOSLIP or STOKES_BASE_SLIP      */
+    int device;                   /* CUDA device ordinal                         */
+} stokes_mesh_desc;
+
+/* Physical parameters.  mu = C0 A^(-1/n) (gamma D:D + delta)^((1-n)/(2n));
+ * the paper's Glen law (Eq. 2.2) is C0 = 1, gamma = 1/2, delta = eps. */
+typedef struct {
+    double n, A, C0, gamma, delta;
+    double body[3];               /* body force b                               */
+    int robin;                    /* 1: add int_{Gamma_b} beta T v . T u ds      */
+    const double* logbeta;        /* DEVICE, [Nb] FP64 nodal log(beta) at the
+                                     basal nodes (ascending global node order);
+                                     required when robin = 1                   */
+} stokes_params;
+
+typedef struct {
+    int64_t E;        /* elements                                               */
+    int64_t Nv;       /* independent velocity nodes (3 Nv velocity dofs)        */
+    int64_t Np;       /* pressure dofs = E * npr                                */
+    int64_t Nb;       /* basal nodes                                            */
+    int32_t k, npr;   /* velocity degree, pressure dofs per element             */
+    int64_t n_hanging_elems;  /* elements with at least one hanging face/edge   */
+} stokes_sizes;
+
+typedef struct stokes_mesh stokes_mesh;
+typedef struct stokes_state stokes_state;
+
+/* Build the mesh on the host (node numbering, hanging-node codes, geometry at
+ * quadrature points in FP64) and upload it to `desc->device`.
+ * Errors: E_INVAL (bad sizes/enums), E_MESH (detJ <= 0), E_NOMEM, E_CUDA.
+ * On success *out owns all device memory; release with stokes_mesh_destroy. */
+int stokes_mesh_create(const stokes_mesh_desc* desc, stokes_mesh** out);
+int stokes_mesh_destroy(stokes_mesh* mesh);
+int stokes_mesh_sizes(const stokes_mesh* mesh, stokes_sizes* out);
+
+/* Host copies of mesh data for verification: physical coordinates of the
+ * global nodes [Nv][3] (x, y wrapped into [0, L) on periodic meshes) and the
+ * global node index of each basal node [Nb].  Caller-owned host buffers. */
+int stokes_mesh_node_coords(const stokes_mesh* mesh, double* xyz);
+int stokes_mesh_basal_nodes(const stokes_mesh* mesh, int64_t* nodes);
+
+/* Residual r_c(up) (Eq. 2.5 with the constraints above).  up, r: [3Nv+Np].
+ * prec selects the arithmetic and the element type of up and r. */
+int stokes_residual(const stokes_mesh* mesh, const stokes_params* params,
+                    const void* up, void* r, int prec, void* stream);
+
+/* y = J_c(up_lin) x, the Newton Jacobian of Eqs. 2.6-2.7 at up_lin, fused:
+ * the linearisation is recomputed at every quadrature point. */
+int stokes_jacobian_apply(const stokes_mesh* mesh, const stokes_params* params,
+                          const void* up_lin, const void* x, void* y,
+                          int prec, void* stream);
+
+/* y = J_c(up_lin)^T x (transposed pointwise map and coupling blocks). */
+int stokes_jacobian_apply_transpose(const stokes_mesh* mesh, const stokes_params* params,
+                                    const void* up_lin, const void* x, void* y,
+                                    int prec, void* stream);
+
+/* Adjoint products with the parameter Jacobians at the state up (FP64):
+ *   g_logbeta[j] = lambda^T d r_c / d log(beta_j)   (device, [Nb], overwritten)
+ *   *g_A         = lambda^T d r_c / d A             (device, 1 double, overwritten)
+ * Either output may be NULL.  up, lambda: device FP64 [3Nv+Np]. */
+int stokes_param_grad(const stokes_mesh* mesh, const stokes_params* params,
+                      const double* up, const double* lambda,
+                      double* g_logbeta, double* g_A, void* stream);
+
+/* Linearised state: the per-quadrature-point Newton coefficients at up_lin
+ * (geometry, mu, and the rank-one term of Eq. 2.7), evaluated in FP64 and
+ * stored in `prec`, so that repeated Jacobian applies (Krylov iterations)
+ * stream them instead of recomputing the viscosity. */
+int stokes_state_create(const stokes_mesh* mesh, int prec, stokes_state** out);
+int stokes_state_destroy(stokes_state* state);
+/* up_lin: device FP64 [3Nv+Np]. params is copied into the state. */
+int stokes_linearize(stokes_state* state, const stokes_params* params,
+                     const double* up_lin, void* stream);
+/* y = J_c x from the stored state; x, y of the state's precision. */
+int stokes_state_apply(const stokes_state* state, const void* x, void* y, void* stream);
+int stokes_state_apply_transpose(const stokes_state* state, const void* x, void* y,
+                                 void* stream);
+
+/* Message describing the calling thread's last error ("" if none). */
+const char* stokes_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* STOKES_GB300_H */

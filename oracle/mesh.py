@@ -300,8 +300,9 @@ class OracleMesh:
         indep = self.elem_gid >= 0
         out[self.elem_gid[indep]] = self.X[indep]
         if self.periodic:
-            out[:, 0] = np.mod(out[:, 0], self.wl.Lx)
-            out[:, 1] = np.mod(out[:, 1], self.wl.Ly)
+            for d, L in ((0, self.wl.Lx), (1, self.wl.Ly)):
+                out[:, d] = np.mod(out[:, d], L)
+                out[L - out[:, d] < 1e-12 * L, d] = 0.0
         return out
 
     def basal_coords(self):

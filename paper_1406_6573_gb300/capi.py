@@ -1,0 +1,185 @@
+"""Thin ctypes binding of the C-ABI in include/stokes.h (argument marshalling only).
+
+Every function here has the name of the C entry point it calls and forwards
+device pointers taken from torch tensors; all arithmetic runs in the CUDA
+library.  The library must have been built (paper_1406_6573_gb300.build or
+__graft_entry__.build()); importing this module without it raises.
+"""
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "lib", "libstokes_gb300.so")
+
+STOKES_OK = 0
+STOKES_F64 = 0
+STOKES_F32 = 1
+STOKES_PRESSURE_P = 0
+STOKES_PRESSURE_Q = 1
+STOKES_BASE_NOSLIP = 0
+STOKES_BASE_SLIP = 1
+
+ERRORS = {-1: "E_INVAL", -2: "E_MESH", -3: "E_NOMEM", -4: "E_CUDA", -5: "E_NONFINITE", -6: "E_NOCONV"}
+
+
+class StokesError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class stokes_field(C.Structure):
+    _fields_ = [("mean", C.c_double), ("n_modes", C.c_int),
+                ("amp", C.POINTER(C.c_double)), ("kx", C.POINTER(C.c_double)),
+                ("ky", C.POINTER(C.c_double)), ("phase", C.POINTER(C.c_double))]
+
+
+class stokes_mesh_desc(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("k", C.c_int),
+                ("pressure_space", C.c_int), ("periodic_xy", C.c_int),
+                ("Lx", C.c_double), ("Ly", C.c_double),
+                ("bed", stokes_field), ("surface", stokes_field),
+                ("refine", C.POINTER(C.c_uint8)), ("basal_bc", C.c_int), ("device", C.c_int)]
+
+
+class stokes_params(C.Structure):
+    _fields_ = [("n", C.c_double), ("A", C.c_double), ("C0", C.c_double),
+                ("gamma", C.c_double), ("delta", C.c_double), ("body", C.c_double * 3),
+                ("robin", C.c_int), ("logbeta", C.c_void_p)]
+
+
+class stokes_sizes(C.Structure):
+    _fields_ = [("E", C.c_int64), ("Nv", C.c_int64), ("Np", C.c_int64), ("Nb", C.c_int64),
+                ("k", C.c_int32), ("npr", C.c_int32), ("n_hanging_elems", C.c_int64)]
+
+
+# every symbol declared in include/stokes.h, with its ctypes signature
+_SIGS = {
+    "stokes_mesh_create": (C.c_int, [C.POINTER(stokes_mesh_desc), C.POINTER(C.c_void_p)]),
+    "stokes_mesh_destroy": (C.c_int, [C.c_void_p]),
+    "stokes_mesh_sizes": (C.c_int, [C.c_void_p, C.POINTER(stokes_sizes)]),
+    "stokes_mesh_node_coords": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "stokes_mesh_basal_nodes": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "stokes_residual": (C.c_int, [C.c_void_p, C.POINTER(stokes_params), C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    "stokes_jacobian_apply": (C.c_int, [C.c_void_p, C.POINTER(stokes_params), C.c_void_p, C.c_void_p,
+                                        C.c_void_p, C.c_int, C.c_void_p]),
+    "stokes_jacobian_apply_transpose": (C.c_int, [C.c_void_p, C.POINTER(stokes_params), C.c_void_p,
+                                                  C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    "stokes_param_grad": (C.c_int, [C.c_void_p, C.POINTER(stokes_params), C.c_void_p, C.c_void_p,
+                                    C.c_void_p, C.c_void_p, C.c_void_p]),
+    "stokes_state_create": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_void_p)]),
+    "stokes_state_destroy": (C.c_int, [C.c_void_p]),
+    "stokes_linearize": (C.c_int, [C.c_void_p, C.POINTER(stokes_params), C.c_void_p, C.c_void_p]),
+    "stokes_state_apply": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "stokes_state_apply_transpose": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "stokes_last_error": (C.c_char_p, []),
+}
+
+_lib = None
+
+
+def lib():
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with "
+                              "`python -c 'import __graft_entry__ as g; g.build()'`")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(rc):
+    if rc != STOKES_OK:
+        raise StokesError(rc, lib().stokes_last_error().decode())
+
+
+def _ptr(t):
+    """Device (or host) pointer of a contiguous torch tensor / numpy array; None -> NULL."""
+    if t is None:
+        return None
+    if hasattr(t, "data_ptr"):
+        if not t.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return C.c_void_p(t.data_ptr())
+    return C.c_void_p(t.ctypes.data)
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+# ------------------------------------------------------------- raw entry points
+def stokes_mesh_create(desc):
+    h = C.c_void_p()
+    _check(lib().stokes_mesh_create(C.byref(desc), C.byref(h)))
+    return h
+
+
+def stokes_mesh_destroy(h):
+    _check(lib().stokes_mesh_destroy(h))
+
+
+def stokes_mesh_sizes(h):
+    s = stokes_sizes()
+    _check(lib().stokes_mesh_sizes(h, C.byref(s)))
+    return s
+
+
+def stokes_mesh_node_coords(h, out):
+    _check(lib().stokes_mesh_node_coords(h, _ptr(out)))
+
+
+def stokes_mesh_basal_nodes(h, out):
+    _check(lib().stokes_mesh_basal_nodes(h, _ptr(out)))
+
+
+def stokes_residual(h, params, up, r, prec, stream=None):
+    _check(lib().stokes_residual(h, C.byref(params), _ptr(up), _ptr(r), prec, _stream(stream)))
+
+
+def stokes_jacobian_apply(h, params, up_lin, x, y, prec, stream=None):
+    _check(lib().stokes_jacobian_apply(h, C.byref(params), _ptr(up_lin), _ptr(x), _ptr(y), prec,
+                                       _stream(stream)))
+
+
+def stokes_jacobian_apply_transpose(h, params, up_lin, x, y, prec, stream=None):
+    _check(lib().stokes_jacobian_apply_transpose(h, C.byref(params), _ptr(up_lin), _ptr(x), _ptr(y),
+                                                 prec, _stream(stream)))
+
+
+def stokes_param_grad(h, params, up, lam, g_logbeta, g_A, stream=None):
+    _check(lib().stokes_param_grad(h, C.byref(params), _ptr(up), _ptr(lam), _ptr(g_logbeta), _ptr(g_A),
+                                   _stream(stream)))
+
+
+def stokes_state_create(h, prec):
+    s = C.c_void_p()
+    _check(lib().stokes_state_create(h, prec, C.byref(s)))
+    return s
+
+
+def stokes_state_destroy(s):
+    _check(lib().stokes_state_destroy(s))
+
+
+def stokes_linearize(s, params, up_lin, stream=None):
+    _check(lib().stokes_linearize(s, C.byref(params), _ptr(up_lin), _stream(stream)))
+
+
+def stokes_state_apply(s, x, y, stream=None):
+    _check(lib().stokes_state_apply(s, _ptr(x), _ptr(y), _stream(stream)))
+
+
+def stokes_state_apply_transpose(s, x, y, stream=None):
+    _check(lib().stokes_state_apply_transpose(s, _ptr(x), _ptr(y), _stream(stream)))

@@ -1,0 +1,406 @@
+// C-ABI entry points (include/stokes.h): argument checking, device memory of
+// the mesh handle, and the launch sequence of each operator.
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+
+#include <cuda_runtime.h>
+
+#include "common.h"
+#include "kernels.h"
+
+using namespace stokes;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+    g_err = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* where) {
+    return fail(STOKES_E_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+// Make `dev` current for the duration of a call, restoring the caller's device.
+struct DeviceGuard {
+    int prev = -1;
+    cudaError_t err = cudaSuccess;
+    explicit DeviceGuard(int dev) {
+        err = cudaGetDevice(&prev);
+        if (err == cudaSuccess && prev != dev) err = cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+constexpr int MAX_DEVICES = 64;
+std::mutex g_tables_mu;
+bool g_tables_done[MAX_DEVICES][KMAX + 1];
+
+int ensure_tables(int dev, int k) {
+    std::lock_guard<std::mutex> lk(g_tables_mu);
+    if (dev < 0 || dev >= MAX_DEVICES) return fail(STOKES_E_INVAL, "device ordinal out of range");
+    if (g_tables_done[dev][k]) return STOKES_OK;
+    Tables1D t[2];
+    build_tables(k, STOKES_PRESSURE_P, t[0]);
+    if (k >= 2) build_tables(k, STOKES_PRESSURE_Q, t[1]); else t[1] = t[0];
+    int e = 0;
+    switch (k) {
+        case 2: e = upload_tables_k2(t); break;
+        case 3: e = upload_tables_k3(t); break;
+        case 4: e = upload_tables_k4(t); break;
+        default: return fail(STOKES_E_INVAL, "the GPU kernels are built for degrees k = 2, 3, 4");
+    }
+    if (e != 0) return cuda_fail(cudaError_t(e), "uploading basis tables");
+    g_tables_done[dev][k] = true;
+    return STOKES_OK;
+}
+
+int launch_elem(int k, int mode, int prec, int state_prec, bool trans, const ElemArgs& a, cudaStream_t s) {
+    switch (k) {
+        case 2: return launch_elem_k2(mode, prec, state_prec, trans, a, s);
+        case 3: return launch_elem_k3(mode, prec, state_prec, trans, a, s);
+        case 4: return launch_elem_k4(mode, prec, state_prec, trans, a, s);
+    }
+    return int(cudaErrorInvalidValue);
+}
+
+int launch_face(int k, int mode, int prec, const FaceArgs& a, cudaStream_t s) {
+    switch (k) {
+        case 2: return launch_face_k2(mode, prec, a, s);
+        case 3: return launch_face_k3(mode, prec, a, s);
+        case 4: return launch_face_k4(mode, prec, a, s);
+    }
+    return int(cudaErrorInvalidValue);
+}
+
+template <typename T>
+int upload(T** dst, const std::vector<T>& src) {
+    *dst = nullptr;
+    if (src.empty()) return STOKES_OK;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(dst), src.size() * sizeof(T));
+    if (e != cudaSuccess) { *dst = nullptr; return fail(STOKES_E_NOMEM, "cudaMalloc of mesh data failed"); }
+    e = cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "uploading mesh data");
+    return STOKES_OK;
+}
+
+}  // namespace
+
+struct stokes_mesh {
+    HostMesh h;
+    int device = -1;
+    bool on_device = false;
+    int32_t* d_nodes = nullptr;
+    uint32_t* d_hang = nullptr;
+    double* d_geo = nullptr;
+    int32_t* d_pidx = nullptr;
+    double* d_pel = nullptr;
+    int32_t* d_face_elem = nullptr;
+    double* d_fgeo = nullptr;
+    int32_t* d_fmap = nullptr;
+    int32_t* d_basal_nodes = nullptr;
+    double* d_basal_P = nullptr;
+};
+
+struct stokes_state {
+    const stokes_mesh* mesh = nullptr;
+    int prec = 0;
+    void* d_state = nullptr;
+    stokes_params params{};
+    bool linearized = false;
+};
+
+namespace {
+
+void free_mesh_device(stokes_mesh* m) {
+    void* ptrs[] = {m->d_nodes, m->d_hang, m->d_geo, m->d_pidx, m->d_pel, m->d_face_elem,
+                    m->d_fgeo, m->d_fmap, m->d_basal_nodes, m->d_basal_P};
+    for (void* p : ptrs) if (p) cudaFree(p);
+}
+
+int check_common(const stokes_mesh* m, int prec) {
+    if (!m) return fail(STOKES_E_INVAL, "mesh is NULL");
+    if (!m->on_device) return fail(STOKES_E_INVAL, "mesh was built for the host only (device = -1)");
+    if (prec != STOKES_F64 && prec != STOKES_F32) return fail(STOKES_E_INVAL, "prec must be STOKES_F64 or STOKES_F32");
+    return STOKES_OK;
+}
+
+int check_params(const stokes_mesh* m, const stokes_params* p) {
+    if (!p) return fail(STOKES_E_INVAL, "params is NULL");
+    if (!(p->n >= 1.0) || !(p->A > 0) || !(p->C0 > 0) || !(p->gamma > 0) || !(p->delta > 0))
+        return fail(STOKES_E_INVAL, "params: need n >= 1, A > 0, C0 > 0, gamma > 0, delta > 0");
+    if (p->robin && !p->logbeta && m->h.Nb > 0) return fail(STOKES_E_INVAL, "params: robin = 1 needs logbeta");
+    return STOKES_OK;
+}
+
+ElemArgs elem_args(const stokes_mesh* m, const stokes_params* p) {
+    ElemArgs a{};
+    a.E = m->h.E; a.Nv = m->h.Nv; a.npr = m->h.npr; a.pspace = m->h.pspace;
+    a.any_hang = m->h.n_hang > 0;
+    a.nodes = m->d_nodes; a.hang = m->d_hang; a.geo = m->d_geo; a.pidx = m->d_pidx; a.pel = m->d_pel;
+    if (p) {
+        a.C = p->C0 * std::pow(p->A, -1.0 / p->n);
+        a.gamma = p->gamma; a.delta = p->delta;
+        a.pexp = (1.0 - p->n) / (2.0 * p->n);
+        a.n_is_3 = (p->n == 3.0);
+        for (int c = 0; c < 3; ++c) a.body[c] = p->body[c];
+    }
+    return a;
+}
+
+FaceArgs face_args(const stokes_mesh* m, const stokes_params* p) {
+    FaceArgs f{};
+    f.nF = m->h.nF; f.Nv = m->h.Nv;
+    f.face_elem = m->d_face_elem; f.nodes = m->d_nodes; f.hang = m->d_hang;
+    f.pidx = m->d_pidx; f.pel = m->d_pel; f.fgeo = m->d_fgeo; f.fmap = m->d_fmap;
+    f.logbeta = p ? p->logbeta : nullptr;
+    return f;
+}
+
+size_t vec_bytes(const stokes_mesh* m, int prec) {
+    return size_t(3 * m->h.Nv + m->h.Np) * (prec == STOKES_F32 ? 4 : 8);
+}
+
+// y = (element terms of x) + Robin(x) + (I - P) x ; mode selects the element term.
+int operator_sequence(const stokes_mesh* m, const stokes_params* p, int mode, int prec, int state_prec,
+                      bool trans, const void* x, const void* u, const void* cstate, void* y, cudaStream_t s) {
+    cudaError_t ce = cudaMemsetAsync(y, 0, vec_bytes(m, prec), s);
+    if (ce != cudaSuccess) return cuda_fail(ce, "clearing the output");
+    ElemArgs a = elem_args(m, p);
+    a.x = x; a.y = y; a.u = u; a.cstate = cstate;
+    int e = launch_elem(m->h.k, mode, prec, state_prec, trans, a, s);
+    if (e) return cuda_fail(cudaError_t(e), "element kernel launch");
+    if (p->robin && m->h.nF > 0) {
+        FaceArgs f = face_args(m, p);
+        f.x = x; f.y = y;
+        e = launch_face(m->h.k, FACE_APPLY, prec, f, s);
+        if (e) return cuda_fail(cudaError_t(e), "basal face kernel launch");
+    }
+    e = launch_constraint(prec, m->h.Nb, m->d_basal_nodes, m->d_basal_P, x, y, s);
+    if (e) return cuda_fail(cudaError_t(e), "constraint kernel launch");
+    return STOKES_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* stokes_last_error(void) { return g_err.c_str(); }
+
+int stokes_mesh_create(const stokes_mesh_desc* desc, stokes_mesh** out) {
+    if (!desc || !out) return fail(STOKES_E_INVAL, "desc and out must be non-NULL");
+    *out = nullptr;
+    stokes_mesh* m = new (std::nothrow) stokes_mesh();
+    if (!m) return fail(STOKES_E_NOMEM, "host allocation failed");
+    std::string err;
+    int rc;
+    try {
+        rc = build_host_mesh(*desc, m->h, err);
+    } catch (const std::bad_alloc&) {
+        rc = STOKES_E_NOMEM; err = "host allocation failed while building the mesh";
+    }
+    if (rc != STOKES_OK) { delete m; return fail(rc, err); }
+    m->device = desc->device;
+    if (desc->device >= 0) {
+        if (m->h.k < 2 || m->h.k > 4) {
+            delete m;
+            return fail(STOKES_E_INVAL, "the GPU kernels are built for degrees k = 2, 3, 4");
+        }
+        DeviceGuard g(desc->device);
+        if (g.err != cudaSuccess) { delete m; return cuda_fail(g.err, "selecting the device"); }
+        rc = ensure_tables(desc->device, m->h.k);
+        if (rc == STOKES_OK) rc = upload(&m->d_nodes, m->h.elem_nodes);
+        if (rc == STOKES_OK) rc = upload(&m->d_hang, m->h.elem_hang);
+        if (rc == STOKES_OK) rc = upload(&m->d_geo, m->h.geo);
+        if (rc == STOKES_OK) rc = upload(&m->d_pidx, m->h.elem_pidx);
+        if (rc == STOKES_OK) rc = upload(&m->d_pel, m->h.pel);
+        if (rc == STOKES_OK) rc = upload(&m->d_face_elem, m->h.face_elem);
+        if (rc == STOKES_OK) rc = upload(&m->d_fgeo, m->h.fgeo);
+        if (rc == STOKES_OK) rc = upload(&m->d_fmap, m->h.fmap);
+        if (rc == STOKES_OK) rc = upload(&m->d_basal_nodes, m->h.basal_nodes);
+        if (rc == STOKES_OK) rc = upload(&m->d_basal_P, m->h.basal_P);
+        if (rc != STOKES_OK) { free_mesh_device(m); delete m; return rc; }
+        m->on_device = true;
+        // the large per-qp arrays live on the device only
+        std::vector<double>().swap(m->h.geo);
+        std::vector<int32_t>().swap(m->h.elem_nodes);
+    }
+    *out = m;
+    return STOKES_OK;
+}
+
+int stokes_mesh_destroy(stokes_mesh* mesh) {
+    if (!mesh) return STOKES_OK;
+    if (mesh->on_device) {
+        DeviceGuard g(mesh->device);
+        free_mesh_device(mesh);
+    }
+    delete mesh;
+    return STOKES_OK;
+}
+
+int stokes_mesh_sizes(const stokes_mesh* mesh, stokes_sizes* out) {
+    if (!mesh || !out) return fail(STOKES_E_INVAL, "mesh and out must be non-NULL");
+    out->E = mesh->h.E; out->Nv = mesh->h.Nv; out->Np = mesh->h.Np; out->Nb = mesh->h.Nb;
+    out->k = mesh->h.k; out->npr = mesh->h.npr; out->n_hanging_elems = mesh->h.n_hang;
+    return STOKES_OK;
+}
+
+int stokes_mesh_node_coords(const stokes_mesh* mesh, double* xyz) {
+    if (!mesh || !xyz) return fail(STOKES_E_INVAL, "mesh and xyz must be non-NULL");
+    std::memcpy(xyz, mesh->h.node_xyz.data(), mesh->h.node_xyz.size() * sizeof(double));
+    return STOKES_OK;
+}
+
+int stokes_mesh_basal_nodes(const stokes_mesh* mesh, int64_t* nodes) {
+    if (!mesh || !nodes) return fail(STOKES_E_INVAL, "mesh and nodes must be non-NULL");
+    for (int64_t b = 0; b < mesh->h.Nb; ++b) nodes[b] = mesh->h.basal_nodes[b];
+    return STOKES_OK;
+}
+
+int stokes_residual(const stokes_mesh* mesh, const stokes_params* params, const void* up, void* r,
+                    int prec, void* stream) {
+    int rc = check_common(mesh, prec);
+    if (rc) return rc;
+    if ((rc = check_params(mesh, params))) return rc;
+    if (!up || !r) return fail(STOKES_E_INVAL, "up and r must be non-NULL device pointers");
+    DeviceGuard g(mesh->device);
+    if (g.err != cudaSuccess) return cuda_fail(g.err, "selecting the device");
+    return operator_sequence(mesh, params, MODE_RESIDUAL, prec, prec, false, up, nullptr, nullptr, r,
+                             static_cast<cudaStream_t>(stream));
+}
+
+static int jacobian_common(const stokes_mesh* mesh, const stokes_params* params, const void* up_lin,
+                           const void* x, void* y, int prec, void* stream, bool trans) {
+    int rc = check_common(mesh, prec);
+    if (rc) return rc;
+    if ((rc = check_params(mesh, params))) return rc;
+    if (!up_lin || !x || !y) return fail(STOKES_E_INVAL, "up_lin, x and y must be non-NULL device pointers");
+    if (x == y) return fail(STOKES_E_INVAL, "x and y must not alias");
+    DeviceGuard g(mesh->device);
+    if (g.err != cudaSuccess) return cuda_fail(g.err, "selecting the device");
+    return operator_sequence(mesh, params, MODE_APPLY, prec, prec, trans, x, up_lin, nullptr, y,
+                             static_cast<cudaStream_t>(stream));
+}
+
+int stokes_jacobian_apply(const stokes_mesh* mesh, const stokes_params* params, const void* up_lin,
+                          const void* x, void* y, int prec, void* stream) {
+    return jacobian_common(mesh, params, up_lin, x, y, prec, stream, false);
+}
+
+int stokes_jacobian_apply_transpose(const stokes_mesh* mesh, const stokes_params* params, const void* up_lin,
+                                    const void* x, void* y, int prec, void* stream) {
+    return jacobian_common(mesh, params, up_lin, x, y, prec, stream, true);
+}
+
+int stokes_param_grad(const stokes_mesh* mesh, const stokes_params* params, const double* up,
+                      const double* lambda, double* g_logbeta, double* g_A, void* stream) {
+    int rc = check_common(mesh, STOKES_F64);
+    if (rc) return rc;
+    if ((rc = check_params(mesh, params))) return rc;
+    if (!up || !lambda) return fail(STOKES_E_INVAL, "up and lambda must be non-NULL device pointers");
+    DeviceGuard g(mesh->device);
+    if (g.err != cudaSuccess) return cuda_fail(g.err, "selecting the device");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (g_logbeta) {
+        cudaError_t ce = cudaMemsetAsync(g_logbeta, 0, size_t(mesh->h.Nb) * sizeof(double), s);
+        if (ce != cudaSuccess) return cuda_fail(ce, "clearing g_logbeta");
+        if (params->robin && mesh->h.nF > 0) {
+            FaceArgs f = face_args(mesh, params);
+            f.u = up; f.lam = lambda; f.g = g_logbeta;
+            int e = launch_face(mesh->h.k, FACE_GRAD_LOGBETA, STOKES_F64, f, s);
+            if (e) return cuda_fail(cudaError_t(e), "log(beta) gradient kernel launch");
+        }
+    }
+    if (g_A) {
+        cudaError_t ce = cudaMemsetAsync(g_A, 0, sizeof(double), s);
+        if (ce != cudaSuccess) return cuda_fail(ce, "clearing g_A");
+        ElemArgs a = elem_args(mesh, params);
+        a.ud = up; a.lam = lambda; a.gA = g_A;
+        a.gA_scale = -1.0 / (params->n * params->A);
+        int e = launch_elem(mesh->h.k, MODE_GRAD_A, STOKES_F64, STOKES_F64, false, a, s);
+        if (e) return cuda_fail(cudaError_t(e), "A gradient kernel launch");
+    }
+    return STOKES_OK;
+}
+
+int stokes_state_create(const stokes_mesh* mesh, int prec, stokes_state** out) {
+    int rc = check_common(mesh, prec);
+    if (rc) return rc;
+    if (!out) return fail(STOKES_E_INVAL, "out is NULL");
+    *out = nullptr;
+    stokes_state* st = new (std::nothrow) stokes_state();
+    if (!st) return fail(STOKES_E_NOMEM, "host allocation failed");
+    st->mesh = mesh;
+    st->prec = prec;
+    DeviceGuard g(mesh->device);
+    if (g.err != cudaSuccess) { delete st; return cuda_fail(g.err, "selecting the device"); }
+    const size_t q3 = size_t(mesh->h.q) * mesh->h.q * mesh->h.q;
+    const size_t bytes = size_t(mesh->h.E) * STATE_FIELDS * q3 * (prec == STOKES_F32 ? 4 : 8);
+    if (cudaMalloc(&st->d_state, bytes) != cudaSuccess) {
+        delete st;
+        return fail(STOKES_E_NOMEM, "cudaMalloc of the linearised state failed");
+    }
+    *out = st;
+    return STOKES_OK;
+}
+
+int stokes_state_destroy(stokes_state* state) {
+    if (!state) return STOKES_OK;
+    DeviceGuard g(state->mesh->device);
+    if (state->d_state) cudaFree(state->d_state);
+    delete state;
+    return STOKES_OK;
+}
+
+int stokes_linearize(stokes_state* state, const stokes_params* params, const double* up_lin, void* stream) {
+    if (!state) return fail(STOKES_E_INVAL, "state is NULL");
+    const stokes_mesh* mesh = state->mesh;
+    int rc = check_common(mesh, state->prec);
+    if (rc) return rc;
+    if ((rc = check_params(mesh, params))) return rc;
+    if (!up_lin) return fail(STOKES_E_INVAL, "up_lin is NULL");
+    DeviceGuard g(mesh->device);
+    if (g.err != cudaSuccess) return cuda_fail(g.err, "selecting the device");
+    ElemArgs a = elem_args(mesh, params);
+    a.ud = up_lin;
+    a.state = state->d_state;
+    int e = launch_elem(mesh->h.k, MODE_LINEARIZE, STOKES_F64, state->prec, false, a,
+                        static_cast<cudaStream_t>(stream));
+    if (e) return cuda_fail(cudaError_t(e), "linearize kernel launch");
+    state->params = *params;
+    state->linearized = true;
+    return STOKES_OK;
+}
+
+static int state_apply_common(const stokes_state* state, const void* x, void* y, void* stream, bool trans) {
+    if (!state) return fail(STOKES_E_INVAL, "state is NULL");
+    if (!state->linearized) return fail(STOKES_E_INVAL, "state has not been linearized");
+    const stokes_mesh* mesh = state->mesh;
+    int rc = check_common(mesh, state->prec);
+    if (rc) return rc;
+    if (!x || !y) return fail(STOKES_E_INVAL, "x and y must be non-NULL device pointers");
+    if (x == y) return fail(STOKES_E_INVAL, "x and y must not alias");
+    DeviceGuard g(mesh->device);
+    if (g.err != cudaSuccess) return cuda_fail(g.err, "selecting the device");
+    return operator_sequence(mesh, &state->params, MODE_STATE_APPLY, state->prec, state->prec, trans, x,
+                             nullptr, state->d_state, y, static_cast<cudaStream_t>(stream));
+}
+
+int stokes_state_apply(const stokes_state* state, const void* x, void* y, void* stream) {
+    return state_apply_common(state, x, y, stream, false);
+}
+
+int stokes_state_apply_transpose(const stokes_state* state, const void* x, void* y, void* stream) {
+    return state_apply_common(state, x, y, stream, true);
+}
+
+}  // extern "C"

@@ -1,0 +1,608 @@
+// Element kernels (volume terms) and basal-face kernels, one instantiation set
+// per degree STOKES_K.  Included by k2.cu, k3.cu, k4.cu.
+#pragma once
+
+#include "elem_kernels.cuh"
+
+namespace stokes {
+namespace dev {
+
+// Load the element's discontinuous pressure dofs into shared memory.
+template <typename T, typename TIN>
+__device__ __forceinline__ void load_pressure(const ElemArgs& a, const TIN* x, int64_t e, bool active,
+                                              int ij, T* pres) {
+    if (active)
+        for (int b = ij; b < a.npr; b += N2) pres[b] = T(ld(x + 3 * a.Nv + e * a.npr + b));
+}
+
+// Physical gradient from the reference gradient at one quadrature point.
+template <typename T>
+__device__ __forceinline__ void phys_grad(const T (&G)[3][3][Q], int lq, const T (&Ji)[9], T (&g)[3][3]) {
+    #pragma unroll
+    for (int c = 0; c < 3; ++c)
+        #pragma unroll
+        for (int d = 0; d < 3; ++d)
+            g[c][d] = G[c][0][lq] * Ji[d] + G[c][1][lq] * Ji[3 + d] + G[c][2][lq] * Ji[6 + d];
+}
+
+// Reference stress S[c][m] = sum_d Jinv[m][d] tau[c][d] written back into G.
+template <typename T>
+__device__ __forceinline__ void ref_stress(T (&G)[3][3][Q], int lq, const T (&Ji)[9], const T (&tau)[3][3]) {
+    #pragma unroll
+    for (int c = 0; c < 3; ++c)
+        #pragma unroll
+        for (int m = 0; m < 3; ++m)
+            G[c][m][lq] = Ji[3 * m] * tau[c][0] + Ji[3 * m + 1] * tau[c][1] + Ji[3 * m + 2] * tau[c][2];
+}
+
+template <typename T>
+__device__ __forceinline__ void load_geo(const ElemArgs& a, int64_t e, int qp, bool active, T (&Ji)[9], T& wdj) {
+    constexpr int Q3 = Q * Q * Q;
+    if (active) {
+        const double* gp = a.geo + e * 10 * Q3 + qp;
+        #pragma unroll
+        for (int f = 0; f < 9; ++f) Ji[f] = T(__ldg(gp + f * Q3));
+        wdj = T(__ldg(gp + 9 * Q3));
+    } else {
+        #pragma unroll
+        for (int f = 0; f < 9; ++f) Ji[f] = T(0);
+        wdj = T(0);
+    }
+}
+
+// ============================================================ volume kernel
+// T: arithmetic type.  S: type of the stored state (linearize / state apply).
+template <typename T, typename S, int MODE, bool TRANS>
+__global__ void __launch_bounds__(THREADS) elem_kernel(ElemArgs a) {
+    constexpr int Q3 = Q * Q * Q;
+    __shared__ T sbuf[EPB + 1][3][N3];
+    __shared__ T spres[EPB + 1][NPRK];
+    __shared__ double sred[THREADS / 32];
+
+    const int tid = threadIdx.x;
+    const int es = tid / N2;
+    const int ij = tid - es * N2;
+    const int i = ij % N1, j = ij / N1;
+    const int64_t e = int64_t(blockIdx.x) * EPB + es;
+    const bool active = (es < EPB) && (e < a.E);
+    T* b0 = sbuf[es][0];
+    T* b1 = sbuf[es][1];
+    T* b2 = sbuf[es][2];
+    T* sb = &sbuf[es][0][0];
+    const uint32_t h = active ? a.hang[e] : 0u;
+    const bool any_h = a.any_hang ? (__syncthreads_or(int(h & ((1u << HANG_CHILD0) - 1))) != 0) : false;
+    const int ps = a.pspace;
+
+    T G[3][3][Q];     // reference gradients, then reference stresses
+    T gq[Q];          // pressure-row integrand  -w detJ div(.)
+
+    if constexpr (MODE == MODE_STATE_APPLY) {
+        T v[3][N1];
+        gather_velocity<T, T>(a, static_cast<const T*>(a.x), e, active, ij, v);
+        if (any_h) hanging_forward<T, 3>(v, h, active, i, j, sb);
+        load_pressure<T, T>(a, static_cast<const T*>(a.x), e, active, ij, spres[es]);
+        #pragma unroll
+        for (int c = 0; c < 3; ++c) ref_gradient<T>(v[c], G[c][0], G[c][1], G[c][2], i, j, b0, b1);
+        const S* st = static_cast<const S*>(a.cstate) + e * STATE_FIELDS * Q3;
+        #pragma unroll
+        for (int lq = 0; lq < Q; ++lq) {
+            const int qp = sidx(i, j, lq);
+            T f[STATE_FIELDS];
+            #pragma unroll
+            for (int r = 0; r < STATE_FIELDS; ++r) f[r] = active ? T(ld(st + r * Q3 + qp)) : T(0);
+            T Ji[9];
+            #pragma unroll
+            for (int r = 0; r < 9; ++r) Ji[r] = f[r];
+            const T wdj = f[9], muw = f[10];
+            const T D00 = f[11], D11 = f[12], D22 = f[13], D01 = f[14], D02 = f[15], D12 = f[16];
+            T g[3][3];
+            phys_grad(G, lq, Ji, g);
+            const T E00 = g[0][0], E11 = g[1][1], E22 = g[2][2];
+            const T E01 = T(0.5) * (g[0][1] + g[1][0]);
+            const T E02 = T(0.5) * (g[0][2] + g[2][0]);
+            const T E12 = T(0.5) * (g[1][2] + g[2][1]);
+            // Eq. 2.7 is a symmetric map on symmetric tensors: its transpose
+            // (TRANS) is the same contraction D^(D^:E).
+            const T s = D00 * E00 + D11 * E11 + D22 * E22 + T(2) * (D01 * E01 + D02 * E02 + D12 * E12);
+            const T pw = pressure_at<T>(spres[es], a.npr, ps, i, j, lq) * wdj;
+            T tau[3][3];
+            tau[0][0] = muw * E00 - s * D00 - pw;
+            tau[1][1] = muw * E11 - s * D11 - pw;
+            tau[2][2] = muw * E22 - s * D22 - pw;
+            tau[0][1] = tau[1][0] = muw * E01 - s * D01;
+            tau[0][2] = tau[2][0] = muw * E02 - s * D02;
+            tau[1][2] = tau[2][1] = muw * E12 - s * D12;
+            gq[lq] = -wdj * (g[0][0] + g[1][1] + g[2][2]);
+            ref_stress(G, lq, Ji, tau);
+        }
+    } else if constexpr (MODE == MODE_RESIDUAL) {
+        T v[3][N1];
+        gather_velocity<T, T>(a, static_cast<const T*>(a.x), e, active, ij, v);
+        if (any_h) hanging_forward<T, 3>(v, h, active, i, j, sb);
+        load_pressure<T, T>(a, static_cast<const T*>(a.x), e, active, ij, spres[es]);
+        #pragma unroll
+        for (int c = 0; c < 3; ++c) ref_gradient<T>(v[c], G[c][0], G[c][1], G[c][2], i, j, b0, b1);
+        T Sv[3][Q];
+        #pragma unroll
+        for (int lq = 0; lq < Q; ++lq) {
+            const int qp = sidx(i, j, lq);
+            T Ji[9], wdj;
+            load_geo<T>(a, e, qp, active, Ji, wdj);
+            T g[3][3];
+            phys_grad(G, lq, Ji, g);
+            const T E00 = g[0][0], E11 = g[1][1], E22 = g[2][2];
+            const T E01 = T(0.5) * (g[0][1] + g[1][0]);
+            const T E02 = T(0.5) * (g[0][2] + g[2][0]);
+            const T E12 = T(0.5) * (g[1][2] + g[2][1]);
+            const T DD = E00 * E00 + E11 * E11 + E22 * E22 + T(2) * (E01 * E01 + E02 * E02 + E12 * E12);
+            const T muw = viscosity<T>(a, DD) * wdj;
+            const T pw = pressure_at<T>(spres[es], a.npr, ps, i, j, lq) * wdj;
+            T tau[3][3];
+            tau[0][0] = muw * E00 - pw;
+            tau[1][1] = muw * E11 - pw;
+            tau[2][2] = muw * E22 - pw;
+            tau[0][1] = tau[1][0] = muw * E01;
+            tau[0][2] = tau[2][0] = muw * E02;
+            tau[1][2] = tau[2][1] = muw * E12;
+            gq[lq] = -wdj * (g[0][0] + g[1][1] + g[2][2]);
+            #pragma unroll
+            for (int c = 0; c < 3; ++c) Sv[c][lq] = -wdj * T(a.body[c]);
+            ref_stress(G, lq, Ji, tau);
+        }
+        T out[3][N1];
+        #pragma unroll
+        for (int c = 0; c < 3; ++c) ref_gradient_T<T, true>(G[c][0], G[c][1], G[c][2], Sv[c], out[c], i, j, b0, b1, b2);
+        pressure_rows<T>(gq, a.npr, ps, i, j, ij, active, sb, static_cast<T*>(a.y) + 3 * a.Nv + e * a.npr);
+        if (any_h) hanging_transpose<T, 3>(out, h, active, i, j, sb);
+        scatter_velocity<T>(a, static_cast<T*>(a.y), e, active, ij, out);
+        return;
+    } else if constexpr (MODE == MODE_APPLY) {
+        // linearisation at u, recomputed at every quadrature point
+        T lin[8][Q];     // mu w detJ, kappa w detJ, D(u) (6)
+        {
+            T v[3][N1];
+            gather_velocity<T, T>(a, static_cast<const T*>(a.u), e, active, ij, v);
+            if (any_h) hanging_forward<T, 3>(v, h, active, i, j, sb);
+            #pragma unroll
+            for (int c = 0; c < 3; ++c) ref_gradient<T>(v[c], G[c][0], G[c][1], G[c][2], i, j, b0, b1);
+            #pragma unroll
+            for (int lq = 0; lq < Q; ++lq) {
+                const int qp = sidx(i, j, lq);
+                T Ji[9], wdj;
+                load_geo<T>(a, e, qp, active, Ji, wdj);
+                T g[3][3];
+                phys_grad(G, lq, Ji, g);
+                const T E00 = g[0][0], E11 = g[1][1], E22 = g[2][2];
+                const T E01 = T(0.5) * (g[0][1] + g[1][0]);
+                const T E02 = T(0.5) * (g[0][2] + g[2][0]);
+                const T E12 = T(0.5) * (g[1][2] + g[2][1]);
+                const T DD = E00 * E00 + E11 * E11 + E22 * E22 + T(2) * (E01 * E01 + E02 * E02 + E12 * E12);
+                const T mu = viscosity<T>(a, DD);
+                lin[0][lq] = mu * wdj;
+                lin[1][lq] = T(2) * T(a.gamma) * T(a.pexp) * mu * wdj / (T(a.gamma) * DD + T(a.delta));
+                lin[2][lq] = E00; lin[3][lq] = E11; lin[4][lq] = E22;
+                lin[5][lq] = E01; lin[6][lq] = E02; lin[7][lq] = E12;
+            }
+        }
+        T v[3][N1];
+        gather_velocity<T, T>(a, static_cast<const T*>(a.x), e, active, ij, v);
+        if (any_h) hanging_forward<T, 3>(v, h, active, i, j, sb);
+        load_pressure<T, T>(a, static_cast<const T*>(a.x), e, active, ij, spres[es]);
+        #pragma unroll
+        for (int c = 0; c < 3; ++c) ref_gradient<T>(v[c], G[c][0], G[c][1], G[c][2], i, j, b0, b1);
+        #pragma unroll
+        for (int lq = 0; lq < Q; ++lq) {
+            const int qp = sidx(i, j, lq);
+            T Ji[9], wdj;
+            load_geo<T>(a, e, qp, active, Ji, wdj);
+            T g[3][3];
+            phys_grad(G, lq, Ji, g);
+            const T E00 = g[0][0], E11 = g[1][1], E22 = g[2][2];
+            const T E01 = T(0.5) * (g[0][1] + g[1][0]);
+            const T E02 = T(0.5) * (g[0][2] + g[2][0]);
+            const T E12 = T(0.5) * (g[1][2] + g[2][1]);
+            const T muw = lin[0][lq], kw = lin[1][lq];
+            const T D00 = lin[2][lq], D11 = lin[3][lq], D22 = lin[4][lq];
+            const T D01 = lin[5][lq], D02 = lin[6][lq], D12 = lin[7][lq];
+            // mu' E = mu E + kappa (D:E) D, symmetric (TRANS gives the same map)
+            const T s = kw * (D00 * E00 + D11 * E11 + D22 * E22 + T(2) * (D01 * E01 + D02 * E02 + D12 * E12));
+            const T pw = pressure_at<T>(spres[es], a.npr, ps, i, j, lq) * wdj;
+            T tau[3][3];
+            tau[0][0] = muw * E00 + s * D00 - pw;
+            tau[1][1] = muw * E11 + s * D11 - pw;
+            tau[2][2] = muw * E22 + s * D22 - pw;
+            tau[0][1] = tau[1][0] = muw * E01 + s * D01;
+            tau[0][2] = tau[2][0] = muw * E02 + s * D02;
+            tau[1][2] = tau[2][1] = muw * E12 + s * D12;
+            gq[lq] = -wdj * (g[0][0] + g[1][1] + g[2][2]);
+            ref_stress(G, lq, Ji, tau);
+        }
+    } else if constexpr (MODE == MODE_LINEARIZE) {
+        T v[3][N1];
+        gather_velocity<T, double>(a, a.ud, e, active, ij, v);
+        if (any_h) hanging_forward<T, 3>(v, h, active, i, j, sb);
+        #pragma unroll
+        for (int c = 0; c < 3; ++c) ref_gradient<T>(v[c], G[c][0], G[c][1], G[c][2], i, j, b0, b1);
+        S* st = static_cast<S*>(a.state) + e * STATE_FIELDS * Q3;
+        #pragma unroll
+        for (int lq = 0; lq < Q; ++lq) {
+            const int qp = sidx(i, j, lq);
+            T Ji[9], wdj;
+            load_geo<T>(a, e, qp, active, Ji, wdj);
+            T g[3][3];
+            phys_grad(G, lq, Ji, g);
+            const T E00 = g[0][0], E11 = g[1][1], E22 = g[2][2];
+            const T E01 = T(0.5) * (g[0][1] + g[1][0]);
+            const T E02 = T(0.5) * (g[0][2] + g[2][0]);
+            const T E12 = T(0.5) * (g[1][2] + g[2][1]);
+            const T DD = E00 * E00 + E11 * E11 + E22 * E22 + T(2) * (E01 * E01 + E02 * E02 + E12 * E12);
+            const T mu = viscosity<T>(a, DD);
+            // -kappa w detJ >= 0 because p_n = (1-n)/(2n) <= 0
+            const T mk = -T(2) * T(a.gamma) * T(a.pexp) * mu * wdj / (T(a.gamma) * DD + T(a.delta));
+            const T sq = sqrt(mk > T(0) ? mk : T(0));
+            if (active) {
+                #pragma unroll
+                for (int r = 0; r < 9; ++r) st[r * Q3 + qp] = S(Ji[r]);
+                st[9 * Q3 + qp] = S(wdj);
+                st[10 * Q3 + qp] = S(mu * wdj);
+                st[11 * Q3 + qp] = S(sq * E00);
+                st[12 * Q3 + qp] = S(sq * E11);
+                st[13 * Q3 + qp] = S(sq * E22);
+                st[14 * Q3 + qp] = S(sq * E01);
+                st[15 * Q3 + qp] = S(sq * E02);
+                st[16 * Q3 + qp] = S(sq * E12);
+            }
+        }
+        return;
+    } else if constexpr (MODE == MODE_GRAD_A) {
+        T acc = 0;
+        T Gl[3][3][Q];
+        {
+            T v[3][N1];
+            gather_velocity<T, double>(a, a.lam, e, active, ij, v);
+            if (any_h) hanging_forward<T, 3>(v, h, active, i, j, sb);
+            #pragma unroll
+            for (int c = 0; c < 3; ++c) ref_gradient<T>(v[c], Gl[c][0], Gl[c][1], Gl[c][2], i, j, b0, b1);
+        }
+        T v[3][N1];
+        gather_velocity<T, double>(a, a.ud, e, active, ij, v);
+        if (any_h) hanging_forward<T, 3>(v, h, active, i, j, sb);
+        #pragma unroll
+        for (int c = 0; c < 3; ++c) ref_gradient<T>(v[c], G[c][0], G[c][1], G[c][2], i, j, b0, b1);
+        #pragma unroll
+        for (int lq = 0; lq < Q; ++lq) {
+            const int qp = sidx(i, j, lq);
+            T Ji[9], wdj;
+            load_geo<T>(a, e, qp, active, Ji, wdj);
+            T g[3][3], gl[3][3];
+            phys_grad(G, lq, Ji, g);
+            phys_grad(Gl, lq, Ji, gl);
+            T DD = 0, DL = 0;
+            #pragma unroll
+            for (int c = 0; c < 3; ++c)
+                #pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    const T Du = T(0.5) * (g[c][d] + g[d][c]);
+                    const T Dl = T(0.5) * (gl[c][d] + gl[d][c]);
+                    DD += Du * Du;
+                    DL += Dl * Du;
+                }
+            if (active) acc += viscosity<T>(a, DD) * wdj * DL;
+        }
+        // block reduction, one atomic per block
+        double r = double(acc);
+        #pragma unroll
+        for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o);
+        if ((tid & 31) == 0) sred[tid >> 5] = r;
+        __syncthreads();
+        if (tid == 0) {
+            double s = 0;
+            for (int w = 0; w < THREADS / 32; ++w) s += sred[w];
+            atomicAdd(a.gA, s * a.gA_scale);
+        }
+        return;
+    }
+
+    // ---- common back end of the two Jacobian modes: integrate and scatter
+    if constexpr (MODE == MODE_STATE_APPLY || MODE == MODE_APPLY) {
+        T out[3][N1];
+        T dummy[Q];
+        #pragma unroll
+        for (int c = 0; c < 3; ++c) ref_gradient_T<T, false>(G[c][0], G[c][1], G[c][2], dummy, out[c], i, j, b0, b1, b2);
+        pressure_rows<T>(gq, a.npr, ps, i, j, ij, active, sb, static_cast<T*>(a.y) + 3 * a.Nv + e * a.npr);
+        if (any_h) hanging_transpose<T, 3>(out, h, active, i, j, sb);
+        scatter_velocity<T>(a, static_cast<T*>(a.y), e, active, ij, out);
+    }
+}
+
+// ============================================================ basal faces
+// Robin term int_{Gamma_b} beta T v . T w ds (Eq. 2.4a in weak form, Eq. 2.5)
+// and its log(beta) adjoint product.  One thread per bottom-plane node
+// (i, j) of a basal element; 2-D sum factorisation through shared memory.
+constexpr int FPB = THREADS / N2;   // faces per block
+
+template <typename T>
+__device__ __forceinline__ void face_gather(const FaceArgs& a, const T* x, int64_t e, bool active, int ij,
+                                            T (&v)[3]) {
+    if (active) {
+        const int64_t g = a.nodes[e * N3 + ij];
+        v[0] = T(ld(x + 3 * g)); v[1] = T(ld(x + 3 * g + 1)); v[2] = T(ld(x + 3 * g + 2));
+        const int pi = a.pidx[e];
+        if (pi >= 0) {
+            const double* P = a.pel + int64_t(pi) * 6 * N2 + ij;
+            const T p00 = T(P[0]), p11 = T(P[N2]), p22 = T(P[2 * N2]);
+            const T p01 = T(P[3 * N2]), p02 = T(P[4 * N2]), p12 = T(P[5 * N2]);
+            const T x0 = v[0], x1 = v[1], x2 = v[2];
+            v[0] = p00 * x0 + p01 * x1 + p02 * x2;
+            v[1] = p01 * x0 + p11 * x1 + p12 * x2;
+            v[2] = p02 * x0 + p12 * x1 + p22 * x2;
+        }
+    } else {
+        v[0] = v[1] = v[2] = T(0);
+    }
+}
+
+// Hanging interpolation on the bottom plane: x-sweeps then y-sweeps (forward)
+// or y^T then x^T (transpose), for NC values per slot held in v.
+template <typename T, int NC, bool TRANSPOSE>
+__device__ void face_hanging(T (&v)[NC], uint32_t h, bool active, int i, int j, T* sb) {
+    #pragma unroll
+    for (int pass = 0; pass < 2; ++pass) {
+        const int axis = TRANSPOSE ? 1 - pass : pass;   // forward: x then y
+        #pragma unroll
+        for (int c = 0; c < NC; ++c) sb[c * N2 + i + N1 * j] = v[c];
+        __syncthreads();
+        if (active && h) {
+            const int bb = child_bit(h, axis);
+            const bool on = (axis == 0) ? line_hanging(h, 0, j, 0, K) : line_hanging(h, 1, i, 0, K);
+            if (on) {
+                #pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    T s = 0;
+                    #pragma unroll
+                    for (int m = 0; m < N1; ++m) {
+                        const T val = (axis == 0) ? sb[c * N2 + m + N1 * j] : sb[c * N2 + i + N1 * m];
+                        const int me = (axis == 0) ? i : j;
+                        s += (TRANSPOSE ? Tab<T>::I(bb, m, me) : Tab<T>::I(bb, me, m)) * val;
+                    }
+                    v[c] = s;
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// values at the face Gauss points (iq = i, jq = j) from bottom-plane nodal values
+template <typename T, int NC>
+__device__ __forceinline__ void face_interp(const T (&v)[NC], T (&o)[NC], int i, int j, T* sb) {
+    #pragma unroll
+    for (int c = 0; c < NC; ++c) sb[c * N2 + i + N1 * j] = v[c];
+    __syncthreads();
+    T t[NC];
+    #pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        T s = 0;
+        #pragma unroll
+        for (int m = 0; m < N1; ++m) s += Tab<T>::B(i, m) * sb[c * N2 + m + N1 * j];
+        t[c] = s;
+    }
+    __syncthreads();
+    #pragma unroll
+    for (int c = 0; c < NC; ++c) sb[c * N2 + i + N1 * j] = t[c];
+    __syncthreads();
+    #pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        T s = 0;
+        #pragma unroll
+        for (int m = 0; m < N1; ++m) s += Tab<T>::B(j, m) * sb[c * N2 + i + N1 * m];
+        o[c] = s;
+    }
+    __syncthreads();
+}
+
+// transposed interpolation: nodal values from values at face Gauss points
+template <typename T, int NC>
+__device__ __forceinline__ void face_interp_T(const T (&v)[NC], T (&o)[NC], int i, int j, T* sb) {
+    #pragma unroll
+    for (int c = 0; c < NC; ++c) sb[c * N2 + i + N1 * j] = v[c];
+    __syncthreads();
+    T t[NC];
+    #pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        T s = 0;
+        #pragma unroll
+        for (int m = 0; m < Q; ++m) s += Tab<T>::B(m, i) * sb[c * N2 + m + N1 * j];
+        t[c] = s;
+    }
+    __syncthreads();
+    #pragma unroll
+    for (int c = 0; c < NC; ++c) sb[c * N2 + i + N1 * j] = t[c];
+    __syncthreads();
+    #pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        T s = 0;
+        #pragma unroll
+        for (int m = 0; m < Q; ++m) s += Tab<T>::B(m, j) * sb[c * N2 + i + N1 * m];
+        o[c] = s;
+    }
+    __syncthreads();
+}
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(THREADS) face_kernel(FaceArgs a) {
+    constexpr int Q2 = Q * Q;
+    __shared__ T sbuf[FPB + 1][4 * N2];
+    const int tid = threadIdx.x;
+    const int fs = tid / N2;
+    const int ij = tid - fs * N2;
+    const int i = ij % N1, j = ij / N1;
+    const int64_t f = int64_t(blockIdx.x) * FPB + fs;
+    const bool active = (fs < FPB) && (f < a.nF);
+    T* sb = sbuf[fs];
+    const int64_t e = active ? a.face_elem[f] : 0;
+    const uint32_t h = active ? a.hang[e] : 0u;
+    const bool any_h = __syncthreads_or(int(h & ((1u << HANG_CHILD0) - 1))) != 0;
+
+    // log(beta) at the face nodes (hanging-interpolated), then at Gauss points
+    T lb[1];
+    lb[0] = active ? T(a.logbeta[a.fmap[f * N2 + ij]]) : T(0);
+    if (any_h) face_hanging<T, 1, false>(lb, h, active, i, j, sb);
+    T lbq[1];
+    face_interp<T, 1>(lb, lbq, i, j, sb);
+    const int fq = i + Q * j;
+    T wa = 0, n0 = 0, n1 = 0, n2 = 0;
+    if (active) {
+        const double* fg = a.fgeo + f * 4 * Q2 + fq;
+        wa = T(fg[0]); n0 = T(fg[Q2]); n1 = T(fg[2 * Q2]); n2 = T(fg[3 * Q2]);
+    }
+    const T bw = exp(lbq[0]) * wa;
+
+    if constexpr (MODE == FACE_APPLY) {
+        T v[3];
+        face_gather<T>(a, static_cast<const T*>(a.x), e, active, ij, v);
+        if (any_h) face_hanging<T, 3, false>(v, h, active, i, j, sb);
+        T vq[3];
+        face_interp<T, 3>(v, vq, i, j, sb);
+        const T nv = n0 * vq[0] + n1 * vq[1] + n2 * vq[2];
+        T t[3] = {bw * (vq[0] - nv * n0), bw * (vq[1] - nv * n1), bw * (vq[2] - nv * n2)};
+        T o[3];
+        face_interp_T<T, 3>(t, o, i, j, sb);
+        if (any_h) face_hanging<T, 3, true>(o, h, active, i, j, sb);
+        if (active) {
+            const int pi = a.pidx[e];
+            if (pi >= 0) {
+                const double* P = a.pel + int64_t(pi) * 6 * N2 + ij;
+                const T p00 = T(P[0]), p11 = T(P[N2]), p22 = T(P[2 * N2]);
+                const T p01 = T(P[3 * N2]), p02 = T(P[4 * N2]), p12 = T(P[5 * N2]);
+                const T x0 = o[0], x1 = o[1], x2 = o[2];
+                o[0] = p00 * x0 + p01 * x1 + p02 * x2;
+                o[1] = p01 * x0 + p11 * x1 + p12 * x2;
+                o[2] = p02 * x0 + p12 * x1 + p22 * x2;
+            }
+            const int64_t g = a.nodes[e * N3 + ij];
+            T* y = static_cast<T*>(a.y);
+            atomic_add(y + 3 * g, o[0]);
+            atomic_add(y + 3 * g + 1, o[1]);
+            atomic_add(y + 3 * g + 2, o[2]);
+        }
+    } else {
+        // g_j += int beta phi_j (T lambda) . (T u) ds
+        T v[3], w[3];
+        face_gather<T>(a, a.u, e, active, ij, v);
+        face_gather<T>(a, a.lam, e, active, ij, w);
+        if (any_h) {
+            face_hanging<T, 3, false>(v, h, active, i, j, sb);
+            face_hanging<T, 3, false>(w, h, active, i, j, sb);
+        }
+        T vq[3], wq[3];
+        face_interp<T, 3>(v, vq, i, j, sb);
+        face_interp<T, 3>(w, wq, i, j, sb);
+        const T nu = n0 * vq[0] + n1 * vq[1] + n2 * vq[2];
+        const T nl = n0 * wq[0] + n1 * wq[1] + n2 * wq[2];
+        const T s = bw * ((vq[0] - nu * n0) * (wq[0] - nl * n0) + (vq[1] - nu * n1) * (wq[1] - nl * n1) +
+                          (vq[2] - nu * n2) * (wq[2] - nl * n2));
+        T sv[1] = {s}, o[1];
+        face_interp_T<T, 1>(sv, o, i, j, sb);
+        if (any_h) face_hanging<T, 1, true>(o, h, active, i, j, sb);
+        if (active) atomic_add(a.g + a.fmap[f * N2 + ij], double(o[0]));
+    }
+}
+
+// ---------------------------------------------------------------- launchers
+template <typename T, typename S, int MODE, bool TRANS>
+int launch_elem_t(const ElemArgs& a, cudaStream_t s) {
+    const int64_t blocks = (a.E + EPB - 1) / EPB;
+    if (blocks == 0) return int(cudaSuccess);
+    elem_kernel<T, S, MODE, TRANS><<<unsigned(blocks), THREADS, 0, s>>>(a);
+    return int(cudaGetLastError());
+}
+
+template <typename T, int MODE>
+int launch_face_t(const FaceArgs& a, cudaStream_t s) {
+    const int64_t blocks = (a.nF + FPB - 1) / FPB;
+    if (blocks == 0) return int(cudaSuccess);
+    face_kernel<T, MODE><<<unsigned(blocks), THREADS, 0, s>>>(a);
+    return int(cudaGetLastError());
+}
+
+inline int launch_elem_any(int mode, int prec, int state_prec, bool trans, const ElemArgs& a, cudaStream_t s) {
+    const bool f32 = prec == 1;
+    switch (mode) {
+        case MODE_RESIDUAL:
+            return f32 ? launch_elem_t<float, float, MODE_RESIDUAL, false>(a, s)
+                       : launch_elem_t<double, double, MODE_RESIDUAL, false>(a, s);
+        case MODE_APPLY:
+            if (trans) return f32 ? launch_elem_t<float, float, MODE_APPLY, true>(a, s)
+                                  : launch_elem_t<double, double, MODE_APPLY, true>(a, s);
+            return f32 ? launch_elem_t<float, float, MODE_APPLY, false>(a, s)
+                       : launch_elem_t<double, double, MODE_APPLY, false>(a, s);
+        case MODE_LINEARIZE:
+            return state_prec == 1 ? launch_elem_t<double, float, MODE_LINEARIZE, false>(a, s)
+                                   : launch_elem_t<double, double, MODE_LINEARIZE, false>(a, s);
+        case MODE_STATE_APPLY:
+            if (trans) return f32 ? launch_elem_t<float, float, MODE_STATE_APPLY, true>(a, s)
+                                  : launch_elem_t<double, double, MODE_STATE_APPLY, true>(a, s);
+            return f32 ? launch_elem_t<float, float, MODE_STATE_APPLY, false>(a, s)
+                       : launch_elem_t<double, double, MODE_STATE_APPLY, false>(a, s);
+        case MODE_GRAD_A:
+            return launch_elem_t<double, double, MODE_GRAD_A, false>(a, s);
+        default:
+            return int(cudaErrorInvalidValue);
+    }
+}
+
+inline int launch_face_any(int mode, int prec, const FaceArgs& a, cudaStream_t s) {
+    if (mode == FACE_GRAD_LOGBETA) return launch_face_t<double, FACE_GRAD_LOGBETA>(a, s);
+    return prec == 1 ? launch_face_t<float, FACE_APPLY>(a, s) : launch_face_t<double, FACE_APPLY>(a, s);
+}
+
+// Upload the degree-K tables (host struct Tables1D for each pressure space).
+inline int upload_tables_any(const void* p) {
+    const Tables1D* t = static_cast<const Tables1D*>(p);   // t[0]: P space, t[1]: Q space
+    double B[Q][N1], Dg[Q][Q], I[2][N1][N1], P1[2][Q][N1];
+    float fb[Q][N1], fd[Q][Q], fi[2][N1][N1], fp[2][Q][N1];
+    int pm[2][NPRK > 0 ? NPRK : 1][3] = {};
+    int np[2];
+    for (int a = 0; a < Q; ++a)
+        for (int b = 0; b < N1; ++b) { B[a][b] = t[0].B[a][b]; fb[a][b] = float(B[a][b]); }
+    for (int a = 0; a < Q; ++a)
+        for (int b = 0; b < Q; ++b) { Dg[a][b] = t[0].Dg[a][b]; fd[a][b] = float(Dg[a][b]); }
+    for (int hh = 0; hh < 2; ++hh)
+        for (int a = 0; a < N1; ++a)
+            for (int b = 0; b < N1; ++b) { I[hh][a][b] = t[0].I[hh][a][b]; fi[hh][a][b] = float(I[hh][a][b]); }
+    for (int sp = 0; sp < 2; ++sp) {
+        np[sp] = t[sp].npr;
+        for (int a = 0; a < Q; ++a)
+            for (int b = 0; b < N1; ++b) { P1[sp][a][b] = t[sp].P1[a][b]; fp[sp][a][b] = float(P1[sp][a][b]); }
+        for (int m = 0; m < t[sp].npr && m < NPRK; ++m)
+            for (int c = 0; c < 3; ++c) pm[sp][m][c] = t[sp].pmode[m][c];
+    }
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(cB, B, sizeof(B));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(cDg, Dg, sizeof(Dg));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(cI, I, sizeof(I));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(cP1, P1, sizeof(P1));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(cPm, pm, sizeof(pm));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(cNpr, np, sizeof(np));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(fB, fb, sizeof(fb));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(fDg, fd, sizeof(fd));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(fI, fi, sizeof(fi));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(fP1, fp, sizeof(fp));
+    return int(e);
+}
+
+}  // namespace dev
+}  // namespace stokes
+
+#define STOKES_DEFINE_DEGREE(KK)                                                                   \
+    namespace stokes {                                                                             \
+    int launch_elem_k##KK(int mode, int prec, int state_prec, bool trans, const ElemArgs& a,        \
+                          cudaStream_t s) {                                                        \
+        return dev::launch_elem_any(mode, prec, state_prec, trans, a, s);                           \
+    }                                                                                              \
+    int launch_face_k##KK(int mode, int prec, const FaceArgs& a, cudaStream_t s) {                 \
+        return dev::launch_face_any(mode, prec, a, s);                                             \
+    }                                                                                              \
+    int upload_tables_k##KK(const void* t) { return dev::upload_tables_any(t); }                   \
+    }

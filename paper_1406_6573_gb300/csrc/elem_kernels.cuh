@@ -1,0 +1,402 @@
+// Sum-factorised element kernels of the nonlinear Stokes operator (sm_103a).
+//
+// One thread owns one (i, j) column of GLL nodes / Gauss points of an element
+// and loops over the third index l: contractions along zeta run in registers,
+// contractions along xi and eta go through shared memory (Section 3.3: every
+// element operation is a sequence of 1-D kernels).  A block holds EPB
+// elements.  Per element:
+//   gather (R_i: global node per slot, basal projector P, hanging-node 1-D
+//   interpolation) -> reference gradients at the Gauss points (3 interpolation
+//   sweeps + 3 collocated derivative sweeps per field) -> pointwise physics
+//   (Glen viscosity Eq. 2.2, Newton tensor Eq. 2.7, pressure / divergence
+//   terms of Eq. 2.5) -> transposed sweeps -> R_i^T -> atomic scatter-add.
+// Each translation unit includes this header with STOKES_K defined and gets
+// its own constant-memory tables for that degree.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "common.h"
+#include "hanging.h"
+#include "kernels.h"
+
+#ifndef STOKES_K
+#error "STOKES_K must be defined before including elem_kernels.cuh"
+#endif
+
+namespace stokes {
+namespace dev {
+
+constexpr int K = STOKES_K;
+constexpr int N1 = K + 1;
+constexpr int Q = N1;
+constexpr int N2 = N1 * N1;
+constexpr int N3 = N1 * N1 * N1;
+constexpr int THREADS = 256;
+constexpr int EPB = THREADS / N2;     // elements per block
+constexpr int NPRK = (K - 1) * (K - 1) * (K - 1) > K * (K + 1) * (K + 2) / 6
+                         ? (K - 1) * (K - 1) * (K - 1) : K * (K + 1) * (K + 2) / 6;
+
+// ---------------------------------------------------------------- tables
+__constant__ double cB[Q][N1];        // GLL Lagrange at Gauss points
+__constant__ double cDg[Q][Q];        // Gauss collocation derivative
+__constant__ double cI[2][N1][N1];    // hanging interpolation, per half
+__constant__ double cP1[2][Q][N1];    // pressure 1-D factors [pspace][iq][a]
+__constant__ int cPm[2][NPRK > 0 ? NPRK : 1][3];
+__constant__ int cNpr[2];
+__constant__ float fB[Q][N1];
+__constant__ float fDg[Q][Q];
+__constant__ float fI[2][N1][N1];
+__constant__ float fP1[2][Q][N1];
+
+template <typename T> struct Tab;
+template <> struct Tab<double> {
+    static __device__ __forceinline__ double B(int a, int b) { return cB[a][b]; }
+    static __device__ __forceinline__ double Dg(int a, int b) { return cDg[a][b]; }
+    static __device__ __forceinline__ double I(int h, int a, int b) { return cI[h][a][b]; }
+    static __device__ __forceinline__ double P1(int s, int a, int b) { return cP1[s][a][b]; }
+};
+template <> struct Tab<float> {
+    static __device__ __forceinline__ float B(int a, int b) { return fB[a][b]; }
+    static __device__ __forceinline__ float Dg(int a, int b) { return fDg[a][b]; }
+    static __device__ __forceinline__ float I(int h, int a, int b) { return fI[h][a][b]; }
+    static __device__ __forceinline__ float P1(int s, int a, int b) { return fP1[s][a][b]; }
+};
+
+// --------------------------------------------------------------- helpers
+template <typename T> __device__ __forceinline__ T ld(const T* p) { return __ldg(p); }
+
+__device__ __forceinline__ void atomic_add(double* p, double v) { atomicAdd(p, v); }
+__device__ __forceinline__ void atomic_add(float* p, float v) { atomicAdd(p, v); }
+
+// Viscosity mu = C (gamma s + delta)^p_n, s = D:D; special-cased for n = 3.
+template <typename T>
+__device__ __forceinline__ T viscosity(const ElemArgs& a, T DD) {
+    T arg = T(a.gamma) * DD + T(a.delta);
+    if (a.n_is_3) return T(a.C) * rcbrt_t(arg);
+    return T(a.C) * pow(arg, T(a.pexp));
+}
+
+// Per-element shared memory.
+template <typename T> struct Smem {
+    T buf[EPB][3][N3];
+    T pres[EPB][NPRK > 0 ? NPRK : 1];
+};
+
+// slot / qp index within the element tensor: (i, j, l) -> i + N1 (j + N1 l)
+__device__ __forceinline__ int sidx(int i, int j, int l) { return i + N1 * (j + N1 * l); }
+
+// ----------------------------------------------------- hanging sweeps
+// Forward R_i interpolation on the element tensor held as columns v[c][l]
+// (thread (i, j)).  All threads of the block call it (it synchronises).
+template <typename T, int NC>
+__device__ void hanging_forward(T (&v)[NC][N1], uint32_t h, bool active, int i, int j, T* sb) {
+    // x-sweeps: lines parallel to x at (j, l)
+    for (int c = 0; c < NC; ++c) {
+        #pragma unroll
+        for (int l = 0; l < N1; ++l) sb[sidx(i, j, l)] = v[c][l];
+        __syncthreads();
+        if (active && h) {
+            const int bx = child_bit(h, 0);
+            #pragma unroll
+            for (int l = 0; l < N1; ++l) {
+                if (line_hanging(h, 0, j, l, K)) {
+                    T s = 0;
+                    #pragma unroll
+                    for (int m = 0; m < N1; ++m) s += Tab<T>::I(bx, i, m) * sb[sidx(m, j, l)];
+                    v[c][l] = s;
+                }
+            }
+        }
+        __syncthreads();
+        // y-sweeps: lines parallel to y at (i, l)
+        #pragma unroll
+        for (int l = 0; l < N1; ++l) sb[sidx(i, j, l)] = v[c][l];
+        __syncthreads();
+        if (active && h) {
+            const int by = child_bit(h, 1);
+            #pragma unroll
+            for (int l = 0; l < N1; ++l) {
+                if (line_hanging(h, 1, i, l, K)) {
+                    T s = 0;
+                    #pragma unroll
+                    for (int m = 0; m < N1; ++m) s += Tab<T>::I(by, j, m) * sb[sidx(i, m, l)];
+                    v[c][l] = s;
+                }
+            }
+        }
+        __syncthreads();
+        // z-sweeps: the thread's own column (registers)
+        if (active && h && line_hanging(h, 2, i, j, K)) {
+            const int bz = child_bit(h, 2);
+            T t[N1];
+            #pragma unroll
+            for (int l = 0; l < N1; ++l) {
+                T s = 0;
+                #pragma unroll
+                for (int m = 0; m < N1; ++m) s += Tab<T>::I(bz, l, m) * v[c][m];
+                t[l] = s;
+            }
+            #pragma unroll
+            for (int l = 0; l < N1; ++l) v[c][l] = t[l];
+        }
+    }
+}
+
+// Transposed R_i interpolation (z^T, then y^T, then x^T).
+template <typename T, int NC>
+__device__ void hanging_transpose(T (&v)[NC][N1], uint32_t h, bool active, int i, int j, T* sb) {
+    for (int c = 0; c < NC; ++c) {
+        if (active && h && line_hanging(h, 2, i, j, K)) {
+            const int bz = child_bit(h, 2);
+            T t[N1];
+            #pragma unroll
+            for (int m = 0; m < N1; ++m) {
+                T s = 0;
+                #pragma unroll
+                for (int l = 0; l < N1; ++l) s += Tab<T>::I(bz, l, m) * v[c][l];
+                t[m] = s;
+            }
+            #pragma unroll
+            for (int l = 0; l < N1; ++l) v[c][l] = t[l];
+        }
+        #pragma unroll
+        for (int l = 0; l < N1; ++l) sb[sidx(i, j, l)] = v[c][l];
+        __syncthreads();
+        if (active && h) {
+            const int by = child_bit(h, 1);
+            #pragma unroll
+            for (int l = 0; l < N1; ++l) {
+                if (line_hanging(h, 1, i, l, K)) {
+                    T s = 0;
+                    #pragma unroll
+                    for (int m = 0; m < N1; ++m) s += Tab<T>::I(by, m, j) * sb[sidx(i, m, l)];
+                    v[c][l] = s;
+                }
+            }
+        }
+        __syncthreads();
+        #pragma unroll
+        for (int l = 0; l < N1; ++l) sb[sidx(i, j, l)] = v[c][l];
+        __syncthreads();
+        if (active && h) {
+            const int bx = child_bit(h, 0);
+            #pragma unroll
+            for (int l = 0; l < N1; ++l) {
+                if (line_hanging(h, 0, j, l, K)) {
+                    T s = 0;
+                    #pragma unroll
+                    for (int m = 0; m < N1; ++m) s += Tab<T>::I(bx, m, i) * sb[sidx(m, j, l)];
+                    v[c][l] = s;
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ----------------------------------------------- sum-factorised gradient
+// Reference gradient at the Gauss points (iq = i, jq = j, lq) of the field
+// whose nodal column the thread holds in vin.  Uses buffers b0, b1.
+template <typename T>
+__device__ __forceinline__ void ref_gradient(const T (&vin)[N1], T (&gx)[Q], T (&gy)[Q], T (&gz)[Q],
+                                             int i, int j, T* b0, T* b1) {
+    T a[Q];
+    #pragma unroll
+    for (int lq = 0; lq < Q; ++lq) {            // zeta interpolation (registers)
+        T s = 0;
+        #pragma unroll
+        for (int l = 0; l < N1; ++l) s += Tab<T>::B(lq, l) * vin[l];
+        a[lq] = s;
+    }
+    #pragma unroll
+    for (int lq = 0; lq < Q; ++lq) b0[sidx(i, j, lq)] = a[lq];
+    __syncthreads();
+    #pragma unroll
+    for (int lq = 0; lq < Q; ++lq) {            // eta interpolation: thread (i, jq = j)
+        T s = 0;
+        #pragma unroll
+        for (int m = 0; m < N1; ++m) s += Tab<T>::B(j, m) * b0[sidx(i, m, lq)];
+        a[lq] = s;
+    }
+    #pragma unroll
+    for (int lq = 0; lq < Q; ++lq) b1[sidx(i, j, lq)] = a[lq];
+    __syncthreads();
+    #pragma unroll
+    for (int lq = 0; lq < Q; ++lq) {            // xi interpolation: thread (iq = i, jq = j)
+        T s = 0;
+        #pragma unroll
+        for (int m = 0; m < N1; ++m) s += Tab<T>::B(i, m) * b1[sidx(m, j, lq)];
+        a[lq] = s;
+    }
+    #pragma unroll
+    for (int lq = 0; lq < Q; ++lq) b0[sidx(i, j, lq)] = a[lq];
+    __syncthreads();
+    #pragma unroll
+    for (int lq = 0; lq < Q; ++lq) {            // collocated derivatives
+        T sx = 0, sy = 0, sz = 0;
+        #pragma unroll
+        for (int m = 0; m < Q; ++m) {
+            sx += Tab<T>::Dg(i, m) * b0[sidx(m, j, lq)];
+            sy += Tab<T>::Dg(j, m) * b0[sidx(i, m, lq)];
+            sz += Tab<T>::Dg(lq, m) * a[m];
+        }
+        gx[lq] = sx; gy[lq] = sy; gz[lq] = sz;
+    }
+    __syncthreads();
+}
+
+// Transposed gradient: nodal column out[l] of
+//   sum_qp (d phi/d xi) Sx + (d phi/d eta) Sy + (d phi/d zeta) Sz + phi Sv.
+template <typename T, bool HAS_VAL>
+__device__ __forceinline__ void ref_gradient_T(const T (&Sx)[Q], const T (&Sy)[Q], const T (&Sz)[Q],
+                                               const T (&Sv)[Q], T (&out)[N1], int i, int j,
+                                               T* b0, T* b1, T* b2) {
+    T t[Q];
+    #pragma unroll
+    for (int lq = 0; lq < Q; ++lq) {
+        b0[sidx(i, j, lq)] = Sx[lq];
+        b1[sidx(i, j, lq)] = Sy[lq];
+        T s = HAS_VAL ? Sv[lq] : T(0);
+        #pragma unroll
+        for (int m = 0; m < Q; ++m) s += Tab<T>::Dg(m, lq) * Sz[m];
+        t[lq] = s;
+    }
+    __syncthreads();
+    #pragma unroll
+    for (int lq = 0; lq < Q; ++lq) {
+        T s = t[lq];
+        #pragma unroll
+        for (int m = 0; m < Q; ++m)
+            s += Tab<T>::Dg(m, i) * b0[sidx(m, j, lq)] + Tab<T>::Dg(m, j) * b1[sidx(i, m, lq)];
+        t[lq] = s;
+    }
+    #pragma unroll
+    for (int lq = 0; lq < Q; ++lq) b2[sidx(i, j, lq)] = t[lq];
+    __syncthreads();
+    #pragma unroll
+    for (int lq = 0; lq < Q; ++lq) {            // xi^T: thread (node i, jq = j)
+        T s = 0;
+        #pragma unroll
+        for (int m = 0; m < Q; ++m) s += Tab<T>::B(m, i) * b2[sidx(m, j, lq)];
+        t[lq] = s;
+    }
+    #pragma unroll
+    for (int lq = 0; lq < Q; ++lq) b0[sidx(i, j, lq)] = t[lq];
+    __syncthreads();
+    #pragma unroll
+    for (int lq = 0; lq < Q; ++lq) {            // eta^T: thread (node i, node j)
+        T s = 0;
+        #pragma unroll
+        for (int m = 0; m < Q; ++m) s += Tab<T>::B(m, j) * b0[sidx(i, m, lq)];
+        t[lq] = s;
+    }
+    #pragma unroll
+    for (int l = 0; l < N1; ++l) {              // zeta^T (registers)
+        T s = 0;
+        #pragma unroll
+        for (int lq = 0; lq < Q; ++lq) s += Tab<T>::B(lq, l) * t[lq];
+        out[l] = s;
+    }
+    __syncthreads();
+}
+
+// ------------------------------------------------------------ gather
+// Velocity columns of element e (3 components) from a state vector x,
+// with the basal projector applied at bottom-plane slots.
+template <typename T, typename TIN>
+__device__ __forceinline__ void gather_velocity(const ElemArgs& a, const TIN* x, int64_t e, bool active,
+                                                int ij, T (&v)[3][N1]) {
+    #pragma unroll
+    for (int l = 0; l < N1; ++l) {
+        if (active) {
+            const int64_t g = a.nodes[e * N3 + ij + N2 * l];
+            v[0][l] = T(ld(x + 3 * g));
+            v[1][l] = T(ld(x + 3 * g + 1));
+            v[2][l] = T(ld(x + 3 * g + 2));
+        } else {
+            v[0][l] = v[1][l] = v[2][l] = T(0);
+        }
+    }
+    if (active) {
+        const int pi = a.pidx[e];
+        if (pi >= 0) {
+            const double* P = a.pel + int64_t(pi) * 6 * N2 + ij;
+            const T p00 = T(P[0]), p11 = T(P[N2]), p22 = T(P[2 * N2]);
+            const T p01 = T(P[3 * N2]), p02 = T(P[4 * N2]), p12 = T(P[5 * N2]);
+            const T x0 = v[0][0], x1 = v[1][0], x2 = v[2][0];
+            v[0][0] = p00 * x0 + p01 * x1 + p02 * x2;
+            v[1][0] = p01 * x0 + p11 * x1 + p12 * x2;
+            v[2][0] = p02 * x0 + p12 * x1 + p22 * x2;
+        }
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void scatter_velocity(const ElemArgs& a, T* y, int64_t e, bool active, int ij,
+                                                 T (&v)[3][N1]) {
+    if (!active) return;
+    const int pi = a.pidx[e];
+    if (pi >= 0) {
+        const double* P = a.pel + int64_t(pi) * 6 * N2 + ij;
+        const T p00 = T(P[0]), p11 = T(P[N2]), p22 = T(P[2 * N2]);
+        const T p01 = T(P[3 * N2]), p02 = T(P[4 * N2]), p12 = T(P[5 * N2]);
+        const T x0 = v[0][0], x1 = v[1][0], x2 = v[2][0];
+        v[0][0] = p00 * x0 + p01 * x1 + p02 * x2;
+        v[1][0] = p01 * x0 + p11 * x1 + p12 * x2;
+        v[2][0] = p02 * x0 + p12 * x1 + p22 * x2;
+    }
+    #pragma unroll
+    for (int l = 0; l < N1; ++l) {
+        const int64_t g = a.nodes[e * N3 + ij + N2 * l];
+        atomic_add(y + 3 * g, v[0][l]);
+        atomic_add(y + 3 * g + 1, v[1][l]);
+        atomic_add(y + 3 * g + 2, v[2][l]);
+    }
+}
+
+// Pressure value at Gauss point (i, j, lq) from the element's pressure dofs in smem.
+template <typename T>
+__device__ __forceinline__ T pressure_at(const T* pres, int npr, int ps, int i, int j, int lq) {
+    T s = 0;
+    #pragma unroll
+    for (int b = 0; b < NPRK; ++b) {
+        if (b < npr) {
+            s += pres[b] * Tab<T>::P1(ps, i, cPm[ps][b][0]) * Tab<T>::P1(ps, j, cPm[ps][b][1]) *
+                 Tab<T>::P1(ps, lq, cPm[ps][b][2]);
+        }
+    }
+    return s;
+}
+
+// Pressure rows: out[b] = sum_qp psi_b(qp) gq(qp), reduced over the element's
+// threads through shared memory in chunks; written (not accumulated) to dst.
+template <typename T>
+__device__ void pressure_rows(const T (&gq)[Q], int npr, int ps, int i, int j, int ij, bool active,
+                              T* sb, T* dst) {
+    constexpr int CH = (3 * N3) / N2;   // rows per chunk
+    for (int b0 = 0; b0 < npr; b0 += CH) {
+        #pragma unroll
+        for (int cb = 0; cb < CH; ++cb) {
+            const int b = b0 + cb;
+            T s = 0;
+            if (b < npr) {
+                const T f = Tab<T>::P1(ps, i, cPm[ps][b][0]) * Tab<T>::P1(ps, j, cPm[ps][b][1]);
+                #pragma unroll
+                for (int lq = 0; lq < Q; ++lq) s += Tab<T>::P1(ps, lq, cPm[ps][b][2]) * gq[lq];
+                s *= f;
+            }
+            sb[cb * N2 + ij] = s;
+        }
+        __syncthreads();
+        if (active && ij < CH && b0 + ij < npr) {
+            T s = 0;
+            for (int t = 0; t < N2; ++t) s += sb[ij * N2 + t];
+            dst[b0 + ij] = s;
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace dev
+}  // namespace stokes

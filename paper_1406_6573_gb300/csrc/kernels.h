@@ -1,0 +1,84 @@
+// Kernel argument blocks and launcher declarations (host + device).
+#pragma once
+
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace stokes {
+
+enum ElemMode : int {
+    MODE_RESIDUAL = 0,     // r  = R^T(int sigma(u, p) : grad v - b . v) , -(q, div u)
+    MODE_APPLY = 1,        // y  = J(u) x, linearisation recomputed per quadrature point
+    MODE_LINEARIZE = 2,    // state <- per-qp Newton coefficients at u (FP64 arithmetic)
+    MODE_STATE_APPLY = 3,  // y  = J x from the stored state
+    MODE_GRAD_A = 4,       // g_A = -(1/(n A)) int mu D(lambda) : D(u)
+};
+
+// Number of stored values per quadrature point of the linearised state:
+// Jinv (9, reference-major), w detJ, mu w detJ, Dhat (6: 00 11 22 01 02 12).
+constexpr int STATE_FIELDS = 17;
+
+struct ElemArgs {
+    int64_t E, Nv;
+    int npr, pspace, any_hang;
+    const int32_t* nodes;      // [E][n1^3]
+    const uint32_t* hang;      // [E]
+    const double* geo;         // [E][10][q^3]
+    const int32_t* pidx;       // [E]
+    const double* pel;         // [nP][6][n1^2]
+    const void* x;             // input state vector (residual: up; apply: direction)
+    void* y;                   // output state vector (accumulated; zeroed by the caller)
+    const void* u;             // linearisation point (fused apply), same type as x
+    const double* ud;          // FP64 state (linearize, gradient)
+    const double* lam;         // FP64 adjoint (gradient)
+    void* state;               // [E][17][q^3] (linearize output)
+    const void* cstate;        // same (state apply input)
+    double C, gamma, delta, pexp;
+    int n_is_3;
+    double body[3];
+    double* gA;                // gradient output (accumulated)
+    double gA_scale;
+};
+
+struct FaceArgs {
+    int64_t nF, Nv;
+    const int32_t* face_elem;  // [nF]
+    const int32_t* nodes;
+    const uint32_t* hang;
+    const int32_t* pidx;
+    const double* pel;
+    const double* fgeo;        // [nF][4][q^2]
+    const int32_t* fmap;       // [nF][n1^2]
+    const double* logbeta;     // [Nb]
+    const void* x;             // vector whose basal trace enters beta T x
+    void* y;                   // output (accumulated)
+    const double* u;           // gradient: state
+    const double* lam;         // gradient: adjoint
+    double* g;                 // gradient output [Nb] (accumulated)
+};
+
+enum FaceMode : int { FACE_APPLY = 0, FACE_GRAD_LOGBETA = 1 };
+
+// Per-degree launchers (one translation unit per degree).  prec: 0 f64, 1 f32.
+// Return a cudaError_t value.
+#define STOKES_DECLARE_DEGREE(KK)                                                            \
+    int launch_elem_k##KK(int mode, int prec, int state_prec, bool trans, const ElemArgs& a,  \
+                          cudaStream_t s);                                                    \
+    int launch_face_k##KK(int mode, int prec, const FaceArgs& a, cudaStream_t s);             \
+    int upload_tables_k##KK(const void* tables_k);
+STOKES_DECLARE_DEGREE(2)
+STOKES_DECLARE_DEGREE(3)
+STOKES_DECLARE_DEGREE(4)
+#undef STOKES_DECLARE_DEGREE
+
+// Degree-independent kernels (misc.cu).
+int launch_constraint(int prec, int64_t Nb, const int32_t* basal_nodes, const double* basal_P,
+                      const void* x, void* y, cudaStream_t s);
+
+}  // namespace stokes
+
+#ifdef __CUDACC__
+__device__ __forceinline__ double rcbrt_t(double x) { return rcbrt(x); }
+__device__ __forceinline__ float rcbrt_t(float x) { return rcbrtf(x); }
+#endif

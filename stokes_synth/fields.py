@@ -4,8 +4,8 @@ Every field is a finite cosine series
     f(x, y) = mean + sum_m amp[m] * cos(kx[m] x + ky[m] y + phase[m]),
 with wavenumbers on the lattice 2*pi*(j/Lx, l/Ly) so that the field is
 periodic on [0, Lx) x [0, Ly).  The recipes follow the paper's synthetic
-workloads: the random Fourier series of Section 4.3 (Eq. 4.3 of the test
-problem, decay |(j,k)|^-gamma) for beds, a sum of 16 sinusoids for the
+workloads: the random Fourier series of Section 4.3 (Eq. 4.2, decay
+|(j,k)|^-gamma) for beds, a sum of 16 sinusoids for the
 surface, and a Gaussian random field realised by random Fourier features
 for log(beta).
 """

@@ -1,0 +1,97 @@
+"""CPU checks of the CUDA library: it loads, exports every symbol of
+include/stokes.h, rejects bad arguments, and its host mesh builder agrees
+with the oracle's independent construction (node count and coordinates,
+basal node set, element count)."""
+import re
+
+import numpy as np
+import pytest
+
+import stokes_synth as synth
+from oracle import OracleMesh
+from paper_1406_6573_gb300 import capi
+from paper_1406_6573_gb300.mesh import Mesh, mesh_desc
+
+
+def _header_symbols():
+    src = open(capi.os.path.join(capi.HERE, "..", "include", "stokes.h")).read()
+    return sorted(set(re.findall(r"\b(stokes_[a-z_]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol():
+    L = capi.lib()
+    names = _header_symbols()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(L, n), n
+    assert set(names) == set(capi._SIGS)
+
+
+def test_invalid_arguments_are_rejected():
+    wl = synth.workload("box_4x4x2_q2p1")
+    d, keep = mesh_desc(wl, device=-1)
+    d.k = 9
+    with pytest.raises(capi.StokesError) as e:
+        capi.stokes_mesh_create(d)
+    assert e.value.code == -1 and "degree" in str(e.value)
+    d.k = 2
+    d.nx = 0
+    with pytest.raises(capi.StokesError):
+        capi.stokes_mesh_create(d)
+    # host-only meshes refuse compute calls
+    m = Mesh(wl, device=-1)
+    p = capi.stokes_params()
+    with pytest.raises(capi.StokesError) as e:
+        capi.stokes_residual(m.handle, p, None, None, capi.STOKES_F64, 0)
+    assert e.value.code == -1
+
+
+def _periodic_dist(a, b, L):
+    d = a - b
+    return np.abs(d - L * np.round(d / L))
+
+
+MESHES = ["box_4x4x2_q2p1", "slab_8x8x2_q2p1", "slab_5x3x3_q2p1", "forest_4x4x2_q2p1",
+          "cforest_3x3x2_q3p2", "forest_6x6x2_q3p2", "cforest_4x3x2_q4p3", "slab_4x4x2_q4p3",
+          "cbox_3x3x2_q3q1", "slab_6x6x2_q3q1"]
+
+
+@pytest.mark.parametrize("name", MESHES)
+def test_host_mesh_matches_oracle(name):
+    wl = synth.workload(name)
+    m = Mesh(wl, device=-1)
+    o = OracleMesh(wl)
+    assert (m.E, m.Nv, m.Np, m.Nb) == (o.E, o.Nv, o.Np, o.Nb)
+    a, b = m.node_coords(), o.node_coords()
+    scale = max(wl.Lx, wl.Ly)
+    for d, L in ((0, wl.Lx), (1, wl.Ly)):
+        dd = _periodic_dist(a[:, d], b[:, d], L) if wl.periodic else np.abs(a[:, d] - b[:, d])
+        assert dd.max() < 1e-12 * scale
+    assert np.abs(a[:, 2] - b[:, 2]).max() < 1e-10 * max(1.0, np.abs(b[:, 2]).max())
+    np.testing.assert_array_equal(m.basal_nodes(), o.basal)
+    assert (m.n_hanging > 0) == bool(o.fine.any() and (o.hang_cell >= 0).any())
+
+
+def test_general_numbering_equals_lattice_numbering():
+    wl = synth.workload("slab_5x3x3_q2p1")
+    a = Mesh(wl, device=-1)
+    b = Mesh(wl, device=-1, force_general=True)
+    assert a.Nv == b.Nv
+    np.testing.assert_allclose(a.node_coords(), b.node_coords(), rtol=0, atol=1e-9)
+
+
+@pytest.mark.parametrize("name", ["slab_128x128x8_q2p1", "slab_64x64x4_q3q1", "slab_64x64x4_q4p3"])
+def test_full_size_counts(name):
+    wl = synth.workload(name)
+    m = Mesh(wl, device=-1)
+    assert m.Nv == (wl.nx * wl.k) * (wl.ny * wl.k) * (wl.nz * wl.k + 1)
+    assert m.Nb == (wl.nx * wl.k) * (wl.ny * wl.k)
+    assert m.E == wl.n_coarse and m.Np == m.E * m.npr
+
+
+def test_forest_full_size_builds():
+    wl = synth.workload("forest_64x64x4_q3p2")
+    m = Mesh(wl, device=-1)
+    nref = int(wl.refine_mask().sum())
+    assert m.E == wl.n_coarse + 7 * nref
+    assert m.n_hanging > 0 and m.Np == m.E * 10
