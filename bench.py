@@ -1,0 +1,364 @@
+#!/usr/bin/env python
+"""Jacobian-apply throughput of the matrix-free Q_k nonlinear Stokes operator on GB300.
+
+One step = a batch of B Newton-Jacobian applies (the hot path: gather with
+R_i and the basal projector, sum-factorised gradients, pointwise Glen /
+Newton physics, transposed contractions, scatter-add, basal Robin face term,
+constraint rows) on B distinct seeded direction vectors resident in HBM,
+using the linearised per-quadrature-point state in FP32 (the apply run inside
+the Krylov iterations).  value = MDoF/s = (3 Nv + Np) * applies / time,
+summed over ranks (independent replicas: the operator has no data-path
+collective on one mesh per GPU).
+
+--impl reference times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Jacobian-apply MDoF/s & %HBM roofline; time-to-1e-10 residual FP32-inner vs FP64"
+UNIT = "MDoF/s"
+STATE_FIELDS = 17
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="slab_128x128x8_q2p1")
+    ap.add_argument("--batch", type=int, default=16, help="applies per step (distinct inputs)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ clocks
+CLOCK_Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+           "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+           "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+def clocks_start(index):
+    f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+    try:
+        p = subprocess.Popen(["nvidia-smi", f"--query-gpu={CLOCK_Q}", "--format=csv,noheader,nounits",
+                              "-i", str(index), "-lms", "20"], stdout=f, stderr=subprocess.DEVNULL)
+    except FileNotFoundError:
+        p = None
+    return p, f.name
+
+
+def clocks_stop(handle):
+    p, path = handle
+    if p is None:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+    p.terminate()
+    try:
+        p.wait(timeout=5)
+    except subprocess.TimeoutExpired:
+        p.kill()
+    sm, smax, reasons, power = [], [], set(), []
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in open(path):
+        parts = [x.strip() for x in line.split(",")]
+        if len(parts) < 9:
+            continue
+        try:
+            sm.append(float(parts[1])); smax.append(float(parts[2]))
+            power.append(float(parts[3]))
+        except ValueError:
+            continue
+        for nm, v in zip(names, parts[5:9]):
+            if v.lower().startswith("active"):
+                reasons.add(nm)
+    os.unlink(path)
+    return {"sm_mhz": statistics.median(sm) if sm else None,
+            "sm_max_mhz": max(smax) if smax else None,
+            "samples": len(sm),
+            "power_w_max": max(power) if power else None,
+            "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------- CPU oracle
+def oracle_sample(wl, n_side=8):
+    """The same workload restricted to an n_side x n_side column block (same element shapes)."""
+    import dataclasses
+    sx = min(n_side, wl.nx)
+    sy = min(n_side, wl.ny)
+    return dataclasses.replace(wl, name=f"{wl.name}[{sx}x{sy}x{wl.nz} block]", nx=sx, ny=sy,
+                               Lx=wl.Lx * sx / wl.nx, Ly=wl.Ly * sy / wl.ny, periodic=False,
+                               refine_frac=wl.refine_frac)
+
+
+def cpu_oracle_rate(wl, seconds=12.0, n_side=8, reps=None):
+    """Oracle FP64 Jacobian applies on a bounded sample; returns (MDoF/s, sample text, applies)."""
+    import numpy as np
+    import stokes_synth as synth
+    from oracle import OracleMesh, stokes as ostokes
+    sw = oracle_sample(wl, n_side)
+    om = OracleMesh(sw)
+    lb = np.zeros(om.Nb) if sw.phys.logbeta is None else sw.phys.logbeta(*om.basal_coords()[:, :2].T)
+    up = synth.uniform_vector(1, om.ndof)
+    x = synth.uniform_vector(1, om.ndof, stream=1)
+    ostokes.jacobian_apply(om, sw.phys, up, x, lb)   # warm
+    n, t0 = 0, time.perf_counter()
+    while True:
+        ostokes.jacobian_apply(om, sw.phys, up, x, lb)
+        n += 1
+        dt = time.perf_counter() - t0
+        if (reps is not None and n >= reps) or (reps is None and dt >= seconds):
+            break
+    rate = om.ndof * n / dt / 1e6
+    text = (f"{sw.nx}x{sw.ny}x{sw.nz} column block of {wl.name} ({om.E} elements, {om.ndof} dofs), "
+            f"{n} FP64 oracle Jacobian applies in {dt:.1f} s, numpy single thread")
+    return rate, text, n, dt
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import numpy as np
+    import stokes_synth as synth
+    from oracle import OracleMesh, stokes as ostokes
+    wl = synth.workload(args.workload)
+    sw = oracle_sample(wl, 4)
+    om = OracleMesh(sw)
+    lb = np.zeros(om.Nb) if sw.phys.logbeta is None else sw.phys.logbeta(*om.basal_coords()[:, :2].T)
+    up = synth.uniform_vector(1, om.ndof)
+    x = synth.uniform_vector(1, om.ndof, stream=1)
+    for _ in range(args.warmup):
+        ostokes.jacobian_apply(om, sw.phys, up, x, lb)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ostokes.jacobian_apply(om, sw.phys, up, x, lb)
+    dt = time.perf_counter() - t0
+    value = om.ndof * args.steps / dt / 1e6
+    sample = (f"{sw.nx}x{sw.ny}x{sw.nz} column block of {wl.name} ({om.E} elements, {om.ndof} dofs); "
+              f"one FP64 oracle Jacobian apply per step")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded thin periodic ice slab)",
+        "config": {"workload": wl.name, "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+# ------------------------------------------------------------------- ours
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import stokes_synth as synth
+    from paper_1406_6573_gb300 import capi
+    from paper_1406_6573_gb300.mesh import Mesh, State, params
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    wl = synth.workload(args.workload)
+    t_build = time.perf_counter()
+    mesh = Mesh(wl, device=local)
+    t_build = time.perf_counter() - t_build
+    ndof = mesh.ndof
+    q3 = (wl.k + 1) ** 3
+    n3 = (wl.k + 1) ** 3
+    coords = mesh.node_coords()
+    bnodes = mesh.basal_nodes()
+    lb_host = (np.zeros(mesh.Nb) if wl.phys.logbeta is None
+               else wl.phys.logbeta(coords[bnodes, 0], coords[bnodes, 1]))
+    lb = torch.as_tensor(lb_host, dtype=torch.float64, device="cuda")
+    p = params(wl.phys, lb)
+    stream = torch.cuda.current_stream()
+
+    # linearisation point: a seeded smooth-in-scale state (velocity m/a, pressure Pa)
+    up = torch.as_tensor(synth.uniform_vector(rank, ndof), dtype=torch.float64, device="cuda")
+    up[: 3 * mesh.Nv] *= 100.0
+    up[3 * mesh.Nv:] *= 1e5
+    st = State(mesh, capi.STOKES_F32)
+    st.linearize(p, up)
+    B = args.batch
+    gen = torch.Generator(device="cuda").manual_seed(1000 + rank)
+    X = [torch.rand(ndof, dtype=torch.float32, device="cuda", generator=gen) * 2 - 1 for _ in range(B)]
+    Y = [torch.empty(ndof, dtype=torch.float32, device="cuda") for _ in range(B)]
+
+    def step():
+        for b in range(B):
+            st.apply(X[b], Y[b], stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    ck = clocks_start(local)
+    time.sleep(0.1)
+    capi.stokes_profile_begin(mesh.handle)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    prof = capi.stokes_profile_end(mesh.handle)
+    clocks = clocks_stop(ck)
+    barrier()
+    ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    applies = args.steps * B
+    value = world * ndof * applies / (ms / 1e3) / 1e6
+
+    # roofline of the dominant kernel (volume element kernel of the FP32 state apply)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    el_launches, el_ms = prof["element"]
+    el_avg_s = el_ms / max(el_launches, 1) / 1e3
+    bytes_alg = (mesh.E * q3 * STATE_FIELDS * 4 + 2 * ndof * 4 + mesh.E * n3 * 4 + mesh.E * 8)
+    achieved = bytes_alg / el_avg_s / 1e9
+    shares = {k: v[1] for k, v in prof.items()}
+    tot = sum(shares.values())
+
+    # e2e: host buffers, host<->device copies inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        Xh = [x.cpu().pin_memory() for x in X]
+        Yh = [torch.empty(ndof, dtype=torch.float32).pin_memory() for _ in range(B)]
+        Xd = [torch.empty_like(x) for x in X]
+        ke = max(1, min(args.steps, 50))
+        def e2e_step():
+            for b in range(B):
+                Xd[b].copy_(Xh[b], non_blocking=True)
+                st.apply(Xd[b], Y[b], stream)
+                Yh[b].copy_(Y[b], non_blocking=True)
+        e2e_step()
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            e2e_step()
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([dt], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        e2e = {"value": world * ndof * B * ke / dt / 1e6, "unit": UNIT,
+               "h2d_bytes_per_step": B * ndof * 4, "d2h_bytes_per_step": B * ndof * 4,
+               "steps": ke}
+
+    # other operators of the path, timed briefly (device time per call)
+    variants = {}
+    if not args.no_variants and rank == 0:
+        def tm(fn, n=10):
+            fn(); torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True); b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(n):
+                fn()
+            b.record(stream); torch.cuda.synchronize()
+            return a.elapsed_time(b) / n
+        x64 = X[0].double()
+        y64 = torch.empty(ndof, dtype=torch.float64, device="cuda")
+        st64 = State(mesh, capi.STOKES_F64)
+        st64.linearize(p, up)
+        up32 = up.float()
+        g = torch.empty(mesh.Nb, dtype=torch.float64, device="cuda")
+        gA = torch.empty(1, dtype=torch.float64, device="cuda")
+        v = {
+            "state_apply_f64": tm(lambda: st64.apply(x64, y64, stream)),
+            "state_apply_f32": tm(lambda: st.apply(X[0], Y[0], stream)),
+            "jacobian_fused_f64": tm(lambda: capi.stokes_jacobian_apply(mesh.handle, p, up, x64, y64, 0, stream), 3),
+            "jacobian_fused_f32": tm(lambda: capi.stokes_jacobian_apply(mesh.handle, p, up32, X[0], Y[0], 1, stream)),
+            "jacobian_transpose_f32": tm(lambda: capi.stokes_jacobian_apply_transpose(mesh.handle, p, up32, X[0], Y[0], 1, stream)),
+            "residual_f64": tm(lambda: capi.stokes_residual(mesh.handle, p, up, y64, 0, stream), 3),
+            "residual_f32": tm(lambda: capi.stokes_residual(mesh.handle, p, up32, Y[0], 1, stream)),
+            "linearize_f64_to_f32": tm(lambda: st.linearize(p, up, stream), 3),
+            "param_grad_f64": tm(lambda: capi.stokes_param_grad(mesh.handle, p, up, x64, g, gA, stream), 3),
+        }
+        variants = {k: {"ms": round(val, 4), "MDoF/s": round(ndof / (val / 1e3) / 1e6, 1)} for k, val in v.items()}
+        del st64
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, text, n, dt = cpu_oracle_rate(wl, args.cpu_seconds)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": text}
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded thin periodic ice slab, random-Fourier bed and surface)",
+            "config": {
+                "workload": f"{wl.name}: {wl.nx}x{wl.ny}x{wl.nz} hexahedra, Q{wl.k} x "
+                            f"{'P' if wl.pspace == 'P' else 'Q'}{wl.k - 1 if wl.pspace == 'P' else wl.k - 2}"
+                            f"^disc, {ndof} dofs, 100 km x 100 km x 1 km",
+                "apply": "Newton Jacobian from the stored FP32 linearised state (Krylov-inner apply)",
+                "applies_per_step": B,
+                "l2": "inputs larger than L2 (FP32 state %d MB + %d distinct x/y pairs of %d MB)"
+                      % (mesh.E * q3 * STATE_FIELDS * 4 // 2**20, B, ndof * 4 // 2**20),
+                "parallelism": f"replicas{world}",
+                "mesh_build_s": round(t_build, 2),
+            },
+            "clocks": clocks,
+            "gpu_launches": int(prof["element"][0] + prof["face"][0] + prof["constraint"][0]),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": achieved / hbm_peak, "traffic": None,
+                         "kernel": "elem_kernel<float,float,STATE_APPLY>",
+                         "bytes_per_launch": bytes_alg, "avg_launch_ms": el_avg_s * 1e3,
+                         "peak_source": f"{peak_src} hbm_gbs"},
+            "kernel_time_share": {k: round(v / tot, 4) for k, v in shares.items()} if tot > 0 else {},
+            "e2e": e2e,
+            "variants": variants,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -175,6 +175,27 @@ int stokes_state_apply(const stokes_state* state, const void* x, void* y, void* 
 int stokes_state_apply_transpose(const stokes_state* state, const void* x, void* y,
                                  void* stream);
 
+/* Per-kernel timing (tracing).  Between stokes_profile_begin and
+ * stokes_profile_end every operator call on this mesh records a CUDA event
+ * pair around each of its launches, on the caller's stream; end synchronises
+ * on the recorded events and returns launch counts and summed device times
+ * per kernel class.  Recording costs a few microseconds of host time per
+ * launch and no device work. */
+typedef struct {
+    int64_t launches;
+    double ms;
+} stokes_kernel_time;
+
+typedef struct {
+    stokes_kernel_time clear;       /* output zeroing (cudaMemsetAsync)          */
+    stokes_kernel_time element;     /* volume element kernel                     */
+    stokes_kernel_time face;        /* basal Robin face kernel                   */
+    stokes_kernel_time constraint;  /* (I - P) constraint kernel                 */
+} stokes_profile;
+
+int stokes_profile_begin(const stokes_mesh* mesh);
+int stokes_profile_end(const stokes_mesh* mesh, stokes_profile* out);
+
 /* Message describing the calling thread's last error ("" if none). */
 const char* stokes_last_error(void);
 

@@ -53,6 +53,15 @@ class stokes_sizes(C.Structure):
                 ("k", C.c_int32), ("npr", C.c_int32), ("n_hanging_elems", C.c_int64)]
 
 
+class stokes_kernel_time(C.Structure):
+    _fields_ = [("launches", C.c_int64), ("ms", C.c_double)]
+
+
+class stokes_profile(C.Structure):
+    _fields_ = [("clear", stokes_kernel_time), ("element", stokes_kernel_time),
+                ("face", stokes_kernel_time), ("constraint", stokes_kernel_time)]
+
+
 # every symbol declared in include/stokes.h, with its ctypes signature
 _SIGS = {
     "stokes_mesh_create": (C.c_int, [C.POINTER(stokes_mesh_desc), C.POINTER(C.c_void_p)]),
@@ -72,6 +81,8 @@ _SIGS = {
     "stokes_linearize": (C.c_int, [C.c_void_p, C.POINTER(stokes_params), C.c_void_p, C.c_void_p]),
     "stokes_state_apply": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "stokes_state_apply_transpose": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "stokes_profile_begin": (C.c_int, [C.c_void_p]),
+    "stokes_profile_end": (C.c_int, [C.c_void_p, C.POINTER(stokes_profile)]),
     "stokes_last_error": (C.c_char_p, []),
 }
 
@@ -183,3 +194,14 @@ def stokes_state_apply(s, x, y, stream=None):
 
 def stokes_state_apply_transpose(s, x, y, stream=None):
     _check(lib().stokes_state_apply_transpose(s, _ptr(x), _ptr(y), _stream(stream)))
+
+
+def stokes_profile_begin(h):
+    _check(lib().stokes_profile_begin(h))
+
+
+def stokes_profile_end(h):
+    p = stokes_profile()
+    _check(lib().stokes_profile_end(h, C.byref(p)))
+    return {name: (getattr(p, name).launches, getattr(p, name).ms)
+            for name in ("clear", "element", "face", "constraint")}

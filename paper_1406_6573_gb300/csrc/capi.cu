@@ -94,7 +94,26 @@ int upload(T** dst, const std::vector<T>& src) {
 
 }  // namespace
 
+namespace {
+// Event pairs recorded around launches while profiling is active.
+struct Profiler {
+    bool active = false;
+    std::vector<cudaEvent_t> pool;            // reusable events
+    std::vector<std::pair<int, size_t>> recs; // (kernel class, index of the start event)
+    size_t used = 0;
+    cudaEvent_t next() {
+        if (used == pool.size()) {
+            cudaEvent_t ev;
+            if (cudaEventCreate(&ev) != cudaSuccess) return nullptr;
+            pool.push_back(ev);
+        }
+        return pool[used++];
+    }
+};
+}  // namespace
+
 struct stokes_mesh {
+    mutable Profiler prof;
     HostMesh h;
     int device = -1;
     bool on_device = false;
@@ -120,7 +139,23 @@ struct stokes_state {
 
 namespace {
 
+// Run `launch` between two recorded events when profiling (class c).
+template <typename F>
+int timed(const stokes_mesh* m, int c, cudaStream_t s, F&& launch) {
+    if (!m->prof.active) return launch();
+    cudaEvent_t a = m->prof.next(), b = m->prof.next();
+    if (!a || !b) return launch();
+    size_t ia = m->prof.used - 2;
+    cudaEventRecord(a, s);
+    int rc = launch();
+    cudaEventRecord(b, s);
+    m->prof.recs.push_back({c, ia});
+    return rc;
+}
+
 void free_mesh_device(stokes_mesh* m) {
+    for (cudaEvent_t ev : m->prof.pool) cudaEventDestroy(ev);
+    m->prof.pool.clear();
     void* ptrs[] = {m->d_nodes, m->d_hang, m->d_geo, m->d_pidx, m->d_pel, m->d_face_elem,
                     m->d_fgeo, m->d_fmap, m->d_basal_nodes, m->d_basal_P};
     for (void* p : ptrs) if (p) cudaFree(p);
@@ -172,19 +207,21 @@ size_t vec_bytes(const stokes_mesh* m, int prec) {
 // y = (element terms of x) + Robin(x) + (I - P) x ; mode selects the element term.
 int operator_sequence(const stokes_mesh* m, const stokes_params* p, int mode, int prec, int state_prec,
                       bool trans, const void* x, const void* u, const void* cstate, void* y, cudaStream_t s) {
-    cudaError_t ce = cudaMemsetAsync(y, 0, vec_bytes(m, prec), s);
-    if (ce != cudaSuccess) return cuda_fail(ce, "clearing the output");
+    int e = timed(m, 0, s, [&] { return int(cudaMemsetAsync(y, 0, vec_bytes(m, prec), s)); });
+    if (e) return cuda_fail(cudaError_t(e), "clearing the output");
     ElemArgs a = elem_args(m, p);
     a.x = x; a.y = y; a.u = u; a.cstate = cstate;
-    int e = launch_elem(m->h.k, mode, prec, state_prec, trans, a, s);
+    e = timed(m, 1, s, [&] { return launch_elem(m->h.k, mode, prec, state_prec, trans, a, s); });
     if (e) return cuda_fail(cudaError_t(e), "element kernel launch");
     if (p->robin && m->h.nF > 0) {
         FaceArgs f = face_args(m, p);
         f.x = x; f.y = y;
-        e = launch_face(m->h.k, FACE_APPLY, prec, f, s);
+        e = timed(m, 2, s, [&] { return launch_face(m->h.k, FACE_APPLY, prec, f, s); });
         if (e) return cuda_fail(cudaError_t(e), "basal face kernel launch");
     }
-    e = launch_constraint(prec, m->h.Nb, m->d_basal_nodes, m->d_basal_P, x, y, s);
+    e = timed(m, 3, s, [&] {
+        return launch_constraint(prec, m->h.Nb, m->d_basal_nodes, m->d_basal_P, x, y, s);
+    });
     if (e) return cuda_fail(cudaError_t(e), "constraint kernel launch");
     return STOKES_OK;
 }
@@ -234,6 +271,36 @@ int stokes_mesh_create(const stokes_mesh_desc* desc, stokes_mesh** out) {
         std::vector<int32_t>().swap(m->h.elem_nodes);
     }
     *out = m;
+    return STOKES_OK;
+}
+
+int stokes_profile_begin(const stokes_mesh* mesh) {
+    if (!mesh || !mesh->on_device) return fail(STOKES_E_INVAL, "profiling needs a device mesh");
+    mesh->prof.active = true;
+    mesh->prof.recs.clear();
+    mesh->prof.used = 0;
+    return STOKES_OK;
+}
+
+int stokes_profile_end(const stokes_mesh* mesh, stokes_profile* out) {
+    if (!mesh || !out) return fail(STOKES_E_INVAL, "mesh and out must be non-NULL");
+    std::memset(out, 0, sizeof(*out));
+    if (!mesh->prof.active) return fail(STOKES_E_INVAL, "profiling was not started");
+    mesh->prof.active = false;
+    DeviceGuard g(mesh->device);
+    stokes_kernel_time* slot[4] = {&out->clear, &out->element, &out->face, &out->constraint};
+    for (auto& r : mesh->prof.recs) {
+        cudaEvent_t a = mesh->prof.pool[r.second], b = mesh->prof.pool[r.second + 1];
+        cudaError_t ce = cudaEventSynchronize(b);
+        if (ce != cudaSuccess) return cuda_fail(ce, "profiling event");
+        float ms = 0.f;
+        ce = cudaEventElapsedTime(&ms, a, b);
+        if (ce != cudaSuccess) return cuda_fail(ce, "profiling event");
+        slot[r.first]->launches += 1;
+        slot[r.first]->ms += ms;
+    }
+    mesh->prof.recs.clear();
+    mesh->prof.used = 0;
     return STOKES_OK;
 }
 

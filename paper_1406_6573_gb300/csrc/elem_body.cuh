@@ -6,6 +6,7 @@
 
 namespace stokes {
 namespace dev {
+namespace STOKES_NS {
 
 // Load the element's discontinuous pressure dofs into shared memory.
 template <typename T, typename TIN>
@@ -592,6 +593,7 @@ inline int upload_tables_any(const void* p) {
     return int(e);
 }
 
+}  // namespace STOKES_NS
 }  // namespace dev
 }  // namespace stokes
 
@@ -599,10 +601,10 @@ inline int upload_tables_any(const void* p) {
     namespace stokes {                                                                             \
     int launch_elem_k##KK(int mode, int prec, int state_prec, bool trans, const ElemArgs& a,        \
                           cudaStream_t s) {                                                        \
-        return dev::launch_elem_any(mode, prec, state_prec, trans, a, s);                           \
+        return dev::STOKES_NS::launch_elem_any(mode, prec, state_prec, trans, a, s);               \
     }                                                                                              \
     int launch_face_k##KK(int mode, int prec, const FaceArgs& a, cudaStream_t s) {                 \
-        return dev::launch_face_any(mode, prec, a, s);                                             \
+        return dev::STOKES_NS::launch_face_any(mode, prec, a, s);                                 \
     }                                                                                              \
-    int upload_tables_k##KK(const void* t) { return dev::upload_tables_any(t); }                   \
+    int upload_tables_k##KK(const void* t) { return dev::STOKES_NS::upload_tables_any(t); }       \
     }

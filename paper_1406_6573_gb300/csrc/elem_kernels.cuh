@@ -24,8 +24,16 @@
 #error "STOKES_K must be defined before including elem_kernels.cuh"
 #endif
 
+// Every degree lives in its own namespace: the kernels, device helpers and
+// constant tables of different degrees share names and must not be merged
+// across translation units by the linker.
+#define STOKES_NS_CAT(a, b) a##b
+#define STOKES_NS_NAME(k) STOKES_NS_CAT(degree, k)
+#define STOKES_NS STOKES_NS_NAME(STOKES_K)
+
 namespace stokes {
 namespace dev {
+namespace STOKES_NS {
 
 constexpr int K = STOKES_K;
 constexpr int N1 = K + 1;
@@ -398,5 +406,6 @@ __device__ void pressure_rows(const T (&gq)[Q], int npr, int ps, int i, int j, i
     }
 }
 
+}  // namespace STOKES_NS
 }  // namespace dev
 }  // namespace stokes
