@@ -131,6 +131,11 @@ int stokes_mesh_create(const stokes_mesh_desc* desc, stokes_mesh** out);
 int stokes_mesh_destroy(stokes_mesh* mesh);
 int stokes_mesh_sizes(const stokes_mesh* mesh, stokes_sizes* out);
 
+/* Synchronise the mesh's device and report STOKES_E_CUDA if a kernel gave up
+ * on a bounded wait since the last call (the status word is then cleared).
+ * Kernels never spin without a limit; this is how such an event is seen. */
+int stokes_mesh_status(const stokes_mesh* mesh);
+
 /* Host copies of mesh data for verification: physical coordinates of the
  * global nodes [Nv][3] (x, y wrapped into [0, L) on periodic meshes) and the
  * global node index of each basal node [Nb].  Caller-owned host buffers. */

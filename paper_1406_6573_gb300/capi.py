@@ -81,6 +81,7 @@ _SIGS = {
     "stokes_linearize": (C.c_int, [C.c_void_p, C.POINTER(stokes_params), C.c_void_p, C.c_void_p]),
     "stokes_state_apply": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "stokes_state_apply_transpose": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "stokes_mesh_status": (C.c_int, [C.c_void_p]),
     "stokes_profile_begin": (C.c_int, [C.c_void_p]),
     "stokes_profile_end": (C.c_int, [C.c_void_p, C.POINTER(stokes_profile)]),
     "stokes_last_error": (C.c_char_p, []),
@@ -205,3 +206,7 @@ def stokes_profile_end(h):
     _check(lib().stokes_profile_end(h, C.byref(p)))
     return {name: (getattr(p, name).launches, getattr(p, name).ms)
             for name in ("clear", "element", "face", "constraint")}
+
+
+def stokes_mesh_status(h):
+    _check(lib().stokes_mesh_status(h))

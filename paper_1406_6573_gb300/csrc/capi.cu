@@ -72,6 +72,15 @@ int launch_elem(int k, int mode, int prec, int state_prec, bool trans, const Ele
     return int(cudaErrorInvalidValue);
 }
 
+int64_t state_stride(int k) {
+    switch (k) {
+        case 2: return state_stride_k2();
+        case 3: return state_stride_k3();
+        case 4: return state_stride_k4();
+    }
+    return 0;
+}
+
 int launch_face(int k, int mode, int prec, const FaceArgs& a, cudaStream_t s) {
     switch (k) {
         case 2: return launch_face_k2(mode, prec, a, s);
@@ -127,6 +136,7 @@ struct stokes_mesh {
     int32_t* d_fmap = nullptr;
     int32_t* d_basal_nodes = nullptr;
     double* d_basal_P = nullptr;
+    int* d_err = nullptr;          // status word written by kernels (bounded waits)
 };
 
 struct stokes_state {
@@ -157,7 +167,7 @@ void free_mesh_device(stokes_mesh* m) {
     for (cudaEvent_t ev : m->prof.pool) cudaEventDestroy(ev);
     m->prof.pool.clear();
     void* ptrs[] = {m->d_nodes, m->d_hang, m->d_geo, m->d_pidx, m->d_pel, m->d_face_elem,
-                    m->d_fgeo, m->d_fmap, m->d_basal_nodes, m->d_basal_P};
+                    m->d_fgeo, m->d_fmap, m->d_basal_nodes, m->d_basal_P, m->d_err};
     for (void* p : ptrs) if (p) cudaFree(p);
 }
 
@@ -181,6 +191,7 @@ ElemArgs elem_args(const stokes_mesh* m, const stokes_params* p) {
     a.E = m->h.E; a.Nv = m->h.Nv; a.npr = m->h.npr; a.pspace = m->h.pspace;
     a.any_hang = m->h.n_hang > 0;
     a.nodes = m->d_nodes; a.hang = m->d_hang; a.geo = m->d_geo; a.pidx = m->d_pidx; a.pel = m->d_pel;
+    a.err = m->d_err;
     if (p) {
         a.C = p->C0 * std::pow(p->A, -1.0 / p->n);
         a.gamma = p->gamma; a.delta = p->delta;
@@ -264,6 +275,7 @@ int stokes_mesh_create(const stokes_mesh_desc* desc, stokes_mesh** out) {
         if (rc == STOKES_OK) rc = upload(&m->d_fmap, m->h.fmap);
         if (rc == STOKES_OK) rc = upload(&m->d_basal_nodes, m->h.basal_nodes);
         if (rc == STOKES_OK) rc = upload(&m->d_basal_P, m->h.basal_P);
+        if (rc == STOKES_OK) rc = upload(&m->d_err, std::vector<int>(1, 0));
         if (rc != STOKES_OK) { free_mesh_device(m); delete m; return rc; }
         m->on_device = true;
         // the large per-qp arrays live on the device only
@@ -301,6 +313,21 @@ int stokes_profile_end(const stokes_mesh* mesh, stokes_profile* out) {
     }
     mesh->prof.recs.clear();
     mesh->prof.used = 0;
+    return STOKES_OK;
+}
+
+int stokes_mesh_status(const stokes_mesh* mesh) {
+    if (!mesh || !mesh->on_device) return fail(STOKES_E_INVAL, "status needs a device mesh");
+    DeviceGuard g(mesh->device);
+    cudaError_t ce = cudaDeviceSynchronize();
+    if (ce != cudaSuccess) return cuda_fail(ce, "device synchronisation");
+    int flag = 0;
+    ce = cudaMemcpy(&flag, mesh->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (ce != cudaSuccess) return cuda_fail(ce, "reading the status word");
+    if (flag) {
+        cudaMemset(mesh->d_err, 0, sizeof(int));
+        return fail(STOKES_E_CUDA, "a kernel gave up waiting for a staged copy (status word set)");
+    }
     return STOKES_OK;
 }
 
@@ -410,8 +437,7 @@ int stokes_state_create(const stokes_mesh* mesh, int prec, stokes_state** out) {
     st->prec = prec;
     DeviceGuard g(mesh->device);
     if (g.err != cudaSuccess) { delete st; return cuda_fail(g.err, "selecting the device"); }
-    const size_t q3 = size_t(mesh->h.q) * mesh->h.q * mesh->h.q;
-    const size_t bytes = size_t(mesh->h.E) * STATE_FIELDS * q3 * (prec == STOKES_F32 ? 4 : 8);
+    const size_t bytes = size_t(mesh->h.E) * size_t(state_stride(mesh->h.k)) * (prec == STOKES_F32 ? 4 : 8);
     if (cudaMalloc(&st->d_state, bytes) != cudaSuccess) {
         delete st;
         return fail(STOKES_E_NOMEM, "cudaMalloc of the linearised state failed");

@@ -3,18 +3,11 @@
 #pragma once
 
 #include "elem_kernels.cuh"
+#include "tma.cuh"
 
 namespace stokes {
 namespace dev {
 namespace STOKES_NS {
-
-// Load the element's discontinuous pressure dofs into shared memory.
-template <typename T, typename TIN>
-__device__ __forceinline__ void load_pressure(const ElemArgs& a, const TIN* x, int64_t e, bool active,
-                                              int ij, T* pres) {
-    if (active)
-        for (int b = ij; b < a.npr; b += N2) pres[b] = T(ld(x + 3 * a.Nv + e * a.npr + b));
-}
 
 // Physical gradient from the reference gradient at one quadrature point.
 template <typename T>
@@ -38,7 +31,6 @@ __device__ __forceinline__ void ref_stress(T (&G)[3][3][Q], int lq, const T (&Ji
 
 template <typename T>
 __device__ __forceinline__ void load_geo(const ElemArgs& a, int64_t e, int qp, bool active, T (&Ji)[9], T& wdj) {
-    constexpr int Q3 = Q * Q * Q;
     if (active) {
         const double* gp = a.geo + e * 10 * Q3 + qp;
         #pragma unroll
@@ -51,93 +43,57 @@ __device__ __forceinline__ void load_geo(const ElemArgs& a, int64_t e, int qp, b
     }
 }
 
+template <typename T>
+__device__ __forceinline__ void sym6(const T (&g)[3][3], T& E00, T& E11, T& E22, T& E01, T& E02, T& E12) {
+    E00 = g[0][0]; E11 = g[1][1]; E22 = g[2][2];
+    E01 = T(0.5) * (g[0][1] + g[1][0]);
+    E02 = T(0.5) * (g[0][2] + g[2][0]);
+    E12 = T(0.5) * (g[1][2] + g[2][1]);
+}
+
 // ============================================================ volume kernel
-// T: arithmetic type.  S: type of the stored state (linearize / state apply).
+// Generic element kernel (residual, fused Jacobian, linearisation, A-gradient).
+// T: arithmetic type.  S: element type of the stored state (linearize).
 template <typename T, typename S, int MODE, bool TRANS>
 __global__ void __launch_bounds__(THREADS) elem_kernel(ElemArgs a) {
-    constexpr int Q3 = Q * Q * Q;
-    __shared__ T sbuf[EPB + 1][3][N3];
-    __shared__ T spres[EPB + 1][NPRK];
-    __shared__ double sred[THREADS / 32];
-
-    const int tid = threadIdx.x;
-    const int es = tid / N2;
-    const int ij = tid - es * N2;
-    const int i = ij % N1, j = ij / N1;
-    const int64_t e = int64_t(blockIdx.x) * EPB + es;
-    const bool active = (es < EPB) && (e < a.E);
-    T* b0 = sbuf[es][0];
-    T* b1 = sbuf[es][1];
-    T* b2 = sbuf[es][2];
-    T* sb = &sbuf[es][0][0];
+    __shared__ T sbuf[WARPS][EPW + 1][3][N3];
+    const LaneMap L;
+    const int i = L.i, j = L.j, ij = L.ij, es = L.es;
+    const int64_t e = int64_t(blockIdx.x) * EPB + L.warp * EPW + es;
+    const bool active = (es < EPW) && (e < a.E);
+    T* b0 = sbuf[L.warp][es][0];
+    T* b1 = sbuf[L.warp][es][1];
+    T* b2 = sbuf[L.warp][es][2];
+    T* sb = &sbuf[L.warp][es][0][0];
     const uint32_t h = active ? a.hang[e] : 0u;
-    const bool any_h = a.any_hang ? (__syncthreads_or(int(h & ((1u << HANG_CHILD0) - 1))) != 0) : false;
+    const bool any_h = a.any_hang ? (__any_sync(0xffffffffu, (h & ((1u << HANG_CHILD0) - 1)) != 0) != 0) : false;
     const int ps = a.pspace;
+    Rows<T> R;
+    R.load(i, j);
 
     T G[3][3][Q];     // reference gradients, then reference stresses
     T gq[Q];          // pressure-row integrand  -w detJ div(.)
 
-    if constexpr (MODE == MODE_STATE_APPLY) {
+    if constexpr (MODE == MODE_RESIDUAL) {
         T v[3][N1];
         gather_velocity<T, T>(a, static_cast<const T*>(a.x), e, active, ij, v);
         if (any_h) hanging_forward<T, 3>(v, h, active, i, j, sb);
-        load_pressure<T, T>(a, static_cast<const T*>(a.x), e, active, ij, spres[es]);
+        T pc[N1];
+        pressure_fold<T, T>(a, static_cast<const T*>(a.x), e, active, i, j, pc);
         #pragma unroll
-        for (int c = 0; c < 3; ++c) ref_gradient<T>(v[c], G[c][0], G[c][1], G[c][2], i, j, b0, b1);
-        const S* st = static_cast<const S*>(a.cstate) + e * STATE_FIELDS * Q3;
-        #pragma unroll
-        for (int lq = 0; lq < Q; ++lq) {
-            const int qp = sidx(i, j, lq);
-            T f[STATE_FIELDS];
-            #pragma unroll
-            for (int r = 0; r < STATE_FIELDS; ++r) f[r] = active ? T(ld(st + r * Q3 + qp)) : T(0);
-            T Ji[9];
-            #pragma unroll
-            for (int r = 0; r < 9; ++r) Ji[r] = f[r];
-            const T wdj = f[9], muw = f[10];
-            const T D00 = f[11], D11 = f[12], D22 = f[13], D01 = f[14], D02 = f[15], D12 = f[16];
-            T g[3][3];
-            phys_grad(G, lq, Ji, g);
-            const T E00 = g[0][0], E11 = g[1][1], E22 = g[2][2];
-            const T E01 = T(0.5) * (g[0][1] + g[1][0]);
-            const T E02 = T(0.5) * (g[0][2] + g[2][0]);
-            const T E12 = T(0.5) * (g[1][2] + g[2][1]);
-            // Eq. 2.7 is a symmetric map on symmetric tensors: its transpose
-            // (TRANS) is the same contraction D^(D^:E).
-            const T s = D00 * E00 + D11 * E11 + D22 * E22 + T(2) * (D01 * E01 + D02 * E02 + D12 * E12);
-            const T pw = pressure_at<T>(spres[es], a.npr, ps, i, j, lq) * wdj;
-            T tau[3][3];
-            tau[0][0] = muw * E00 - s * D00 - pw;
-            tau[1][1] = muw * E11 - s * D11 - pw;
-            tau[2][2] = muw * E22 - s * D22 - pw;
-            tau[0][1] = tau[1][0] = muw * E01 - s * D01;
-            tau[0][2] = tau[2][0] = muw * E02 - s * D02;
-            tau[1][2] = tau[2][1] = muw * E12 - s * D12;
-            gq[lq] = -wdj * (g[0][0] + g[1][1] + g[2][2]);
-            ref_stress(G, lq, Ji, tau);
-        }
-    } else if constexpr (MODE == MODE_RESIDUAL) {
-        T v[3][N1];
-        gather_velocity<T, T>(a, static_cast<const T*>(a.x), e, active, ij, v);
-        if (any_h) hanging_forward<T, 3>(v, h, active, i, j, sb);
-        load_pressure<T, T>(a, static_cast<const T*>(a.x), e, active, ij, spres[es]);
-        #pragma unroll
-        for (int c = 0; c < 3; ++c) ref_gradient<T>(v[c], G[c][0], G[c][1], G[c][2], i, j, b0, b1);
+        for (int c = 0; c < 3; ++c) ref_gradient<T>(R, v[c], G[c][0], G[c][1], G[c][2], i, j, b0, b1);
         T Sv[3][Q];
         #pragma unroll
         for (int lq = 0; lq < Q; ++lq) {
-            const int qp = sidx(i, j, lq);
             T Ji[9], wdj;
-            load_geo<T>(a, e, qp, active, Ji, wdj);
+            load_geo<T>(a, e, sidx(i, j, lq), active, Ji, wdj);
             T g[3][3];
             phys_grad(G, lq, Ji, g);
-            const T E00 = g[0][0], E11 = g[1][1], E22 = g[2][2];
-            const T E01 = T(0.5) * (g[0][1] + g[1][0]);
-            const T E02 = T(0.5) * (g[0][2] + g[2][0]);
-            const T E12 = T(0.5) * (g[1][2] + g[2][1]);
+            T E00, E11, E22, E01, E02, E12;
+            sym6(g, E00, E11, E22, E01, E02, E12);
             const T DD = E00 * E00 + E11 * E11 + E22 * E22 + T(2) * (E01 * E01 + E02 * E02 + E12 * E12);
             const T muw = viscosity<T>(a, DD) * wdj;
-            const T pw = pressure_at<T>(spres[es], a.npr, ps, i, j, lq) * wdj;
+            const T pw = pressure_at<T>(pc, ps, lq) * wdj;
             T tau[3][3];
             tau[0][0] = muw * E00 - pw;
             tau[1][1] = muw * E11 - pw;
@@ -152,11 +108,10 @@ __global__ void __launch_bounds__(THREADS) elem_kernel(ElemArgs a) {
         }
         T out[3][N1];
         #pragma unroll
-        for (int c = 0; c < 3; ++c) ref_gradient_T<T, true>(G[c][0], G[c][1], G[c][2], Sv[c], out[c], i, j, b0, b1, b2);
+        for (int c = 0; c < 3; ++c) ref_gradient_T<T, true>(R, G[c][0], G[c][1], G[c][2], Sv[c], out[c], i, j, b0, b1, b2);
         pressure_rows<T>(gq, a.npr, ps, i, j, ij, active, sb, static_cast<T*>(a.y) + 3 * a.Nv + e * a.npr);
         if (any_h) hanging_transpose<T, 3>(out, h, active, i, j, sb);
         scatter_velocity<T>(a, static_cast<T*>(a.y), e, active, ij, out);
-        return;
     } else if constexpr (MODE == MODE_APPLY) {
         // linearisation at u, recomputed at every quadrature point
         T lin[8][Q];     // mu w detJ, kappa w detJ, D(u) (6)
@@ -165,18 +120,15 @@ __global__ void __launch_bounds__(THREADS) elem_kernel(ElemArgs a) {
             gather_velocity<T, T>(a, static_cast<const T*>(a.u), e, active, ij, v);
             if (any_h) hanging_forward<T, 3>(v, h, active, i, j, sb);
             #pragma unroll
-            for (int c = 0; c < 3; ++c) ref_gradient<T>(v[c], G[c][0], G[c][1], G[c][2], i, j, b0, b1);
+            for (int c = 0; c < 3; ++c) ref_gradient<T>(R, v[c], G[c][0], G[c][1], G[c][2], i, j, b0, b1);
             #pragma unroll
             for (int lq = 0; lq < Q; ++lq) {
-                const int qp = sidx(i, j, lq);
                 T Ji[9], wdj;
-                load_geo<T>(a, e, qp, active, Ji, wdj);
+                load_geo<T>(a, e, sidx(i, j, lq), active, Ji, wdj);
                 T g[3][3];
                 phys_grad(G, lq, Ji, g);
-                const T E00 = g[0][0], E11 = g[1][1], E22 = g[2][2];
-                const T E01 = T(0.5) * (g[0][1] + g[1][0]);
-                const T E02 = T(0.5) * (g[0][2] + g[2][0]);
-                const T E12 = T(0.5) * (g[1][2] + g[2][1]);
+                T E00, E11, E22, E01, E02, E12;
+                sym6(g, E00, E11, E22, E01, E02, E12);
                 const T DD = E00 * E00 + E11 * E11 + E22 * E22 + T(2) * (E01 * E01 + E02 * E02 + E12 * E12);
                 const T mu = viscosity<T>(a, DD);
                 lin[0][lq] = mu * wdj;
@@ -188,26 +140,25 @@ __global__ void __launch_bounds__(THREADS) elem_kernel(ElemArgs a) {
         T v[3][N1];
         gather_velocity<T, T>(a, static_cast<const T*>(a.x), e, active, ij, v);
         if (any_h) hanging_forward<T, 3>(v, h, active, i, j, sb);
-        load_pressure<T, T>(a, static_cast<const T*>(a.x), e, active, ij, spres[es]);
+        T pc[N1];
+        pressure_fold<T, T>(a, static_cast<const T*>(a.x), e, active, i, j, pc);
         #pragma unroll
-        for (int c = 0; c < 3; ++c) ref_gradient<T>(v[c], G[c][0], G[c][1], G[c][2], i, j, b0, b1);
+        for (int c = 0; c < 3; ++c) ref_gradient<T>(R, v[c], G[c][0], G[c][1], G[c][2], i, j, b0, b1);
         #pragma unroll
         for (int lq = 0; lq < Q; ++lq) {
-            const int qp = sidx(i, j, lq);
             T Ji[9], wdj;
-            load_geo<T>(a, e, qp, active, Ji, wdj);
+            load_geo<T>(a, e, sidx(i, j, lq), active, Ji, wdj);
             T g[3][3];
             phys_grad(G, lq, Ji, g);
-            const T E00 = g[0][0], E11 = g[1][1], E22 = g[2][2];
-            const T E01 = T(0.5) * (g[0][1] + g[1][0]);
-            const T E02 = T(0.5) * (g[0][2] + g[2][0]);
-            const T E12 = T(0.5) * (g[1][2] + g[2][1]);
+            T E00, E11, E22, E01, E02, E12;
+            sym6(g, E00, E11, E22, E01, E02, E12);
             const T muw = lin[0][lq], kw = lin[1][lq];
             const T D00 = lin[2][lq], D11 = lin[3][lq], D22 = lin[4][lq];
             const T D01 = lin[5][lq], D02 = lin[6][lq], D12 = lin[7][lq];
-            // mu' E = mu E + kappa (D:E) D, symmetric (TRANS gives the same map)
+            // mu' E = mu E + kappa (D:E) D is a symmetric map on symmetric
+            // tensors (Eq. 2.7): the transpose (TRANS) is the same contraction.
             const T s = kw * (D00 * E00 + D11 * E11 + D22 * E22 + T(2) * (D01 * E01 + D02 * E02 + D12 * E12));
-            const T pw = pressure_at<T>(spres[es], a.npr, ps, i, j, lq) * wdj;
+            const T pw = pressure_at<T>(pc, ps, lq) * wdj;
             T tau[3][3];
             tau[0][0] = muw * E00 + s * D00 - pw;
             tau[1][1] = muw * E11 + s * D11 - pw;
@@ -218,13 +169,20 @@ __global__ void __launch_bounds__(THREADS) elem_kernel(ElemArgs a) {
             gq[lq] = -wdj * (g[0][0] + g[1][1] + g[2][2]);
             ref_stress(G, lq, Ji, tau);
         }
+        T out[3][N1];
+        T dummy[Q];
+        #pragma unroll
+        for (int c = 0; c < 3; ++c) ref_gradient_T<T, false>(R, G[c][0], G[c][1], G[c][2], dummy, out[c], i, j, b0, b1, b2);
+        pressure_rows<T>(gq, a.npr, ps, i, j, ij, active, sb, static_cast<T*>(a.y) + 3 * a.Nv + e * a.npr);
+        if (any_h) hanging_transpose<T, 3>(out, h, active, i, j, sb);
+        scatter_velocity<T>(a, static_cast<T*>(a.y), e, active, ij, out);
     } else if constexpr (MODE == MODE_LINEARIZE) {
         T v[3][N1];
         gather_velocity<T, double>(a, a.ud, e, active, ij, v);
         if (any_h) hanging_forward<T, 3>(v, h, active, i, j, sb);
         #pragma unroll
-        for (int c = 0; c < 3; ++c) ref_gradient<T>(v[c], G[c][0], G[c][1], G[c][2], i, j, b0, b1);
-        S* st = static_cast<S*>(a.state) + e * STATE_FIELDS * Q3;
+        for (int c = 0; c < 3; ++c) ref_gradient<T>(R, v[c], G[c][0], G[c][1], G[c][2], i, j, b0, b1);
+        S* st = static_cast<S*>(a.state) + e * SSTRIDE;
         #pragma unroll
         for (int lq = 0; lq < Q; ++lq) {
             const int qp = sidx(i, j, lq);
@@ -232,29 +190,29 @@ __global__ void __launch_bounds__(THREADS) elem_kernel(ElemArgs a) {
             load_geo<T>(a, e, qp, active, Ji, wdj);
             T g[3][3];
             phys_grad(G, lq, Ji, g);
-            const T E00 = g[0][0], E11 = g[1][1], E22 = g[2][2];
-            const T E01 = T(0.5) * (g[0][1] + g[1][0]);
-            const T E02 = T(0.5) * (g[0][2] + g[2][0]);
-            const T E12 = T(0.5) * (g[1][2] + g[2][1]);
+            T E00, E11, E22, E01, E02, E12;
+            sym6(g, E00, E11, E22, E01, E02, E12);
             const T DD = E00 * E00 + E11 * E11 + E22 * E22 + T(2) * (E01 * E01 + E02 * E02 + E12 * E12);
             const T mu = viscosity<T>(a, DD);
             // -kappa w detJ >= 0 because p_n = (1-n)/(2n) <= 0
             const T mk = -T(2) * T(a.gamma) * T(a.pexp) * mu * wdj / (T(a.gamma) * DD + T(a.delta));
             const T sq = sqrt(mk > T(0) ? mk : T(0));
             if (active) {
-                #pragma unroll
-                for (int r = 0; r < 9; ++r) st[r * Q3 + qp] = S(Ji[r]);
-                st[9 * Q3 + qp] = S(wdj);
-                st[10 * Q3 + qp] = S(mu * wdj);
-                st[11 * Q3 + qp] = S(sq * E00);
-                st[12 * Q3 + qp] = S(sq * E11);
-                st[13 * Q3 + qp] = S(sq * E22);
-                st[14 * Q3 + qp] = S(sq * E01);
-                st[15 * Q3 + qp] = S(sq * E02);
-                st[16 * Q3 + qp] = S(sq * E12);
+                if (qp == 0) { st[0] = S(Ji[0]); st[1] = S(Ji[4]); }
+                S* q = st + 2 + qp;
+                q[0 * Q3] = S(Ji[6]);
+                q[1 * Q3] = S(Ji[7]);
+                q[2 * Q3] = S(Ji[8]);
+                q[3 * Q3] = S(wdj);
+                q[4 * Q3] = S(mu * wdj);
+                q[5 * Q3] = S(sq * E00);
+                q[6 * Q3] = S(sq * E11);
+                q[7 * Q3] = S(sq * E22);
+                q[8 * Q3] = S(sq * E01);
+                q[9 * Q3] = S(sq * E02);
+                q[10 * Q3] = S(sq * E12);
             }
         }
-        return;
     } else if constexpr (MODE == MODE_GRAD_A) {
         T acc = 0;
         T Gl[3][3][Q];
@@ -263,18 +221,17 @@ __global__ void __launch_bounds__(THREADS) elem_kernel(ElemArgs a) {
             gather_velocity<T, double>(a, a.lam, e, active, ij, v);
             if (any_h) hanging_forward<T, 3>(v, h, active, i, j, sb);
             #pragma unroll
-            for (int c = 0; c < 3; ++c) ref_gradient<T>(v[c], Gl[c][0], Gl[c][1], Gl[c][2], i, j, b0, b1);
+            for (int c = 0; c < 3; ++c) ref_gradient<T>(R, v[c], Gl[c][0], Gl[c][1], Gl[c][2], i, j, b0, b1);
         }
         T v[3][N1];
         gather_velocity<T, double>(a, a.ud, e, active, ij, v);
         if (any_h) hanging_forward<T, 3>(v, h, active, i, j, sb);
         #pragma unroll
-        for (int c = 0; c < 3; ++c) ref_gradient<T>(v[c], G[c][0], G[c][1], G[c][2], i, j, b0, b1);
+        for (int c = 0; c < 3; ++c) ref_gradient<T>(R, v[c], G[c][0], G[c][1], G[c][2], i, j, b0, b1);
         #pragma unroll
         for (int lq = 0; lq < Q; ++lq) {
-            const int qp = sidx(i, j, lq);
             T Ji[9], wdj;
-            load_geo<T>(a, e, qp, active, Ji, wdj);
+            load_geo<T>(a, e, sidx(i, j, lq), active, Ji, wdj);
             T g[3][3], gl[3][3];
             phys_grad(G, lq, Ji, g);
             phys_grad(Gl, lq, Ji, gl);
@@ -290,38 +247,155 @@ __global__ void __launch_bounds__(THREADS) elem_kernel(ElemArgs a) {
                 }
             if (active) acc += viscosity<T>(a, DD) * wdj * DL;
         }
-        // block reduction, one atomic per block
         double r = double(acc);
         #pragma unroll
         for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o);
-        if ((tid & 31) == 0) sred[tid >> 5] = r;
-        __syncthreads();
-        if (tid == 0) {
-            double s = 0;
-            for (int w = 0; w < THREADS / 32; ++w) s += sred[w];
-            atomicAdd(a.gA, s * a.gA_scale);
-        }
-        return;
+        if (L.lane == 0) atomicAdd(a.gA, r * a.gA_scale);
     }
+}
 
-    // ---- common back end of the two Jacobian modes: integrate and scatter
-    if constexpr (MODE == MODE_STATE_APPLY || MODE == MODE_APPLY) {
+// ================================================== state apply (hot path)
+// y = J x from the stored linearised state.  Persistent: each warp walks its
+// element groups (EPW consecutive elements); the state block of the next
+// group (contiguous, 16-byte multiple) is staged into shared memory by a bulk
+// asynchronous copy (TMA, cp.async.bulk) completing on a per-warp mbarrier,
+// double-buffered, so the state stream overlaps the gather and the forward
+// contractions of the current group.
+template <typename T>
+struct StateApplyCfg {
+    static constexpr int W = sizeof(T) == 8 ? 4 : 8;        // warps per block
+    static constexpr int BUF = EPW * SSTRIDE;                // values per stage buffer
+    static constexpr int SCR = (EPW + 1) * 3 * N3;           // scratch per warp
+    static constexpr int PER_WARP = ((2 * BUF + SCR) * int(sizeof(T)) + 127) / 128 * 128;
+    static constexpr int SMEM = W * PER_WARP + W * 2 * 8;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(32 * StateApplyCfg<T>::W) state_apply_kernel(ElemArgs a) {
+    using C = StateApplyCfg<T>;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const LaneMap L;
+    const int i = L.i, j = L.j, ij = L.ij, es = L.es, lane = L.lane;
+    unsigned char* wbase = smem_raw + L.warp * C::PER_WARP;
+    T* stage[2] = {reinterpret_cast<T*>(wbase), reinterpret_cast<T*>(wbase) + C::BUF};
+    T* scratch = reinterpret_cast<T*>(wbase) + 2 * C::BUF;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + C::W * C::PER_WARP) + 2 * L.warp;
+    T* sb = scratch + es * 3 * N3;
+    T* b0 = sb;
+    T* b1 = sb + N3;
+    T* b2 = sb + 2 * N3;
+    const int ps = a.pspace;
+    const T* S = static_cast<const T*>(a.cstate);
+    const T* x = static_cast<const T*>(a.x);
+    T* y = static_cast<T*>(a.y);
+    Rows<T> R;
+    R.load(i, j);
+
+    const int64_t ngroups = (a.E + EPW - 1) / EPW;
+    const int64_t gstride = int64_t(gridDim.x) * C::W;
+    int64_t g = int64_t(blockIdx.x) * C::W + L.warp;
+
+    auto group_bytes = [&](int64_t gg) -> uint32_t {
+        const int64_t ne = (a.E - gg * EPW) < EPW ? (a.E - gg * EPW) : EPW;
+        return uint32_t(ne * SSTRIDE * int64_t(sizeof(T)));
+    };
+    if (lane == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+    if (g < ngroups && lane == 0) {
+        const uint32_t nb = group_bytes(g);
+        mbar_arrive_expect_tx(&bar[0], nb);
+        bulk_g2s(stage[0], S + g * EPW * SSTRIDE, nb, &bar[0]);
+    }
+    for (int it = 0; g < ngroups; g += gstride, ++it) {
+        const int buf = it & 1;
+        // prefetch the next group into the other buffer (its readers finished
+        // at the end of the previous iteration)
+        if (lane == 0 && g + gstride < ngroups) {
+            const uint32_t nb = group_bytes(g + gstride);
+            fence_proxy_async();
+            mbar_arrive_expect_tx(&bar[buf ^ 1], nb);
+            bulk_g2s(stage[buf ^ 1], S + (g + gstride) * EPW * SSTRIDE, nb, &bar[buf ^ 1]);
+        }
+        const int64_t e = g * EPW + es;
+        const bool active = (es < EPW) && (e < a.E);
+        const uint32_t h = active ? a.hang[e] : 0u;
+        const bool any_h = a.any_hang ? (__any_sync(0xffffffffu, (h & ((1u << HANG_CHILD0) - 1)) != 0) != 0) : false;
+
+        T v[3][N1];
+        gather_velocity<T, T>(a, x, e, active, ij, v);
+        if (any_h) hanging_forward<T, 3>(v, h, active, i, j, sb);
+        T pc[N1];
+        pressure_fold<T, T>(a, x, e, active, i, j, pc);
+        T G[3][3][Q];
+        #pragma unroll
+        for (int c = 0; c < 3; ++c) ref_gradient<T>(R, v[c], G[c][0], G[c][1], G[c][2], i, j, b0, b1);
+
+        if (!mbar_wait_bounded(&bar[buf], uint32_t((it >> 1) & 1))) {
+            // the staged state never arrived: report, let the copy drain, stop
+            if (lane == 0) atomicOr(a.err, 1);
+            mbar_wait_bounded(&bar[buf], uint32_t((it >> 1) & 1));
+            return;
+        }
+        const T* st = stage[buf] + (es < EPW ? es : 0) * SSTRIDE;
+        const T ia = st[0], ib = st[1];
+        T gq[Q];
+        #pragma unroll
+        for (int lq = 0; lq < Q; ++lq) {
+            const T* f = st + 2 + sidx(i, j, lq);
+            const T g0 = f[0], g1 = f[Q3], g2 = f[2 * Q3];
+            const T wdj = f[3 * Q3], muw = f[4 * Q3];
+            const T D00 = f[5 * Q3], D11 = f[6 * Q3], D22 = f[7 * Q3];
+            const T D01 = f[8 * Q3], D02 = f[9 * Q3], D12 = f[10 * Q3];
+            // physical gradient: Jinv = [[ia,0,0],[0,ib,0],[g0,g1,g2]]
+            T gr[3][3];
+            #pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const T gz = G[c][2][lq];
+                gr[c][0] = G[c][0][lq] * ia + gz * g0;
+                gr[c][1] = G[c][1][lq] * ib + gz * g1;
+                gr[c][2] = gz * g2;
+            }
+            T E00, E11, E22, E01, E02, E12;
+            sym6(gr, E00, E11, E22, E01, E02, E12);
+            // Eq. 2.7 as a symmetric map: w detJ mu' E = muw E - (Dhat:E) Dhat
+            const T s = D00 * E00 + D11 * E11 + D22 * E22 + T(2) * (D01 * E01 + D02 * E02 + D12 * E12);
+            const T pw = active ? pressure_at<T>(pc, ps, lq) * wdj : T(0);
+            T tau[3][3];
+            tau[0][0] = muw * E00 - s * D00 - pw;
+            tau[1][1] = muw * E11 - s * D11 - pw;
+            tau[2][2] = muw * E22 - s * D22 - pw;
+            tau[0][1] = tau[1][0] = muw * E01 - s * D01;
+            tau[0][2] = tau[2][0] = muw * E02 - s * D02;
+            tau[1][2] = tau[2][1] = muw * E12 - s * D12;
+            gq[lq] = -wdj * (gr[0][0] + gr[1][1] + gr[2][2]);
+            // reference stress S[c][m] = sum_d Jinv[m][d] tau[c][d]
+            #pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                G[c][0][lq] = ia * tau[c][0];
+                G[c][1][lq] = ib * tau[c][1];
+                G[c][2][lq] = g0 * tau[c][0] + g1 * tau[c][1] + g2 * tau[c][2];
+            }
+        }
+        __syncwarp();
         T out[3][N1];
         T dummy[Q];
         #pragma unroll
-        for (int c = 0; c < 3; ++c) ref_gradient_T<T, false>(G[c][0], G[c][1], G[c][2], dummy, out[c], i, j, b0, b1, b2);
-        pressure_rows<T>(gq, a.npr, ps, i, j, ij, active, sb, static_cast<T*>(a.y) + 3 * a.Nv + e * a.npr);
+        for (int c = 0; c < 3; ++c) ref_gradient_T<T, false>(R, G[c][0], G[c][1], G[c][2], dummy, out[c], i, j, b0, b1, b2);
+        pressure_rows<T>(gq, a.npr, ps, i, j, ij, active, sb, y + 3 * a.Nv + e * a.npr);
         if (any_h) hanging_transpose<T, 3>(out, h, active, i, j, sb);
-        scatter_velocity<T>(a, static_cast<T*>(a.y), e, active, ij, out);
+        scatter_velocity<T>(a, y, e, active, ij, out);
+        __syncwarp();
     }
 }
 
 // ============================================================ basal faces
 // Robin term int_{Gamma_b} beta T v . T w ds (Eq. 2.4a in weak form, Eq. 2.5)
-// and its log(beta) adjoint product.  One thread per bottom-plane node
-// (i, j) of a basal element; 2-D sum factorisation through shared memory.
-constexpr int FPB = THREADS / N2;   // faces per block
-
+// and its log(beta) adjoint product.  One lane per bottom-plane node (i, j) of
+// a basal element; 2-D sum factorisation through warp-local shared memory.
 template <typename T>
 __device__ __forceinline__ void face_gather(const FaceArgs& a, const T* x, int64_t e, bool active, int ij,
                                             T (&v)[3]) {
@@ -329,15 +403,7 @@ __device__ __forceinline__ void face_gather(const FaceArgs& a, const T* x, int64
         const int64_t g = a.nodes[e * N3 + ij];
         v[0] = T(ld(x + 3 * g)); v[1] = T(ld(x + 3 * g + 1)); v[2] = T(ld(x + 3 * g + 2));
         const int pi = a.pidx[e];
-        if (pi >= 0) {
-            const double* P = a.pel + int64_t(pi) * 6 * N2 + ij;
-            const T p00 = T(P[0]), p11 = T(P[N2]), p22 = T(P[2 * N2]);
-            const T p01 = T(P[3 * N2]), p02 = T(P[4 * N2]), p12 = T(P[5 * N2]);
-            const T x0 = v[0], x1 = v[1], x2 = v[2];
-            v[0] = p00 * x0 + p01 * x1 + p02 * x2;
-            v[1] = p01 * x0 + p11 * x1 + p12 * x2;
-            v[2] = p02 * x0 + p12 * x1 + p22 * x2;
-        }
+        if (pi >= 0) project3<T>(a.pel + int64_t(pi) * 6 * N2 + ij, v[0], v[1], v[2]);
     } else {
         v[0] = v[1] = v[2] = T(0);
     }
@@ -352,7 +418,7 @@ __device__ void face_hanging(T (&v)[NC], uint32_t h, bool active, int i, int j, 
         const int axis = TRANSPOSE ? 1 - pass : pass;   // forward: x then y
         #pragma unroll
         for (int c = 0; c < NC; ++c) sb[c * N2 + i + N1 * j] = v[c];
-        __syncthreads();
+        wsync();
         if (active && h) {
             const int bb = child_bit(h, axis);
             const bool on = (axis == 0) ? line_hanging(h, 0, j, 0, K) : line_hanging(h, 1, i, 0, K);
@@ -370,87 +436,87 @@ __device__ void face_hanging(T (&v)[NC], uint32_t h, bool active, int i, int j, 
                 }
             }
         }
-        __syncthreads();
+        wsync();
     }
 }
 
 // values at the face Gauss points (iq = i, jq = j) from bottom-plane nodal values
 template <typename T, int NC>
-__device__ __forceinline__ void face_interp(const T (&v)[NC], T (&o)[NC], int i, int j, T* sb) {
+__device__ __forceinline__ void face_interp(const Rows<T>& R, const T (&v)[NC], T (&o)[NC], int i, int j, T* sb) {
     #pragma unroll
     for (int c = 0; c < NC; ++c) sb[c * N2 + i + N1 * j] = v[c];
-    __syncthreads();
+    wsync();
     T t[NC];
     #pragma unroll
     for (int c = 0; c < NC; ++c) {
         T s = 0;
         #pragma unroll
-        for (int m = 0; m < N1; ++m) s += Tab<T>::B(i, m) * sb[c * N2 + m + N1 * j];
+        for (int m = 0; m < N1; ++m) s += R.Bi[m] * sb[c * N2 + m + N1 * j];
         t[c] = s;
     }
-    __syncthreads();
+    wsync();
     #pragma unroll
     for (int c = 0; c < NC; ++c) sb[c * N2 + i + N1 * j] = t[c];
-    __syncthreads();
+    wsync();
     #pragma unroll
     for (int c = 0; c < NC; ++c) {
         T s = 0;
         #pragma unroll
-        for (int m = 0; m < N1; ++m) s += Tab<T>::B(j, m) * sb[c * N2 + i + N1 * m];
+        for (int m = 0; m < N1; ++m) s += R.Bj[m] * sb[c * N2 + i + N1 * m];
         o[c] = s;
     }
-    __syncthreads();
+    wsync();
 }
 
 // transposed interpolation: nodal values from values at face Gauss points
 template <typename T, int NC>
-__device__ __forceinline__ void face_interp_T(const T (&v)[NC], T (&o)[NC], int i, int j, T* sb) {
+__device__ __forceinline__ void face_interp_T(const Rows<T>& R, const T (&v)[NC], T (&o)[NC], int i, int j, T* sb) {
     #pragma unroll
     for (int c = 0; c < NC; ++c) sb[c * N2 + i + N1 * j] = v[c];
-    __syncthreads();
+    wsync();
     T t[NC];
     #pragma unroll
     for (int c = 0; c < NC; ++c) {
         T s = 0;
         #pragma unroll
-        for (int m = 0; m < Q; ++m) s += Tab<T>::B(m, i) * sb[c * N2 + m + N1 * j];
+        for (int m = 0; m < Q; ++m) s += R.BTi[m] * sb[c * N2 + m + N1 * j];
         t[c] = s;
     }
-    __syncthreads();
+    wsync();
     #pragma unroll
     for (int c = 0; c < NC; ++c) sb[c * N2 + i + N1 * j] = t[c];
-    __syncthreads();
+    wsync();
     #pragma unroll
     for (int c = 0; c < NC; ++c) {
         T s = 0;
         #pragma unroll
-        for (int m = 0; m < Q; ++m) s += Tab<T>::B(m, j) * sb[c * N2 + i + N1 * m];
+        for (int m = 0; m < Q; ++m) s += R.BTj[m] * sb[c * N2 + i + N1 * m];
         o[c] = s;
     }
-    __syncthreads();
+    wsync();
 }
 
 template <typename T, int MODE>
 __global__ void __launch_bounds__(THREADS) face_kernel(FaceArgs a) {
     constexpr int Q2 = Q * Q;
-    __shared__ T sbuf[FPB + 1][4 * N2];
-    const int tid = threadIdx.x;
-    const int fs = tid / N2;
-    const int ij = tid - fs * N2;
-    const int i = ij % N1, j = ij / N1;
-    const int64_t f = int64_t(blockIdx.x) * FPB + fs;
-    const bool active = (fs < FPB) && (f < a.nF);
-    T* sb = sbuf[fs];
+    __shared__ T sbuf[WARPS][EPW + 1][4 * N2];
+    const LaneMap L;
+    const int i = L.i, j = L.j, ij = L.ij, fs = L.es;
+    const int64_t f = int64_t(blockIdx.x) * EPB + L.warp * EPW + fs;
+    const bool active = (fs < EPW) && (f < a.nF);
+    T* sb = sbuf[L.warp][fs];
     const int64_t e = active ? a.face_elem[f] : 0;
     const uint32_t h = active ? a.hang[e] : 0u;
-    const bool any_h = __syncthreads_or(int(h & ((1u << HANG_CHILD0) - 1))) != 0;
+    const bool any_h = __any_sync(0xffffffffu, (h & ((1u << HANG_CHILD0) - 1)) != 0) != 0;
+    Rows<T> R;
+    R.load(i, j);
 
     // log(beta) at the face nodes (hanging-interpolated), then at Gauss points
     T lb[1];
     lb[0] = active ? T(a.logbeta[a.fmap[f * N2 + ij]]) : T(0);
     if (any_h) face_hanging<T, 1, false>(lb, h, active, i, j, sb);
     T lbq[1];
-    face_interp<T, 1>(lb, lbq, i, j, sb);
+    face_interp<T, 1>(R, lb, lbq, i, j, sb);
     const int fq = i + Q * j;
     T wa = 0, n0 = 0, n1 = 0, n2 = 0;
     if (active) {
@@ -464,23 +530,15 @@ __global__ void __launch_bounds__(THREADS) face_kernel(FaceArgs a) {
         face_gather<T>(a, static_cast<const T*>(a.x), e, active, ij, v);
         if (any_h) face_hanging<T, 3, false>(v, h, active, i, j, sb);
         T vq[3];
-        face_interp<T, 3>(v, vq, i, j, sb);
+        face_interp<T, 3>(R, v, vq, i, j, sb);
         const T nv = n0 * vq[0] + n1 * vq[1] + n2 * vq[2];
         T t[3] = {bw * (vq[0] - nv * n0), bw * (vq[1] - nv * n1), bw * (vq[2] - nv * n2)};
         T o[3];
-        face_interp_T<T, 3>(t, o, i, j, sb);
+        face_interp_T<T, 3>(R, t, o, i, j, sb);
         if (any_h) face_hanging<T, 3, true>(o, h, active, i, j, sb);
         if (active) {
             const int pi = a.pidx[e];
-            if (pi >= 0) {
-                const double* P = a.pel + int64_t(pi) * 6 * N2 + ij;
-                const T p00 = T(P[0]), p11 = T(P[N2]), p22 = T(P[2 * N2]);
-                const T p01 = T(P[3 * N2]), p02 = T(P[4 * N2]), p12 = T(P[5 * N2]);
-                const T x0 = o[0], x1 = o[1], x2 = o[2];
-                o[0] = p00 * x0 + p01 * x1 + p02 * x2;
-                o[1] = p01 * x0 + p11 * x1 + p12 * x2;
-                o[2] = p02 * x0 + p12 * x1 + p22 * x2;
-            }
+            if (pi >= 0) project3<T>(a.pel + int64_t(pi) * 6 * N2 + ij, o[0], o[1], o[2]);
             const int64_t g = a.nodes[e * N3 + ij];
             T* y = static_cast<T*>(a.y);
             atomic_add(y + 3 * g, o[0]);
@@ -497,14 +555,14 @@ __global__ void __launch_bounds__(THREADS) face_kernel(FaceArgs a) {
             face_hanging<T, 3, false>(w, h, active, i, j, sb);
         }
         T vq[3], wq[3];
-        face_interp<T, 3>(v, vq, i, j, sb);
-        face_interp<T, 3>(w, wq, i, j, sb);
+        face_interp<T, 3>(R, v, vq, i, j, sb);
+        face_interp<T, 3>(R, w, wq, i, j, sb);
         const T nu = n0 * vq[0] + n1 * vq[1] + n2 * vq[2];
         const T nl = n0 * wq[0] + n1 * wq[1] + n2 * wq[2];
         const T s = bw * ((vq[0] - nu * n0) * (wq[0] - nl * n0) + (vq[1] - nu * n1) * (wq[1] - nl * n1) +
                           (vq[2] - nu * n2) * (wq[2] - nl * n2));
         T sv[1] = {s}, o[1];
-        face_interp_T<T, 1>(sv, o, i, j, sb);
+        face_interp_T<T, 1>(R, sv, o, i, j, sb);
         if (any_h) face_hanging<T, 1, true>(o, h, active, i, j, sb);
         if (active) atomic_add(a.g + a.fmap[f * N2 + ij], double(o[0]));
     }
@@ -519,9 +577,35 @@ int launch_elem_t(const ElemArgs& a, cudaStream_t s) {
     return int(cudaGetLastError());
 }
 
+template <typename T>
+int launch_state_apply_t(const ElemArgs& a, cudaStream_t s) {
+    using C = StateApplyCfg<T>;
+    if (a.E == 0) return int(cudaSuccess);
+    static int configured_device = -1;
+    static int max_blocks = 0;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (configured_device != dev) {
+        cudaError_t e = cudaFuncSetAttribute(state_apply_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+        if (e != cudaSuccess) return int(e);
+        int per_sm = 0, sms = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, state_apply_kernel<T>, 32 * C::W, C::SMEM);
+        if (e != cudaSuccess) return int(e);
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return int(e);
+        max_blocks = (per_sm > 0 ? per_sm : 1) * sms;
+        configured_device = dev;
+    }
+    const int64_t ngroups = (a.E + EPW - 1) / EPW;
+    int64_t blocks = (ngroups + C::W - 1) / C::W;
+    if (blocks > max_blocks) blocks = max_blocks;
+    state_apply_kernel<T><<<unsigned(blocks), 32 * C::W, C::SMEM, s>>>(a);
+    return int(cudaGetLastError());
+}
+
 template <typename T, int MODE>
 int launch_face_t(const FaceArgs& a, cudaStream_t s) {
-    const int64_t blocks = (a.nF + FPB - 1) / FPB;
+    const int64_t blocks = (a.nF + EPB - 1) / EPB;
     if (blocks == 0) return int(cudaSuccess);
     face_kernel<T, MODE><<<unsigned(blocks), THREADS, 0, s>>>(a);
     return int(cudaGetLastError());
@@ -542,10 +626,9 @@ inline int launch_elem_any(int mode, int prec, int state_prec, bool trans, const
             return state_prec == 1 ? launch_elem_t<double, float, MODE_LINEARIZE, false>(a, s)
                                    : launch_elem_t<double, double, MODE_LINEARIZE, false>(a, s);
         case MODE_STATE_APPLY:
-            if (trans) return f32 ? launch_elem_t<float, float, MODE_STATE_APPLY, true>(a, s)
-                                  : launch_elem_t<double, double, MODE_STATE_APPLY, true>(a, s);
-            return f32 ? launch_elem_t<float, float, MODE_STATE_APPLY, false>(a, s)
-                       : launch_elem_t<double, double, MODE_STATE_APPLY, false>(a, s);
+            // the pointwise map of Eq. 2.7 is symmetric: the transposed apply
+            // runs the same kernel
+            return f32 ? launch_state_apply_t<float>(a, s) : launch_state_apply_t<double>(a, s);
         case MODE_GRAD_A:
             return launch_elem_t<double, double, MODE_GRAD_A, false>(a, s);
         default:
@@ -607,4 +690,5 @@ inline int upload_tables_any(const void* p) {
         return dev::STOKES_NS::launch_face_any(mode, prec, a, s);                                 \
     }                                                                                              \
     int upload_tables_k##KK(const void* t) { return dev::STOKES_NS::upload_tables_any(t); }       \
+    int64_t state_stride_k##KK() { return dev::STOKES_NS::SSTRIDE; }                             \
     }

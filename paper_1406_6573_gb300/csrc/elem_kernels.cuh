@@ -1,10 +1,14 @@
-// Sum-factorised element kernels of the nonlinear Stokes operator (sm_103a).
+// Sum-factorised element kernels of the nonlinear Stokes operator (sm_103a):
+// shared layout, tables and device helpers.
 //
 // One thread owns one (i, j) column of GLL nodes / Gauss points of an element
 // and loops over the third index l: contractions along zeta run in registers,
-// contractions along xi and eta go through shared memory (Section 3.3: every
-// element operation is a sequence of 1-D kernels).  A block holds EPB
-// elements.  Per element:
+// contractions along xi and eta exchange through shared memory (Section 3.3:
+// every element operation is a sequence of 1-D kernels).  The N1^2 threads of
+// an element always sit in one warp (EPW = 32 / N1^2 elements per warp), so
+// every exchange is warp-synchronous: there is no block-wide barrier in the
+// element loop and each warp streams through its own element groups.
+// Per element:
 //   gather (R_i: global node per slot, basal projector P, hanging-node 1-D
 //   interpolation) -> reference gradients at the Gauss points (3 interpolation
 //   sweeps + 3 collocated derivative sweeps per field) -> pointwise physics
@@ -40,10 +44,17 @@ constexpr int N1 = K + 1;
 constexpr int Q = N1;
 constexpr int N2 = N1 * N1;
 constexpr int N3 = N1 * N1 * N1;
-constexpr int THREADS = 256;
-constexpr int EPB = THREADS / N2;     // elements per block
+constexpr int Q3 = N3;
+constexpr int WARPS = 8;
+constexpr int THREADS = 32 * WARPS;
+constexpr int EPW = 32 / N2;          // elements per warp
+constexpr int EPB = WARPS * EPW;      // elements per block
+static_assert(EPW >= 1, "an element's columns must fit in one warp");
 constexpr int NPRK = (K - 1) * (K - 1) * (K - 1) > K * (K + 1) * (K + 2) / 6
                          ? (K - 1) * (K - 1) * (K - 1) : K * (K + 1) * (K + 2) / 6;
+// per-element stride of the linearised state: 2 element constants then
+// STATE_FIELDS values per quadrature point, padded to a 16-byte multiple
+constexpr int SSTRIDE = ((2 + STATE_FIELDS * Q3) + 3) / 4 * 4;
 
 // ---------------------------------------------------------------- tables
 __constant__ double cB[Q][N1];        // GLL Lagrange at Gauss points
@@ -71,11 +82,32 @@ template <> struct Tab<float> {
     static __device__ __forceinline__ float P1(int s, int a, int b) { return fP1[s][a][b]; }
 };
 
+// Table entries whose index depends on the thread's (i, j): loaded once into
+// registers (constant-cache reads with divergent addresses would serialise).
+template <typename T> struct Rows {
+    T Bi[N1], Bj[N1];      // B[i][m], B[j][m]
+    T BTi[Q], BTj[Q];      // B[m][i], B[m][j]
+    T Di[Q], Dj[Q];        // Dg[i][m], Dg[j][m]
+    T DTi[Q], DTj[Q];      // Dg[m][i], Dg[m][j]
+    __device__ __forceinline__ void load(int i, int j) {
+        #pragma unroll
+        for (int m = 0; m < N1; ++m) { Bi[m] = Tab<T>::B(i, m); Bj[m] = Tab<T>::B(j, m); }
+        #pragma unroll
+        for (int m = 0; m < Q; ++m) {
+            BTi[m] = Tab<T>::B(m, i); BTj[m] = Tab<T>::B(m, j);
+            Di[m] = Tab<T>::Dg(i, m); Dj[m] = Tab<T>::Dg(j, m);
+            DTi[m] = Tab<T>::Dg(m, i); DTj[m] = Tab<T>::Dg(m, j);
+        }
+    }
+};
+
 // --------------------------------------------------------------- helpers
 template <typename T> __device__ __forceinline__ T ld(const T* p) { return __ldg(p); }
 
 __device__ __forceinline__ void atomic_add(double* p, double v) { atomicAdd(p, v); }
 __device__ __forceinline__ void atomic_add(float* p, float v) { atomicAdd(p, v); }
+
+__device__ __forceinline__ void wsync() { __syncwarp(); }
 
 // Viscosity mu = C (gamma s + delta)^p_n, s = D:D; special-cased for n = 3.
 template <typename T>
@@ -85,10 +117,18 @@ __device__ __forceinline__ T viscosity(const ElemArgs& a, T DD) {
     return T(a.C) * pow(arg, T(a.pexp));
 }
 
-// Per-element shared memory.
-template <typename T> struct Smem {
-    T buf[EPB][3][N3];
-    T pres[EPB][NPRK > 0 ? NPRK : 1];
+// Lane layout of a warp: EPW element slots of N2 lanes; idle lanes form slot EPW.
+struct LaneMap {
+    int warp, lane, es, ij, i, j;
+    __device__ __forceinline__ LaneMap() {
+        warp = threadIdx.x >> 5;
+        lane = threadIdx.x & 31;
+        es = lane / N2;
+        if (es > EPW) es = EPW;
+        ij = lane - es * N2;
+        i = ij % N1;
+        j = ij / N1;
+    }
 };
 
 // slot / qp index within the element tensor: (i, j, l) -> i + N1 (j + N1 l)
@@ -96,14 +136,14 @@ __device__ __forceinline__ int sidx(int i, int j, int l) { return i + N1 * (j + 
 
 // ----------------------------------------------------- hanging sweeps
 // Forward R_i interpolation on the element tensor held as columns v[c][l]
-// (thread (i, j)).  All threads of the block call it (it synchronises).
+// (thread (i, j)); sb is the element's shared scratch (N3 values).
 template <typename T, int NC>
 __device__ void hanging_forward(T (&v)[NC][N1], uint32_t h, bool active, int i, int j, T* sb) {
-    // x-sweeps: lines parallel to x at (j, l)
     for (int c = 0; c < NC; ++c) {
+        // x-sweeps: lines parallel to x at (j, l)
         #pragma unroll
         for (int l = 0; l < N1; ++l) sb[sidx(i, j, l)] = v[c][l];
-        __syncthreads();
+        wsync();
         if (active && h) {
             const int bx = child_bit(h, 0);
             #pragma unroll
@@ -116,11 +156,11 @@ __device__ void hanging_forward(T (&v)[NC][N1], uint32_t h, bool active, int i, 
                 }
             }
         }
-        __syncthreads();
+        wsync();
         // y-sweeps: lines parallel to y at (i, l)
         #pragma unroll
         for (int l = 0; l < N1; ++l) sb[sidx(i, j, l)] = v[c][l];
-        __syncthreads();
+        wsync();
         if (active && h) {
             const int by = child_bit(h, 1);
             #pragma unroll
@@ -133,7 +173,7 @@ __device__ void hanging_forward(T (&v)[NC][N1], uint32_t h, bool active, int i, 
                 }
             }
         }
-        __syncthreads();
+        wsync();
         // z-sweeps: the thread's own column (registers)
         if (active && h && line_hanging(h, 2, i, j, K)) {
             const int bz = child_bit(h, 2);
@@ -170,7 +210,7 @@ __device__ void hanging_transpose(T (&v)[NC][N1], uint32_t h, bool active, int i
         }
         #pragma unroll
         for (int l = 0; l < N1; ++l) sb[sidx(i, j, l)] = v[c][l];
-        __syncthreads();
+        wsync();
         if (active && h) {
             const int by = child_bit(h, 1);
             #pragma unroll
@@ -183,10 +223,10 @@ __device__ void hanging_transpose(T (&v)[NC][N1], uint32_t h, bool active, int i
                 }
             }
         }
-        __syncthreads();
+        wsync();
         #pragma unroll
         for (int l = 0; l < N1; ++l) sb[sidx(i, j, l)] = v[c][l];
-        __syncthreads();
+        wsync();
         if (active && h) {
             const int bx = child_bit(h, 0);
             #pragma unroll
@@ -199,16 +239,16 @@ __device__ void hanging_transpose(T (&v)[NC][N1], uint32_t h, bool active, int i
                 }
             }
         }
-        __syncthreads();
+        wsync();
     }
 }
 
 // ----------------------------------------------- sum-factorised gradient
 // Reference gradient at the Gauss points (iq = i, jq = j, lq) of the field
-// whose nodal column the thread holds in vin.  Uses buffers b0, b1.
+// whose nodal column the thread holds in vin.  Uses scratch buffers b0, b1.
 template <typename T>
-__device__ __forceinline__ void ref_gradient(const T (&vin)[N1], T (&gx)[Q], T (&gy)[Q], T (&gz)[Q],
-                                             int i, int j, T* b0, T* b1) {
+__device__ __forceinline__ void ref_gradient(const Rows<T>& R, const T (&vin)[N1], T (&gx)[Q], T (&gy)[Q],
+                                             T (&gz)[Q], int i, int j, T* b0, T* b1) {
     T a[Q];
     #pragma unroll
     for (int lq = 0; lq < Q; ++lq) {            // zeta interpolation (registers)
@@ -219,46 +259,46 @@ __device__ __forceinline__ void ref_gradient(const T (&vin)[N1], T (&gx)[Q], T (
     }
     #pragma unroll
     for (int lq = 0; lq < Q; ++lq) b0[sidx(i, j, lq)] = a[lq];
-    __syncthreads();
+    wsync();
     #pragma unroll
     for (int lq = 0; lq < Q; ++lq) {            // eta interpolation: thread (i, jq = j)
         T s = 0;
         #pragma unroll
-        for (int m = 0; m < N1; ++m) s += Tab<T>::B(j, m) * b0[sidx(i, m, lq)];
+        for (int m = 0; m < N1; ++m) s += R.Bj[m] * b0[sidx(i, m, lq)];
         a[lq] = s;
     }
     #pragma unroll
     for (int lq = 0; lq < Q; ++lq) b1[sidx(i, j, lq)] = a[lq];
-    __syncthreads();
+    wsync();
     #pragma unroll
     for (int lq = 0; lq < Q; ++lq) {            // xi interpolation: thread (iq = i, jq = j)
         T s = 0;
         #pragma unroll
-        for (int m = 0; m < N1; ++m) s += Tab<T>::B(i, m) * b1[sidx(m, j, lq)];
+        for (int m = 0; m < N1; ++m) s += R.Bi[m] * b1[sidx(m, j, lq)];
         a[lq] = s;
     }
     #pragma unroll
     for (int lq = 0; lq < Q; ++lq) b0[sidx(i, j, lq)] = a[lq];
-    __syncthreads();
+    wsync();
     #pragma unroll
     for (int lq = 0; lq < Q; ++lq) {            // collocated derivatives
         T sx = 0, sy = 0, sz = 0;
         #pragma unroll
         for (int m = 0; m < Q; ++m) {
-            sx += Tab<T>::Dg(i, m) * b0[sidx(m, j, lq)];
-            sy += Tab<T>::Dg(j, m) * b0[sidx(i, m, lq)];
+            sx += R.Di[m] * b0[sidx(m, j, lq)];
+            sy += R.Dj[m] * b0[sidx(i, m, lq)];
             sz += Tab<T>::Dg(lq, m) * a[m];
         }
         gx[lq] = sx; gy[lq] = sy; gz[lq] = sz;
     }
-    __syncthreads();
+    wsync();
 }
 
 // Transposed gradient: nodal column out[l] of
 //   sum_qp (d phi/d xi) Sx + (d phi/d eta) Sy + (d phi/d zeta) Sz + phi Sv.
 template <typename T, bool HAS_VAL>
-__device__ __forceinline__ void ref_gradient_T(const T (&Sx)[Q], const T (&Sy)[Q], const T (&Sz)[Q],
-                                               const T (&Sv)[Q], T (&out)[N1], int i, int j,
+__device__ __forceinline__ void ref_gradient_T(const Rows<T>& R, const T (&Sx)[Q], const T (&Sy)[Q],
+                                               const T (&Sz)[Q], const T (&Sv)[Q], T (&out)[N1], int i, int j,
                                                T* b0, T* b1, T* b2) {
     T t[Q];
     #pragma unroll
@@ -270,33 +310,32 @@ __device__ __forceinline__ void ref_gradient_T(const T (&Sx)[Q], const T (&Sy)[Q
         for (int m = 0; m < Q; ++m) s += Tab<T>::Dg(m, lq) * Sz[m];
         t[lq] = s;
     }
-    __syncthreads();
+    wsync();
     #pragma unroll
     for (int lq = 0; lq < Q; ++lq) {
         T s = t[lq];
         #pragma unroll
-        for (int m = 0; m < Q; ++m)
-            s += Tab<T>::Dg(m, i) * b0[sidx(m, j, lq)] + Tab<T>::Dg(m, j) * b1[sidx(i, m, lq)];
+        for (int m = 0; m < Q; ++m) s += R.DTi[m] * b0[sidx(m, j, lq)] + R.DTj[m] * b1[sidx(i, m, lq)];
         t[lq] = s;
     }
     #pragma unroll
     for (int lq = 0; lq < Q; ++lq) b2[sidx(i, j, lq)] = t[lq];
-    __syncthreads();
+    wsync();
     #pragma unroll
     for (int lq = 0; lq < Q; ++lq) {            // xi^T: thread (node i, jq = j)
         T s = 0;
         #pragma unroll
-        for (int m = 0; m < Q; ++m) s += Tab<T>::B(m, i) * b2[sidx(m, j, lq)];
+        for (int m = 0; m < Q; ++m) s += R.BTi[m] * b2[sidx(m, j, lq)];
         t[lq] = s;
     }
     #pragma unroll
     for (int lq = 0; lq < Q; ++lq) b0[sidx(i, j, lq)] = t[lq];
-    __syncthreads();
+    wsync();
     #pragma unroll
     for (int lq = 0; lq < Q; ++lq) {            // eta^T: thread (node i, node j)
         T s = 0;
         #pragma unroll
-        for (int m = 0; m < Q; ++m) s += Tab<T>::B(m, j) * b0[sidx(i, m, lq)];
+        for (int m = 0; m < Q; ++m) s += R.BTj[m] * b0[sidx(i, m, lq)];
         t[lq] = s;
     }
     #pragma unroll
@@ -306,10 +345,20 @@ __device__ __forceinline__ void ref_gradient_T(const T (&Sx)[Q], const T (&Sy)[Q
         for (int lq = 0; lq < Q; ++lq) s += Tab<T>::B(lq, l) * t[lq];
         out[l] = s;
     }
-    __syncthreads();
+    wsync();
 }
 
 // ------------------------------------------------------------ gather
+template <typename T>
+__device__ __forceinline__ void project3(const double* P, T& x0, T& x1, T& x2) {
+    const T p00 = T(P[0]), p11 = T(P[N2]), p22 = T(P[2 * N2]);
+    const T p01 = T(P[3 * N2]), p02 = T(P[4 * N2]), p12 = T(P[5 * N2]);
+    const T a = x0, b = x1, c = x2;
+    x0 = p00 * a + p01 * b + p02 * c;
+    x1 = p01 * a + p11 * b + p12 * c;
+    x2 = p02 * a + p12 * b + p22 * c;
+}
+
 // Velocity columns of element e (3 components) from a state vector x,
 // with the basal projector applied at bottom-plane slots.
 template <typename T, typename TIN>
@@ -328,15 +377,7 @@ __device__ __forceinline__ void gather_velocity(const ElemArgs& a, const TIN* x,
     }
     if (active) {
         const int pi = a.pidx[e];
-        if (pi >= 0) {
-            const double* P = a.pel + int64_t(pi) * 6 * N2 + ij;
-            const T p00 = T(P[0]), p11 = T(P[N2]), p22 = T(P[2 * N2]);
-            const T p01 = T(P[3 * N2]), p02 = T(P[4 * N2]), p12 = T(P[5 * N2]);
-            const T x0 = v[0][0], x1 = v[1][0], x2 = v[2][0];
-            v[0][0] = p00 * x0 + p01 * x1 + p02 * x2;
-            v[1][0] = p01 * x0 + p11 * x1 + p12 * x2;
-            v[2][0] = p02 * x0 + p12 * x1 + p22 * x2;
-        }
+        if (pi >= 0) project3<T>(a.pel + int64_t(pi) * 6 * N2 + ij, v[0][0], v[1][0], v[2][0]);
     }
 }
 
@@ -345,15 +386,7 @@ __device__ __forceinline__ void scatter_velocity(const ElemArgs& a, T* y, int64_
                                                  T (&v)[3][N1]) {
     if (!active) return;
     const int pi = a.pidx[e];
-    if (pi >= 0) {
-        const double* P = a.pel + int64_t(pi) * 6 * N2 + ij;
-        const T p00 = T(P[0]), p11 = T(P[N2]), p22 = T(P[2 * N2]);
-        const T p01 = T(P[3 * N2]), p02 = T(P[4 * N2]), p12 = T(P[5 * N2]);
-        const T x0 = v[0][0], x1 = v[1][0], x2 = v[2][0];
-        v[0][0] = p00 * x0 + p01 * x1 + p02 * x2;
-        v[1][0] = p01 * x0 + p11 * x1 + p12 * x2;
-        v[2][0] = p02 * x0 + p12 * x1 + p22 * x2;
-    }
+    if (pi >= 0) project3<T>(a.pel + int64_t(pi) * 6 * N2 + ij, v[0][0], v[1][0], v[2][0]);
     #pragma unroll
     for (int l = 0; l < N1; ++l) {
         const int64_t g = a.nodes[e * N3 + ij + N2 * l];
@@ -363,46 +396,72 @@ __device__ __forceinline__ void scatter_velocity(const ElemArgs& a, T* y, int64_
     }
 }
 
-// Pressure value at Gauss point (i, j, lq) from the element's pressure dofs in smem.
-template <typename T>
-__device__ __forceinline__ T pressure_at(const T* pres, int npr, int ps, int i, int j, int lq) {
-    T s = 0;
+// Discontinuous pressure of the element folded per thread: pc[c] =
+// sum_{modes b with zeta factor c} p_b f_b(i) g_b(j), so that the pressure at
+// Gauss point (i, j, lq) is sum_c P1[lq][c] pc[c] (uniform table reads).
+template <typename T, typename TIN>
+__device__ __forceinline__ void pressure_fold(const ElemArgs& a, const TIN* x, int64_t e, bool active, int i, int j,
+                                              T (&pc)[N1]) {
+    const int ps = a.pspace;
+    #pragma unroll
+    for (int c = 0; c < N1; ++c) pc[c] = T(0);
+    if (!active) return;
+    const TIN* pe = x + 3 * a.Nv + e * a.npr;
     #pragma unroll
     for (int b = 0; b < NPRK; ++b) {
-        if (b < npr) {
-            s += pres[b] * Tab<T>::P1(ps, i, cPm[ps][b][0]) * Tab<T>::P1(ps, j, cPm[ps][b][1]) *
-                 Tab<T>::P1(ps, lq, cPm[ps][b][2]);
+        if (b < a.npr) {
+            const T f = Tab<T>::P1(ps, i, cPm[ps][b][0]) * Tab<T>::P1(ps, j, cPm[ps][b][1]);
+            const T pb = T(ld(pe + b)) * f;
+            const int cz = cPm[ps][b][2];
+            #pragma unroll
+            for (int c = 0; c < N1; ++c) if (c == cz) pc[c] += pb;
         }
     }
+}
+
+template <typename T>
+__device__ __forceinline__ T pressure_at(const T (&pc)[N1], int ps, int lq) {
+    T s = 0;
+    #pragma unroll
+    for (int c = 0; c < N1; ++c) s += Tab<T>::P1(ps, lq, c) * pc[c];
     return s;
 }
 
-// Pressure rows: out[b] = sum_qp psi_b(qp) gq(qp), reduced over the element's
-// threads through shared memory in chunks; written (not accumulated) to dst.
+// Pressure rows: dst[b] = sum_qp psi_b(qp) gq(qp), reduced over the element's
+// lanes through the element's shared scratch (3 N3 values) in chunks.
 template <typename T>
 __device__ void pressure_rows(const T (&gq)[Q], int npr, int ps, int i, int j, int ij, bool active,
                               T* sb, T* dst) {
     constexpr int CH = (3 * N3) / N2;   // rows per chunk
+    T h[N1];                            // sum_lq P1[lq][c] gq[lq]
+    #pragma unroll
+    for (int c = 0; c < N1; ++c) {
+        T s = 0;
+        #pragma unroll
+        for (int lq = 0; lq < Q; ++lq) s += Tab<T>::P1(ps, lq, c) * gq[lq];
+        h[c] = s;
+    }
     for (int b0 = 0; b0 < npr; b0 += CH) {
         #pragma unroll
         for (int cb = 0; cb < CH; ++cb) {
             const int b = b0 + cb;
             T s = 0;
             if (b < npr) {
-                const T f = Tab<T>::P1(ps, i, cPm[ps][b][0]) * Tab<T>::P1(ps, j, cPm[ps][b][1]);
+                const int cz = cPm[ps][b][2];
+                T hz = 0;
                 #pragma unroll
-                for (int lq = 0; lq < Q; ++lq) s += Tab<T>::P1(ps, lq, cPm[ps][b][2]) * gq[lq];
-                s *= f;
+                for (int c = 0; c < N1; ++c) if (c == cz) hz = h[c];
+                s = Tab<T>::P1(ps, i, cPm[ps][b][0]) * Tab<T>::P1(ps, j, cPm[ps][b][1]) * hz;
             }
             sb[cb * N2 + ij] = s;
         }
-        __syncthreads();
+        wsync();
         if (active && ij < CH && b0 + ij < npr) {
             T s = 0;
             for (int t = 0; t < N2; ++t) s += sb[ij * N2 + t];
             dst[b0 + ij] = s;
         }
-        __syncthreads();
+        wsync();
     }
 }
 

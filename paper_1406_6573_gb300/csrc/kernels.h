@@ -15,9 +15,12 @@ enum ElemMode : int {
     MODE_GRAD_A = 4,       // g_A = -(1/(n A)) int mu D(lambda) : D(u)
 };
 
-// Number of stored values per quadrature point of the linearised state:
-// Jinv (9, reference-major), w detJ, mu w detJ, Dhat (6: 00 11 22 01 02 12).
-constexpr int STATE_FIELDS = 17;
+// Linearised state, per element: two element constants (Jinv[0][0] = 1/a,
+// Jinv[1][1] = 1/b: x and y are affine in xi and eta on the extruded slab
+// meshes, so the first two rows of Jinv are diagonal and constant), then
+// STATE_FIELDS values per quadrature point: Jinv[2][0..2], w detJ, mu w detJ,
+// Dhat (6: 00 11 22 01 02 12).
+constexpr int STATE_FIELDS = 11;
 
 struct ElemArgs {
     int64_t E, Nv;
@@ -32,13 +35,15 @@ struct ElemArgs {
     const void* u;             // linearisation point (fused apply), same type as x
     const double* ud;          // FP64 state (linearize, gradient)
     const double* lam;         // FP64 adjoint (gradient)
-    void* state;               // [E][17][q^3] (linearize output)
+    void* state;               // [E][state stride] (linearize output)
     const void* cstate;        // same (state apply input)
     double C, gamma, delta, pexp;
     int n_is_3;
     double body[3];
     double* gA;                // gradient output (accumulated)
     double gA_scale;
+    int* err;                  // device status word (bounded waits that expired)
+    int persistent_blocks;     // grid size of the persistent state-apply kernel
 };
 
 struct FaceArgs {
@@ -66,7 +71,8 @@ enum FaceMode : int { FACE_APPLY = 0, FACE_GRAD_LOGBETA = 1 };
     int launch_elem_k##KK(int mode, int prec, int state_prec, bool trans, const ElemArgs& a,  \
                           cudaStream_t s);                                                    \
     int launch_face_k##KK(int mode, int prec, const FaceArgs& a, cudaStream_t s);             \
-    int upload_tables_k##KK(const void* tables_k);
+    int upload_tables_k##KK(const void* tables_k);                                            \
+    int64_t state_stride_k##KK();
 STOKES_DECLARE_DEGREE(2)
 STOKES_DECLARE_DEGREE(3)
 STOKES_DECLARE_DEGREE(4)

@@ -435,6 +435,23 @@ int build_host_mesh(const stokes_mesh_desc& d, HostMesh& m, std::string& err) {
         }
     }
     if (inverted) { err = "element with det J <= 0"; return STOKES_E_MESH; }
+    // The linearised state stores only the third row of Jinv per quadrature
+    // point: x and y must be affine in (xi, eta) on every element, i.e. the
+    // first two rows of Jinv diagonal and constant.
+    bool not_slab = false;
+    #pragma omp parallel for schedule(static) reduction(|| : not_slab)
+    for (int64_t e = 0; e < E; ++e) {
+        const double* G = &m.geo[size_t(e) * 10 * Q3];
+        const double a0 = G[0 * Q3], b0 = G[4 * Q3];
+        for (int qp = 0; qp < Q3; ++qp) {
+            const double tol = 1e-11 * (std::fabs(a0) + std::fabs(b0));
+            if (std::fabs(G[1 * Q3 + qp]) > tol || std::fabs(G[2 * Q3 + qp]) > tol ||
+                std::fabs(G[3 * Q3 + qp]) > tol || std::fabs(G[5 * Q3 + qp]) > tol ||
+                std::fabs(G[0 * Q3 + qp] - a0) > tol || std::fabs(G[4 * Q3 + qp] - b0) > tol)
+                not_slab = true;
+        }
+    }
+    if (not_slab) { err = "internal: element map is not affine in x and y"; return STOKES_E_MESH; }
 
     // ------------------------------------------------------- basal nodes
     // global nodes on z = 0: every bottom-plane slot of a basal face maps to one
