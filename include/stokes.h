@@ -180,6 +180,48 @@ int stokes_state_apply(const stokes_state* state, const void* x, void* y, void* 
 int stokes_state_apply_transpose(const stokes_state* state, const void* x, void* y,
                                  void* stream);
 
+/* ---- Newton-Krylov solver (Section 4) -------------------------------------
+ * Inexact Newton with backtracking on ||r||_2 and Eisenstat-Walker forcing;
+ * right-preconditioned FGMRES(m) with the block upper-triangular
+ * preconditioner of Eq. 4.1 (velocity block: exact vertical-column blocks of
+ * F; Schur complement: -diag of the 1/mu-weighted pressure mass, Section 6).
+ * inner_prec = STOKES_F32: Krylov vectors, operator applies and
+ * preconditioner in FP32, the linear residual recomputed in FP64 at every
+ * restart (iterative refinement), residual and Newton update in FP64.
+ * inner_prec = STOKES_F64: the same loop entirely in FP64.
+ * The solver handle owns its workspaces (allocated by stokes_solver_create:
+ * about (2m+3) inner-precision and 6 FP64 state vectors, two linearised
+ * states and the banded column blocks). */
+typedef struct stokes_solver stokes_solver;
+
+typedef struct {
+    int inner_prec;      /* STOKES_F32 (mixed precision) or STOKES_F64               */
+    int restart;         /* FGMRES restart length m (default 30)                      */
+    int max_krylov;      /* Krylov iterations per linear solve (default 1000)         */
+    int max_newton;      /* Newton steps (default 50)                                 */
+    double rtol;         /* Newton stop: ||r|| <= rtol ||r_0|| (default 1e-10)        */
+    double eta_max;      /* cap of the forcing term (default 0.1)                     */
+} stokes_solver_opts;
+
+typedef struct {
+    int converged, newton_its, krylov_its, line_search_cuts;
+    double res0, res_final, seconds;
+    double history[64];          /* ||r_j||, j = 0 .. newton_its (first 64)          */
+    int krylov_per_newton[64];
+} stokes_solve_report;
+
+int stokes_solver_create(const stokes_mesh* mesh, const stokes_solver_opts* opts, stokes_solver** out);
+int stokes_solver_destroy(stokes_solver* solver);
+/* Solve r_c(up) = 0 starting from the device FP64 state up (overwritten).
+ * Returns STOKES_E_NOCONV (report filled) if rtol is not reached. */
+int stokes_newton_solve(stokes_solver* solver, const stokes_params* params, double* up,
+                        stokes_solve_report* report, void* stream);
+/* Solve J_c(up_lin) x = b (transpose = 0) or J_c(up_lin)^T x = b (transpose = 1)
+ * to ||b - J x|| <= rtol ||b||; up_lin, b, x: device FP64 [3Nv+Np]. */
+int stokes_linear_solve(stokes_solver* solver, const stokes_params* params, const double* up_lin,
+                        const double* b, double* x, int transpose, double rtol,
+                        stokes_solve_report* report, void* stream);
+
 /* Per-kernel timing (tracing).  Between stokes_profile_begin and
  * stokes_profile_end every operator call on this mesh records a CUDA event
  * pair around each of its launches, on the caller's stream; end synchronises

@@ -62,6 +62,25 @@ class stokes_profile(C.Structure):
                 ("face", stokes_kernel_time), ("constraint", stokes_kernel_time)]
 
 
+class stokes_solver_opts(C.Structure):
+    _fields_ = [("inner_prec", C.c_int), ("restart", C.c_int), ("max_krylov", C.c_int),
+                ("max_newton", C.c_int), ("rtol", C.c_double), ("eta_max", C.c_double)]
+
+
+class stokes_solve_report(C.Structure):
+    _fields_ = [("converged", C.c_int), ("newton_its", C.c_int), ("krylov_its", C.c_int),
+                ("line_search_cuts", C.c_int), ("res0", C.c_double), ("res_final", C.c_double),
+                ("seconds", C.c_double), ("history", C.c_double * 64), ("krylov_per_newton", C.c_int * 64)]
+
+    def as_dict(self):
+        n = min(self.newton_its + 1, 64)
+        return {"converged": bool(self.converged), "newton_its": self.newton_its,
+                "krylov_its": self.krylov_its, "line_search_cuts": self.line_search_cuts,
+                "res0": self.res0, "res_final": self.res_final, "seconds": self.seconds,
+                "history": list(self.history[:n]),
+                "krylov_per_newton": list(self.krylov_per_newton[:max(n - 1, 0)])}
+
+
 # every symbol declared in include/stokes.h, with its ctypes signature
 _SIGS = {
     "stokes_mesh_create": (C.c_int, [C.POINTER(stokes_mesh_desc), C.POINTER(C.c_void_p)]),
@@ -82,6 +101,13 @@ _SIGS = {
     "stokes_state_apply": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "stokes_state_apply_transpose": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "stokes_mesh_status": (C.c_int, [C.c_void_p]),
+    "stokes_solver_create": (C.c_int, [C.c_void_p, C.POINTER(stokes_solver_opts), C.POINTER(C.c_void_p)]),
+    "stokes_solver_destroy": (C.c_int, [C.c_void_p]),
+    "stokes_newton_solve": (C.c_int, [C.c_void_p, C.POINTER(stokes_params), C.c_void_p,
+                                      C.POINTER(stokes_solve_report), C.c_void_p]),
+    "stokes_linear_solve": (C.c_int, [C.c_void_p, C.POINTER(stokes_params), C.c_void_p, C.c_void_p,
+                                      C.c_void_p, C.c_int, C.c_double, C.POINTER(stokes_solve_report),
+                                      C.c_void_p]),
     "stokes_profile_begin": (C.c_int, [C.c_void_p]),
     "stokes_profile_end": (C.c_int, [C.c_void_p, C.POINTER(stokes_profile)]),
     "stokes_last_error": (C.c_char_p, []),
@@ -210,3 +236,31 @@ def stokes_profile_end(h):
 
 def stokes_mesh_status(h):
     _check(lib().stokes_mesh_status(h))
+
+
+def stokes_solver_create(h, opts=None):
+    s = C.c_void_p()
+    _check(lib().stokes_solver_create(h, C.byref(opts) if opts is not None else None, C.byref(s)))
+    return s
+
+
+def stokes_solver_destroy(s):
+    _check(lib().stokes_solver_destroy(s))
+
+
+def stokes_newton_solve(s, params, up, stream=None, check=True):
+    """Returns (status code, report dict); raises on errors other than E_NOCONV when check."""
+    rep = stokes_solve_report()
+    rc = lib().stokes_newton_solve(s, C.byref(params), _ptr(up), C.byref(rep), _stream(stream))
+    if check and rc not in (STOKES_OK, -6):
+        _check(rc)
+    return rc, rep.as_dict()
+
+
+def stokes_linear_solve(s, params, up_lin, b, x, transpose=False, rtol=1e-8, stream=None, check=True):
+    rep = stokes_solve_report()
+    rc = lib().stokes_linear_solve(s, C.byref(params), _ptr(up_lin), _ptr(b), _ptr(x), int(transpose),
+                                   float(rtol), C.byref(rep), _stream(stream))
+    if check and rc not in (STOKES_OK, -6):
+        _check(rc)
+    return rc, rep.as_dict()

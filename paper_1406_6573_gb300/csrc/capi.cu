@@ -8,37 +8,13 @@
 
 #include <cuda_runtime.h>
 
-#include "common.h"
-#include "kernels.h"
+#include "handles.h"
 
 using namespace stokes;
 
 namespace {
 
 thread_local std::string g_err;
-
-int fail(int code, const std::string& msg) {
-    g_err = msg;
-    return code;
-}
-
-int cuda_fail(cudaError_t e, const char* where) {
-    return fail(STOKES_E_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
-}
-
-// Make `dev` current for the duration of a call, restoring the caller's device.
-struct DeviceGuard {
-    int prev = -1;
-    cudaError_t err = cudaSuccess;
-    explicit DeviceGuard(int dev) {
-        err = cudaGetDevice(&prev);
-        if (err == cudaSuccess && prev != dev) err = cudaSetDevice(dev);
-    }
-    ~DeviceGuard() {
-        int cur = -1;
-        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-    }
-};
 
 constexpr int MAX_DEVICES = 64;
 std::mutex g_tables_mu;
@@ -61,6 +37,53 @@ int ensure_tables(int dev, int k) {
     if (e != 0) return cuda_fail(cudaError_t(e), "uploading basis tables");
     g_tables_done[dev][k] = true;
     return STOKES_OK;
+}
+
+template <typename T>
+int upload(T** dst, const std::vector<T>& src) {
+    *dst = nullptr;
+    if (src.empty()) return STOKES_OK;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(dst), src.size() * sizeof(T));
+    if (e != cudaSuccess) { *dst = nullptr; return fail(STOKES_E_NOMEM, "cudaMalloc of mesh data failed"); }
+    e = cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "uploading mesh data");
+    return STOKES_OK;
+}
+
+// Run `launch` between two recorded events when profiling (class c).
+template <typename F>
+int timed(const stokes_mesh* m, int c, cudaStream_t s, F&& launch) {
+    if (!m->prof.active) return launch();
+    cudaEvent_t a = m->prof.next(), b = m->prof.next();
+    if (!a || !b) return launch();
+    size_t ia = m->prof.used - 2;
+    cudaEventRecord(a, s);
+    int rc = launch();
+    cudaEventRecord(b, s);
+    m->prof.recs.push_back({c, ia});
+    return rc;
+}
+
+void free_mesh_device(stokes_mesh* m) {
+    for (cudaEvent_t ev : m->prof.pool) cudaEventDestroy(ev);
+    m->prof.pool.clear();
+    void* ptrs[] = {m->d_nodes, m->d_hang, m->d_geo, m->d_pidx, m->d_pel, m->d_face_elem, m->d_fidx,
+                    m->d_fgeo, m->d_fmap, m->d_basal_nodes, m->d_basal_P, m->d_err, m->d_col_of,
+                    m->d_pos_of, m->d_col_nodes, m->d_col_len, m->d_col_basal};
+    for (void* p : ptrs) if (p) cudaFree(p);
+}
+
+}  // namespace
+
+namespace stokes {
+
+int fail(int code, const std::string& msg) {
+    g_err = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* where) {
+    return fail(STOKES_E_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
 
 int launch_elem(int k, int mode, int prec, int state_prec, bool trans, const ElemArgs& a, cudaStream_t s) {
@@ -90,85 +113,13 @@ int launch_face(int k, int mode, int prec, const FaceArgs& a, cudaStream_t s) {
     return int(cudaErrorInvalidValue);
 }
 
-template <typename T>
-int upload(T** dst, const std::vector<T>& src) {
-    *dst = nullptr;
-    if (src.empty()) return STOKES_OK;
-    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(dst), src.size() * sizeof(T));
-    if (e != cudaSuccess) { *dst = nullptr; return fail(STOKES_E_NOMEM, "cudaMalloc of mesh data failed"); }
-    e = cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) return cuda_fail(e, "uploading mesh data");
-    return STOKES_OK;
-}
-
-}  // namespace
-
-namespace {
-// Event pairs recorded around launches while profiling is active.
-struct Profiler {
-    bool active = false;
-    std::vector<cudaEvent_t> pool;            // reusable events
-    std::vector<std::pair<int, size_t>> recs; // (kernel class, index of the start event)
-    size_t used = 0;
-    cudaEvent_t next() {
-        if (used == pool.size()) {
-            cudaEvent_t ev;
-            if (cudaEventCreate(&ev) != cudaSuccess) return nullptr;
-            pool.push_back(ev);
-        }
-        return pool[used++];
+int launch_precond_assembly(int k, int prec, const ColArgs& a, cudaStream_t s) {
+    switch (k) {
+        case 2: return launch_precond_assembly_k2(prec, a, s);
+        case 3: return launch_precond_assembly_k3(prec, a, s);
+        case 4: return launch_precond_assembly_k4(prec, a, s);
     }
-};
-}  // namespace
-
-struct stokes_mesh {
-    mutable Profiler prof;
-    HostMesh h;
-    int device = -1;
-    bool on_device = false;
-    int32_t* d_nodes = nullptr;
-    uint32_t* d_hang = nullptr;
-    double* d_geo = nullptr;
-    int32_t* d_pidx = nullptr;
-    double* d_pel = nullptr;
-    int32_t* d_face_elem = nullptr;
-    double* d_fgeo = nullptr;
-    int32_t* d_fmap = nullptr;
-    int32_t* d_basal_nodes = nullptr;
-    double* d_basal_P = nullptr;
-    int* d_err = nullptr;          // status word written by kernels (bounded waits)
-};
-
-struct stokes_state {
-    const stokes_mesh* mesh = nullptr;
-    int prec = 0;
-    void* d_state = nullptr;
-    stokes_params params{};
-    bool linearized = false;
-};
-
-namespace {
-
-// Run `launch` between two recorded events when profiling (class c).
-template <typename F>
-int timed(const stokes_mesh* m, int c, cudaStream_t s, F&& launch) {
-    if (!m->prof.active) return launch();
-    cudaEvent_t a = m->prof.next(), b = m->prof.next();
-    if (!a || !b) return launch();
-    size_t ia = m->prof.used - 2;
-    cudaEventRecord(a, s);
-    int rc = launch();
-    cudaEventRecord(b, s);
-    m->prof.recs.push_back({c, ia});
-    return rc;
-}
-
-void free_mesh_device(stokes_mesh* m) {
-    for (cudaEvent_t ev : m->prof.pool) cudaEventDestroy(ev);
-    m->prof.pool.clear();
-    void* ptrs[] = {m->d_nodes, m->d_hang, m->d_geo, m->d_pidx, m->d_pel, m->d_face_elem,
-                    m->d_fgeo, m->d_fmap, m->d_basal_nodes, m->d_basal_P, m->d_err};
-    for (void* p : ptrs) if (p) cudaFree(p);
+    return int(cudaErrorInvalidValue);
 }
 
 int check_common(const stokes_mesh* m, int prec) {
@@ -215,7 +166,6 @@ size_t vec_bytes(const stokes_mesh* m, int prec) {
     return size_t(3 * m->h.Nv + m->h.Np) * (prec == STOKES_F32 ? 4 : 8);
 }
 
-// y = (element terms of x) + Robin(x) + (I - P) x ; mode selects the element term.
 int operator_sequence(const stokes_mesh* m, const stokes_params* p, int mode, int prec, int state_prec,
                       bool trans, const void* x, const void* u, const void* cstate, void* y, cudaStream_t s) {
     int e = timed(m, 0, s, [&] { return int(cudaMemsetAsync(y, 0, vec_bytes(m, prec), s)); });
@@ -224,6 +174,7 @@ int operator_sequence(const stokes_mesh* m, const stokes_params* p, int mode, in
     a.x = x; a.y = y; a.u = u; a.cstate = cstate;
     e = timed(m, 1, s, [&] { return launch_elem(m->h.k, mode, prec, state_prec, trans, a, s); });
     if (e) return cuda_fail(cudaError_t(e), "element kernel launch");
+    if (mode == MODE_STATE_GRADP) return STOKES_OK;   // zero velocity input: no Robin or (I - P) term
     if (p->robin && m->h.nF > 0) {
         FaceArgs f = face_args(m, p);
         f.x = x; f.y = y;
@@ -237,7 +188,12 @@ int operator_sequence(const stokes_mesh* m, const stokes_params* p, int mode, in
     return STOKES_OK;
 }
 
-}  // namespace
+int state_gradp(const stokes_state* st, const void* x, void* y, cudaStream_t s) {
+    return operator_sequence(st->mesh, &st->params, MODE_STATE_GRADP, st->prec, st->prec, false, x, nullptr,
+                             st->d_state, y, s);
+}
+
+}  // namespace stokes
 
 extern "C" {
 
@@ -276,6 +232,19 @@ int stokes_mesh_create(const stokes_mesh_desc* desc, stokes_mesh** out) {
         if (rc == STOKES_OK) rc = upload(&m->d_basal_nodes, m->h.basal_nodes);
         if (rc == STOKES_OK) rc = upload(&m->d_basal_P, m->h.basal_P);
         if (rc == STOKES_OK) rc = upload(&m->d_err, std::vector<int>(1, 0));
+        if (rc == STOKES_OK) rc = upload(&m->d_fidx, m->h.elem_fidx);
+        if (rc == STOKES_OK) rc = upload(&m->d_col_of, m->h.col_of);
+        if (rc == STOKES_OK) rc = upload(&m->d_pos_of, m->h.pos_of);
+        if (rc == STOKES_OK) rc = upload(&m->d_col_nodes, m->h.col_nodes);
+        if (rc == STOKES_OK) rc = upload(&m->d_col_len, m->h.col_len);
+        if (rc == STOKES_OK) {
+            std::vector<int32_t> cb(size_t(m->h.ncol), -1);
+            for (int64_t b = 0; b < m->h.Nb; ++b) {
+                const int32_t g = m->h.basal_nodes[b];
+                if (m->h.pos_of[g] == 0) cb[m->h.col_of[g]] = int32_t(b);
+            }
+            rc = upload(&m->d_col_basal, cb);
+        }
         if (rc != STOKES_OK) { free_mesh_device(m); delete m; return rc; }
         m->on_device = true;
         // the large per-qp arrays live on the device only

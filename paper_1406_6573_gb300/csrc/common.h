@@ -61,6 +61,15 @@ struct HostMesh {
     std::vector<int32_t> basal_nodes;  // [Nb] global node of each basal node
     std::vector<double> basal_P;       // [Nb][6] P00 P11 P22 P01 P02 P12
     std::vector<double> node_xyz;      // [Nv][3]
+    // vertical node columns (nodes sharing the reference (X, Y) position),
+    // used by the column-block preconditioner of the velocity block
+    int64_t ncol = 0;
+    int colmax = 0;                    // most nodes in one column
+    int bnode = 0;                     // largest in-element distance of two column positions
+    std::vector<int32_t> col_of;       // [Nv] column of each node
+    std::vector<int32_t> pos_of;       // [Nv] position (Z rank) within its column
+    std::vector<int32_t> col_nodes;    // [colmax][ncol] node at (pos, column), -1 padding
+    std::vector<int32_t> col_len;      // [ncol]
 };
 
 // Returns STOKES_OK or an error code; `err` receives a message on failure.

@@ -55,11 +55,11 @@ __device__ __forceinline__ void sym6(const T (&g)[3][3], T& E00, T& E11, T& E22,
 // Generic element kernel (residual, fused Jacobian, linearisation, A-gradient).
 // T: arithmetic type.  S: element type of the stored state (linearize).
 template <typename T, typename S, int MODE, bool TRANS>
-__global__ void __launch_bounds__(THREADS) elem_kernel(ElemArgs a) {
-    __shared__ T sbuf[WARPS][EPW + 1][3][N3];
+__global__ void __launch_bounds__(32 * GW<T>) elem_kernel(ElemArgs a) {
+    __shared__ __align__(16) T sbuf[GW<T>][EPW + 1][3][BUFLEN<T>];
     const LaneMap L;
     const int i = L.i, j = L.j, ij = L.ij, es = L.es;
-    const int64_t e = int64_t(blockIdx.x) * EPB + L.warp * EPW + es;
+    const int64_t e = int64_t(blockIdx.x) * (GW<T> * EPW) + L.warp * EPW + es;
     const bool active = (es < EPW) && (e < a.E);
     T* b0 = sbuf[L.warp][es][0];
     T* b1 = sbuf[L.warp][es][1];
@@ -81,7 +81,7 @@ __global__ void __launch_bounds__(THREADS) elem_kernel(ElemArgs a) {
         T pc[N1];
         pressure_fold<T, T>(a, static_cast<const T*>(a.x), e, active, i, j, pc);
         #pragma unroll
-        for (int c = 0; c < 3; ++c) ref_gradient<T>(R, v[c], G[c][0], G[c][1], G[c][2], i, j, b0, b1);
+        for (int c = 0; c < 3; ++c) ref_gradient<T>(R, v[c], G[c][0], G[c][1], G[c][2], i, j, b0, b1, b2);
         T Sv[3][Q];
         #pragma unroll
         for (int lq = 0; lq < Q; ++lq) {
@@ -120,7 +120,7 @@ __global__ void __launch_bounds__(THREADS) elem_kernel(ElemArgs a) {
             gather_velocity<T, T>(a, static_cast<const T*>(a.u), e, active, ij, v);
             if (any_h) hanging_forward<T, 3>(v, h, active, i, j, sb);
             #pragma unroll
-            for (int c = 0; c < 3; ++c) ref_gradient<T>(R, v[c], G[c][0], G[c][1], G[c][2], i, j, b0, b1);
+            for (int c = 0; c < 3; ++c) ref_gradient<T>(R, v[c], G[c][0], G[c][1], G[c][2], i, j, b0, b1, b2);
             #pragma unroll
             for (int lq = 0; lq < Q; ++lq) {
                 T Ji[9], wdj;
@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(THREADS) elem_kernel(ElemArgs a) {
         T pc[N1];
         pressure_fold<T, T>(a, static_cast<const T*>(a.x), e, active, i, j, pc);
         #pragma unroll
-        for (int c = 0; c < 3; ++c) ref_gradient<T>(R, v[c], G[c][0], G[c][1], G[c][2], i, j, b0, b1);
+        for (int c = 0; c < 3; ++c) ref_gradient<T>(R, v[c], G[c][0], G[c][1], G[c][2], i, j, b0, b1, b2);
         #pragma unroll
         for (int lq = 0; lq < Q; ++lq) {
             T Ji[9], wdj;
@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(THREADS) elem_kernel(ElemArgs a) {
         gather_velocity<T, double>(a, a.ud, e, active, ij, v);
         if (any_h) hanging_forward<T, 3>(v, h, active, i, j, sb);
         #pragma unroll
-        for (int c = 0; c < 3; ++c) ref_gradient<T>(R, v[c], G[c][0], G[c][1], G[c][2], i, j, b0, b1);
+        for (int c = 0; c < 3; ++c) ref_gradient<T>(R, v[c], G[c][0], G[c][1], G[c][2], i, j, b0, b1, b2);
         S* st = static_cast<S*>(a.state) + e * SSTRIDE;
         #pragma unroll
         for (int lq = 0; lq < Q; ++lq) {
@@ -221,13 +221,13 @@ __global__ void __launch_bounds__(THREADS) elem_kernel(ElemArgs a) {
             gather_velocity<T, double>(a, a.lam, e, active, ij, v);
             if (any_h) hanging_forward<T, 3>(v, h, active, i, j, sb);
             #pragma unroll
-            for (int c = 0; c < 3; ++c) ref_gradient<T>(R, v[c], Gl[c][0], Gl[c][1], Gl[c][2], i, j, b0, b1);
+            for (int c = 0; c < 3; ++c) ref_gradient<T>(R, v[c], Gl[c][0], Gl[c][1], Gl[c][2], i, j, b0, b1, b2);
         }
         T v[3][N1];
         gather_velocity<T, double>(a, a.ud, e, active, ij, v);
         if (any_h) hanging_forward<T, 3>(v, h, active, i, j, sb);
         #pragma unroll
-        for (int c = 0; c < 3; ++c) ref_gradient<T>(R, v[c], G[c][0], G[c][1], G[c][2], i, j, b0, b1);
+        for (int c = 0; c < 3; ++c) ref_gradient<T>(R, v[c], G[c][0], G[c][1], G[c][2], i, j, b0, b1, b2);
         #pragma unroll
         for (int lq = 0; lq < Q; ++lq) {
             T Ji[9], wdj;
@@ -265,12 +265,14 @@ template <typename T>
 struct StateApplyCfg {
     static constexpr int W = sizeof(T) == 8 ? 4 : 8;        // warps per block
     static constexpr int BUF = EPW * SSTRIDE;                // values per stage buffer
-    static constexpr int SCR = (EPW + 1) * 3 * N3;           // scratch per warp
+    static constexpr int SCR = (EPW + 1) * 3 * BUFLEN<T>;    // scratch per warp
     static constexpr int PER_WARP = ((2 * BUF + SCR) * int(sizeof(T)) + 127) / 128 * 128;
     static constexpr int SMEM = W * PER_WARP + W * 2 * 8;
 };
 
-template <typename T>
+// PONLY: the velocity part of x is taken as zero (B^T p only, used by the
+// block preconditioner): no gather, no forward contractions, no pressure rows.
+template <typename T, bool PONLY>
 __global__ void __launch_bounds__(32 * StateApplyCfg<T>::W) state_apply_kernel(ElemArgs a) {
     using C = StateApplyCfg<T>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -280,10 +282,10 @@ __global__ void __launch_bounds__(32 * StateApplyCfg<T>::W) state_apply_kernel(E
     T* stage[2] = {reinterpret_cast<T*>(wbase), reinterpret_cast<T*>(wbase) + C::BUF};
     T* scratch = reinterpret_cast<T*>(wbase) + 2 * C::BUF;
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + C::W * C::PER_WARP) + 2 * L.warp;
-    T* sb = scratch + es * 3 * N3;
+    T* sb = scratch + es * 3 * BUFLEN<T>;
     T* b0 = sb;
-    T* b1 = sb + N3;
-    T* b2 = sb + 2 * N3;
+    T* b1 = sb + BUFLEN<T>;
+    T* b2 = sb + 2 * BUFLEN<T>;
     const int ps = a.pspace;
     const T* S = static_cast<const T*>(a.cstate);
     const T* x = static_cast<const T*>(a.x);
@@ -325,14 +327,23 @@ __global__ void __launch_bounds__(32 * StateApplyCfg<T>::W) state_apply_kernel(E
         const uint32_t h = active ? a.hang[e] : 0u;
         const bool any_h = a.any_hang ? (__any_sync(0xffffffffu, (h & ((1u << HANG_CHILD0) - 1)) != 0) != 0) : false;
 
-        T v[3][N1];
-        gather_velocity<T, T>(a, x, e, active, ij, v);
-        if (any_h) hanging_forward<T, 3>(v, h, active, i, j, sb);
         T pc[N1];
         pressure_fold<T, T>(a, x, e, active, i, j, pc);
         T G[3][3][Q];
-        #pragma unroll
-        for (int c = 0; c < 3; ++c) ref_gradient<T>(R, v[c], G[c][0], G[c][1], G[c][2], i, j, b0, b1);
+        if constexpr (!PONLY) {
+            T v[3][N1];
+            gather_velocity<T, T>(a, x, e, active, ij, v);
+            if (any_h) hanging_forward<T, 3>(v, h, active, i, j, sb);
+            #pragma unroll
+            for (int c = 0; c < 3; ++c) ref_gradient<T>(R, v[c], G[c][0], G[c][1], G[c][2], i, j, b0, b1, b2);
+        } else {
+            #pragma unroll
+            for (int c = 0; c < 3; ++c)
+                #pragma unroll
+                for (int m = 0; m < 3; ++m)
+                    #pragma unroll
+                    for (int lq = 0; lq < Q; ++lq) G[c][m][lq] = T(0);
+        }
 
         if (!mbar_wait_bounded(&bar[buf], uint32_t((it >> 1) & 1))) {
             // the staged state never arrived: report, let the copy drain, stop
@@ -385,7 +396,7 @@ __global__ void __launch_bounds__(32 * StateApplyCfg<T>::W) state_apply_kernel(E
         T dummy[Q];
         #pragma unroll
         for (int c = 0; c < 3; ++c) ref_gradient_T<T, false>(R, G[c][0], G[c][1], G[c][2], dummy, out[c], i, j, b0, b1, b2);
-        pressure_rows<T>(gq, a.npr, ps, i, j, ij, active, sb, y + 3 * a.Nv + e * a.npr);
+        if constexpr (!PONLY) pressure_rows<T>(gq, a.npr, ps, i, j, ij, active, sb, y + 3 * a.Nv + e * a.npr);
         if (any_h) hanging_transpose<T, 3>(out, h, active, i, j, sb);
         scatter_velocity<T>(a, y, e, active, ij, out);
         __syncwarp();
@@ -571,13 +582,14 @@ __global__ void __launch_bounds__(THREADS) face_kernel(FaceArgs a) {
 // ---------------------------------------------------------------- launchers
 template <typename T, typename S, int MODE, bool TRANS>
 int launch_elem_t(const ElemArgs& a, cudaStream_t s) {
-    const int64_t blocks = (a.E + EPB - 1) / EPB;
+    const int64_t epb = GW<T> * EPW;
+    const int64_t blocks = (a.E + epb - 1) / epb;
     if (blocks == 0) return int(cudaSuccess);
-    elem_kernel<T, S, MODE, TRANS><<<unsigned(blocks), THREADS, 0, s>>>(a);
+    elem_kernel<T, S, MODE, TRANS><<<unsigned(blocks), 32 * GW<T>, 0, s>>>(a);
     return int(cudaGetLastError());
 }
 
-template <typename T>
+template <typename T, bool PONLY>
 int launch_state_apply_t(const ElemArgs& a, cudaStream_t s) {
     using C = StateApplyCfg<T>;
     if (a.E == 0) return int(cudaSuccess);
@@ -586,10 +598,10 @@ int launch_state_apply_t(const ElemArgs& a, cudaStream_t s) {
     int dev = 0;
     cudaGetDevice(&dev);
     if (configured_device != dev) {
-        cudaError_t e = cudaFuncSetAttribute(state_apply_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+        cudaError_t e = cudaFuncSetAttribute(state_apply_kernel<T, PONLY>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
         if (e != cudaSuccess) return int(e);
         int per_sm = 0, sms = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, state_apply_kernel<T>, 32 * C::W, C::SMEM);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, state_apply_kernel<T, PONLY>, 32 * C::W, C::SMEM);
         if (e != cudaSuccess) return int(e);
         e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return int(e);
@@ -599,7 +611,7 @@ int launch_state_apply_t(const ElemArgs& a, cudaStream_t s) {
     const int64_t ngroups = (a.E + EPW - 1) / EPW;
     int64_t blocks = (ngroups + C::W - 1) / C::W;
     if (blocks > max_blocks) blocks = max_blocks;
-    state_apply_kernel<T><<<unsigned(blocks), 32 * C::W, C::SMEM, s>>>(a);
+    state_apply_kernel<T, PONLY><<<unsigned(blocks), 32 * C::W, C::SMEM, s>>>(a);
     return int(cudaGetLastError());
 }
 
@@ -628,7 +640,9 @@ inline int launch_elem_any(int mode, int prec, int state_prec, bool trans, const
         case MODE_STATE_APPLY:
             // the pointwise map of Eq. 2.7 is symmetric: the transposed apply
             // runs the same kernel
-            return f32 ? launch_state_apply_t<float>(a, s) : launch_state_apply_t<double>(a, s);
+            return f32 ? launch_state_apply_t<float, false>(a, s) : launch_state_apply_t<double, false>(a, s);
+        case MODE_STATE_GRADP:
+            return f32 ? launch_state_apply_t<float, true>(a, s) : launch_state_apply_t<double, true>(a, s);
         case MODE_GRAD_A:
             return launch_elem_t<double, double, MODE_GRAD_A, false>(a, s);
         default:

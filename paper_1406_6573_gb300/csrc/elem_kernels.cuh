@@ -48,8 +48,17 @@ constexpr int Q3 = N3;
 constexpr int WARPS = 8;
 constexpr int THREADS = 32 * WARPS;
 constexpr int EPW = 32 / N2;          // elements per warp
-constexpr int EPB = WARPS * EPW;      // elements per block
+constexpr int EPB = WARPS * EPW;      // elements per block (face kernels)
+// warps per block of the generic element kernel: fewer in FP64 so that the
+// static exchange buffers stay within 48 KB
+template <typename T> constexpr int GW = sizeof(T) == 8 ? 4 : 8;
 static_assert(EPW >= 1, "an element's columns must fit in one warp");
+// padded length of a contraction line in shared memory: a 16-byte multiple,
+// so that one line is read with vector loads
+template <typename T> struct LineLen { static constexpr int v = (N1 + (16 / int(sizeof(T))) - 1) / (16 / int(sizeof(T))) * (16 / int(sizeof(T))); };
+template <typename T> constexpr int LP = LineLen<T>::v;
+// one exchange buffer holds an N1 x N1 x N1 tensor as N1^2 padded lines
+template <typename T> constexpr int BUFLEN = LP<T> * N2;
 constexpr int NPRK = (K - 1) * (K - 1) * (K - 1) > K * (K + 1) * (K + 2) / 6
                          ? (K - 1) * (K - 1) * (K - 1) : K * (K + 1) * (K + 2) / 6;
 // per-element stride of the linearised state: 2 element constants then
@@ -87,15 +96,20 @@ template <> struct Tab<float> {
 template <typename T> struct Rows {
     T Bi[N1], Bj[N1];      // B[i][m], B[j][m]
     T BTi[Q], BTj[Q];      // B[m][i], B[m][j]
-    T Di[Q], Dj[Q];        // Dg[i][m], Dg[j][m]
+    T Ti[N1], Tj[N1];      // (Dg B)[i][m], (Dg B)[j][m]: derivative of the nodal interpolant
     T DTi[Q], DTj[Q];      // Dg[m][i], Dg[m][j]
     __device__ __forceinline__ void load(int i, int j) {
         #pragma unroll
-        for (int m = 0; m < N1; ++m) { Bi[m] = Tab<T>::B(i, m); Bj[m] = Tab<T>::B(j, m); }
+        for (int m = 0; m < N1; ++m) {
+            Bi[m] = Tab<T>::B(i, m); Bj[m] = Tab<T>::B(j, m);
+            T si = 0, sj = 0;
+            #pragma unroll
+            for (int p = 0; p < Q; ++p) { si += Tab<T>::Dg(i, p) * Tab<T>::B(p, m); sj += Tab<T>::Dg(j, p) * Tab<T>::B(p, m); }
+            Ti[m] = si; Tj[m] = sj;
+        }
         #pragma unroll
         for (int m = 0; m < Q; ++m) {
             BTi[m] = Tab<T>::B(m, i); BTj[m] = Tab<T>::B(m, j);
-            Di[m] = Tab<T>::Dg(i, m); Dj[m] = Tab<T>::Dg(j, m);
             DTi[m] = Tab<T>::Dg(m, i); DTj[m] = Tab<T>::Dg(m, j);
         }
     }
@@ -244,58 +258,87 @@ __device__ void hanging_transpose(T (&v)[NC][N1], uint32_t h, bool active, int i
 }
 
 // ----------------------------------------------- sum-factorised gradient
+// Exchange buffers hold the element tensor as padded lines; the layout of
+// each buffer puts the direction of the next contraction fastest, so that a
+// thread reads a whole line with 16-byte vector loads:
+//   X layout  xl(i, j, l) = i + LP (j + N1 l)   (xi-lines contiguous)
+//   Y layout  yl(i, j, l) = j + LP (i + N1 l)   (eta-lines contiguous)
+template <typename T> __device__ __forceinline__ int xl(int i, int j, int l) { return i + LP<T> * (j + N1 * l); }
+template <typename T> __device__ __forceinline__ int yl(int i, int j, int l) { return j + LP<T> * (i + N1 * l); }
+
+template <typename T>
+__device__ __forceinline__ void load_line(const T* p, T (&o)[N1]) {
+    if constexpr (sizeof(T) == 4) {
+        #pragma unroll
+        for (int k = 0; k < N1; k += 4) {
+            const float4 v = *reinterpret_cast<const float4*>(p + k);
+            o[k] = v.x;
+            if (k + 1 < N1) o[k + 1] = v.y;
+            if (k + 2 < N1) o[k + 2] = v.z;
+            if (k + 3 < N1) o[k + 3] = v.w;
+        }
+    } else {
+        #pragma unroll
+        for (int k = 0; k < N1; k += 2) {
+            const double2 v = *reinterpret_cast<const double2*>(p + k);
+            o[k] = v.x;
+            if (k + 1 < N1) o[k + 1] = v.y;
+        }
+    }
+}
+
 // Reference gradient at the Gauss points (iq = i, jq = j, lq) of the field
-// whose nodal column the thread holds in vin.  Uses scratch buffers b0, b1.
+// whose nodal column the thread holds in vin:
+//   zeta: interpolate (registers);  eta: interpolate and differentiate the
+//   same line;  xi: interpolate and differentiate the interpolated line, and
+//   interpolate the eta-derivative line;  zeta derivative by collocation.
 template <typename T>
 __device__ __forceinline__ void ref_gradient(const Rows<T>& R, const T (&vin)[N1], T (&gx)[Q], T (&gy)[Q],
-                                             T (&gz)[Q], int i, int j, T* b0, T* b1) {
+                                             T (&gz)[Q], int i, int j, T* b0, T* b1, T* b2) {
     T a[Q];
     #pragma unroll
-    for (int lq = 0; lq < Q; ++lq) {            // zeta interpolation (registers)
+    for (int lq = 0; lq < Q; ++lq) {
         T s = 0;
         #pragma unroll
         for (int l = 0; l < N1; ++l) s += Tab<T>::B(lq, l) * vin[l];
-        a[lq] = s;
+        b0[yl<T>(i, j, lq)] = s;
     }
-    #pragma unroll
-    for (int lq = 0; lq < Q; ++lq) b0[sidx(i, j, lq)] = a[lq];
     wsync();
     #pragma unroll
-    for (int lq = 0; lq < Q; ++lq) {            // eta interpolation: thread (i, jq = j)
+    for (int lq = 0; lq < Q; ++lq) {            // eta: thread (node i, jq = j)
+        T ln[N1];
+        load_line<T>(b0 + yl<T>(i, 0, lq), ln);
+        T si = 0, sd = 0;
+        #pragma unroll
+        for (int m = 0; m < N1; ++m) { si += R.Bj[m] * ln[m]; sd += R.Tj[m] * ln[m]; }
+        b1[xl<T>(i, j, lq)] = si;
+        b2[xl<T>(i, j, lq)] = sd;
+    }
+    wsync();
+    #pragma unroll
+    for (int lq = 0; lq < Q; ++lq) {            // xi: thread (iq = i, jq = j)
+        T l1[N1], l2[N1];
+        load_line<T>(b1 + xl<T>(0, j, lq), l1);
+        load_line<T>(b2 + xl<T>(0, j, lq), l2);
+        T sv = 0, sx = 0, sy = 0;
+        #pragma unroll
+        for (int m = 0; m < N1; ++m) { sv += R.Bi[m] * l1[m]; sx += R.Ti[m] * l1[m]; sy += R.Bi[m] * l2[m]; }
+        a[lq] = sv; gx[lq] = sx; gy[lq] = sy;
+    }
+    #pragma unroll
+    for (int lq = 0; lq < Q; ++lq) {            // zeta derivative, collocated
         T s = 0;
         #pragma unroll
-        for (int m = 0; m < N1; ++m) s += R.Bj[m] * b0[sidx(i, m, lq)];
-        a[lq] = s;
-    }
-    #pragma unroll
-    for (int lq = 0; lq < Q; ++lq) b1[sidx(i, j, lq)] = a[lq];
-    wsync();
-    #pragma unroll
-    for (int lq = 0; lq < Q; ++lq) {            // xi interpolation: thread (iq = i, jq = j)
-        T s = 0;
-        #pragma unroll
-        for (int m = 0; m < N1; ++m) s += R.Bi[m] * b1[sidx(m, j, lq)];
-        a[lq] = s;
-    }
-    #pragma unroll
-    for (int lq = 0; lq < Q; ++lq) b0[sidx(i, j, lq)] = a[lq];
-    wsync();
-    #pragma unroll
-    for (int lq = 0; lq < Q; ++lq) {            // collocated derivatives
-        T sx = 0, sy = 0, sz = 0;
-        #pragma unroll
-        for (int m = 0; m < Q; ++m) {
-            sx += R.Di[m] * b0[sidx(m, j, lq)];
-            sy += R.Dj[m] * b0[sidx(i, m, lq)];
-            sz += Tab<T>::Dg(lq, m) * a[m];
-        }
-        gx[lq] = sx; gy[lq] = sy; gz[lq] = sz;
+        for (int m = 0; m < Q; ++m) s += Tab<T>::Dg(lq, m) * a[m];
+        gz[lq] = s;
     }
     wsync();
 }
 
 // Transposed gradient: nodal column out[l] of
-//   sum_qp (d phi/d xi) Sx + (d phi/d eta) Sy + (d phi/d zeta) Sz + phi Sv.
+//   sum_qp (d phi/d xi) Sx + (d phi/d eta) Sy + (d phi/d zeta) Sz + phi Sv
+// (collocated derivative transposes at the Gauss points, then the three
+// transposed interpolations).
 template <typename T, bool HAS_VAL>
 __device__ __forceinline__ void ref_gradient_T(const Rows<T>& R, const T (&Sx)[Q], const T (&Sy)[Q],
                                                const T (&Sz)[Q], const T (&Sv)[Q], T (&out)[N1], int i, int j,
@@ -303,8 +346,8 @@ __device__ __forceinline__ void ref_gradient_T(const Rows<T>& R, const T (&Sx)[Q
     T t[Q];
     #pragma unroll
     for (int lq = 0; lq < Q; ++lq) {
-        b0[sidx(i, j, lq)] = Sx[lq];
-        b1[sidx(i, j, lq)] = Sy[lq];
+        b0[xl<T>(i, j, lq)] = Sx[lq];
+        b1[yl<T>(i, j, lq)] = Sy[lq];
         T s = HAS_VAL ? Sv[lq] : T(0);
         #pragma unroll
         for (int m = 0; m < Q; ++m) s += Tab<T>::Dg(m, lq) * Sz[m];
@@ -313,29 +356,32 @@ __device__ __forceinline__ void ref_gradient_T(const Rows<T>& R, const T (&Sx)[Q
     wsync();
     #pragma unroll
     for (int lq = 0; lq < Q; ++lq) {
+        T lx[N1], ly[N1];
+        load_line<T>(b0 + xl<T>(0, j, lq), lx);
+        load_line<T>(b1 + yl<T>(i, 0, lq), ly);
         T s = t[lq];
         #pragma unroll
-        for (int m = 0; m < Q; ++m) s += R.DTi[m] * b0[sidx(m, j, lq)] + R.DTj[m] * b1[sidx(i, m, lq)];
-        t[lq] = s;
+        for (int m = 0; m < Q; ++m) s += R.DTi[m] * lx[m] + R.DTj[m] * ly[m];
+        b2[xl<T>(i, j, lq)] = s;
     }
-    #pragma unroll
-    for (int lq = 0; lq < Q; ++lq) b2[sidx(i, j, lq)] = t[lq];
     wsync();
     #pragma unroll
     for (int lq = 0; lq < Q; ++lq) {            // xi^T: thread (node i, jq = j)
+        T ln[N1];
+        load_line<T>(b2 + xl<T>(0, j, lq), ln);
         T s = 0;
         #pragma unroll
-        for (int m = 0; m < Q; ++m) s += R.BTi[m] * b2[sidx(m, j, lq)];
-        t[lq] = s;
+        for (int m = 0; m < Q; ++m) s += R.BTi[m] * ln[m];
+        b0[yl<T>(i, j, lq)] = s;
     }
-    #pragma unroll
-    for (int lq = 0; lq < Q; ++lq) b0[sidx(i, j, lq)] = t[lq];
     wsync();
     #pragma unroll
     for (int lq = 0; lq < Q; ++lq) {            // eta^T: thread (node i, node j)
+        T ln[N1];
+        load_line<T>(b0 + yl<T>(i, 0, lq), ln);
         T s = 0;
         #pragma unroll
-        for (int m = 0; m < Q; ++m) s += R.BTj[m] * b0[sidx(i, m, lq)];
+        for (int m = 0; m < Q; ++m) s += R.BTj[m] * ln[m];
         t[lq] = s;
     }
     #pragma unroll

@@ -1,0 +1,103 @@
+// Internal handle definitions and helpers shared by the C-ABI layer (capi.cu)
+// and the Newton-Krylov driver (solver.cu).
+#pragma once
+
+#include <string>
+#include <utility>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "common.h"
+#include "kernels.h"
+#include "precond.h"
+
+namespace stokes {
+
+// Event pairs recorded around launches while profiling is active.
+struct Profiler {
+    bool active = false;
+    std::vector<cudaEvent_t> pool;            // reusable events
+    std::vector<std::pair<int, size_t>> recs; // (kernel class, index of the start event)
+    size_t used = 0;
+    cudaEvent_t next() {
+        if (used == pool.size()) {
+            cudaEvent_t ev;
+            if (cudaEventCreate(&ev) != cudaSuccess) return nullptr;
+            pool.push_back(ev);
+        }
+        return pool[used++];
+    }
+};
+
+int fail(int code, const std::string& msg);
+int cuda_fail(cudaError_t e, const char* where);
+
+// Make `dev` current for the duration of a call, restoring the caller's device.
+struct DeviceGuard {
+    int prev = -1;
+    cudaError_t err = cudaSuccess;
+    explicit DeviceGuard(int dev) {
+        err = cudaGetDevice(&prev);
+        if (err == cudaSuccess && prev != dev) err = cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+int launch_elem(int k, int mode, int prec, int state_prec, bool trans, const ElemArgs& a, cudaStream_t s);
+int launch_face(int k, int mode, int prec, const FaceArgs& a, cudaStream_t s);
+int launch_precond_assembly(int k, int prec, const ColArgs& a, cudaStream_t s);
+int64_t state_stride(int k);
+
+}  // namespace stokes
+
+struct stokes_mesh {
+    mutable stokes::Profiler prof;
+    stokes::HostMesh h;
+    int device = -1;
+    bool on_device = false;
+    int32_t* d_nodes = nullptr;
+    uint32_t* d_hang = nullptr;
+    double* d_geo = nullptr;
+    int32_t* d_pidx = nullptr;
+    double* d_pel = nullptr;
+    int32_t* d_face_elem = nullptr;
+    int32_t* d_fidx = nullptr;
+    double* d_fgeo = nullptr;
+    int32_t* d_fmap = nullptr;
+    int32_t* d_basal_nodes = nullptr;
+    double* d_basal_P = nullptr;
+    int* d_err = nullptr;          // status word written by kernels (bounded waits)
+    // vertical node columns (preconditioner)
+    int32_t* d_col_of = nullptr;
+    int32_t* d_pos_of = nullptr;
+    int32_t* d_col_nodes = nullptr;
+    int32_t* d_col_len = nullptr;
+    int32_t* d_col_basal = nullptr;
+};
+
+struct stokes_state {
+    const stokes_mesh* mesh = nullptr;
+    int prec = 0;
+    void* d_state = nullptr;
+    stokes_params params{};
+    bool linearized = false;
+};
+
+namespace stokes {
+
+int check_common(const stokes_mesh* m, int prec);
+int check_params(const stokes_mesh* m, const stokes_params* p);
+ElemArgs elem_args(const stokes_mesh* m, const stokes_params* p);
+FaceArgs face_args(const stokes_mesh* m, const stokes_params* p);
+size_t vec_bytes(const stokes_mesh* m, int prec);
+// y = (element terms of x) + Robin(x) + (I - P) x ; mode selects the element term
+int operator_sequence(const stokes_mesh* m, const stokes_params* p, int mode, int prec, int state_prec,
+                      bool trans, const void* x, const void* u, const void* cstate, void* y, cudaStream_t s);
+// velocity part of y = B^T p  for the pressure part of x (from the stored state)
+int state_gradp(const stokes_state* st, const void* x, void* y, cudaStream_t s);
+
+}  // namespace stokes

@@ -13,6 +13,7 @@ enum ElemMode : int {
     MODE_LINEARIZE = 2,    // state <- per-qp Newton coefficients at u (FP64 arithmetic)
     MODE_STATE_APPLY = 3,  // y  = J x from the stored state
     MODE_GRAD_A = 4,       // g_A = -(1/(n A)) int mu D(lambda) : D(u)
+    MODE_STATE_GRADP = 5,  // velocity rows of B^T p for the pressure part of x (stored state)
 };
 
 // Linearised state, per element: two element constants (Jinv[0][0] = 1/a,

@@ -199,6 +199,10 @@ int build_host_mesh(const stokes_mesh_desc& d, HostMesh& m, std::string& err) {
                     }
         }
         if (m.Nv >= (int64_t(1) << 31)) { err = "too many nodes"; return STOKES_E_INVAL; }
+        m.ncol = NX * NY;
+        m.col_of.resize(size_t(m.Nv));
+        m.pos_of.resize(size_t(m.Nv));
+        for (int64_t g = 0; g < m.Nv; ++g) { m.col_of[g] = int32_t(g % m.ncol); m.pos_of[g] = int32_t(g / m.ncol); }
     } else {
         std::vector<Key> keys;
         keys.reserve(size_t(E) * A);
@@ -223,6 +227,22 @@ int build_host_mesh(const stokes_mesh_desc& d, HostMesh& m, std::string& err) {
         uniq.erase(std::unique(uniq.begin(), uniq.end()), uniq.end());
         m.Nv = int64_t(uniq.size());
         if (m.Nv >= (int64_t(1) << 31)) { err = "too many nodes"; return STOKES_E_INVAL; }
+        {   // columns: distinct (Y, X) positions; nodes arrive in increasing Z
+            std::vector<std::pair<int64_t, int64_t>> yx(size_t(m.Nv));
+            for (int64_t g = 0; g < m.Nv; ++g) yx[g] = {uniq[g].y, uniq[g].x};
+            std::vector<std::pair<int64_t, int64_t>> cols = yx;
+            std::sort(cols.begin(), cols.end());
+            cols.erase(std::unique(cols.begin(), cols.end()), cols.end());
+            m.ncol = int64_t(cols.size());
+            m.col_of.resize(size_t(m.Nv));
+            m.pos_of.resize(size_t(m.Nv));
+            std::vector<int32_t> cnt(size_t(m.ncol), 0);
+            for (int64_t g = 0; g < m.Nv; ++g) {
+                int64_t c = int64_t(std::lower_bound(cols.begin(), cols.end(), yx[g]) - cols.begin());
+                m.col_of[g] = int32_t(c);
+                m.pos_of[g] = cnt[c]++;
+            }
+        }
         auto find = [&](const Key& kk) -> int64_t {
             auto it = std::lower_bound(uniq.begin(), uniq.end(), kk);
             if (it == uniq.end() || !(*it == kk)) return -1;
@@ -249,6 +269,29 @@ int build_host_mesh(const stokes_mesh_desc& d, HostMesh& m, std::string& err) {
                     }
         }
         if (bad) { err = "internal: hanging slot without a global node"; return STOKES_E_MESH; }
+    }
+
+    // ------------------------------------------------------- node columns
+    m.col_len.assign(size_t(m.ncol), 0);
+    for (int64_t g = 0; g < m.Nv; ++g) m.col_len[m.col_of[g]] = std::max(m.col_len[m.col_of[g]], m.pos_of[g] + 1);
+    m.colmax = 0;
+    for (int64_t c = 0; c < m.ncol; ++c) m.colmax = std::max(m.colmax, m.col_len[c]);
+    m.col_nodes.assign(size_t(m.colmax) * m.ncol, -1);
+    for (int64_t g = 0; g < m.Nv; ++g) m.col_nodes[size_t(m.pos_of[g]) * m.ncol + m.col_of[g]] = int32_t(g);
+    {
+        int bn = 0;
+        #pragma omp parallel for schedule(static) reduction(max : bn)
+        for (int64_t e = 0; e < E; ++e) {
+            for (int j = 0; j < n1; ++j)
+                for (int i = 0; i < n1; ++i)
+                    for (int l = 0; l < n1; ++l)
+                        for (int l2 = 0; l2 < n1; ++l2) {
+                            const int64_t a = m.elem_nodes[size_t(e) * A + slot(n1, i, j, l)];
+                            const int64_t b = m.elem_nodes[size_t(e) * A + slot(n1, i, j, l2)];
+                            if (m.col_of[a] == m.col_of[b]) bn = std::max(bn, std::abs(m.pos_of[a] - m.pos_of[b]));
+                        }
+        }
+        m.bnode = bn;
     }
 
     // ------------------------------------------------------------- geometry

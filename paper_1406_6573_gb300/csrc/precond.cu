@@ -1,0 +1,151 @@
+// Column-block factorisation and solves of the velocity-block preconditioner
+// (degree independent: the band width is a run-time value).
+//
+// Thin ice couples nodes far more strongly along a vertical column than across
+// columns (element aspect ratios 6 to 100 in the paper's meshes, Sections 4.3
+// and 7), so the velocity block is approximated by its vertical-column blocks,
+// each a banded SPD matrix factored exactly (LU without pivoting).  One thread
+// owns one column; band entries are stored column-interleaved so that the
+// threads of a warp touch consecutive addresses.
+#include <cuda_runtime.h>
+
+#include "precond.h"
+
+namespace stokes {
+namespace {
+
+template <typename T>
+__device__ __forceinline__ T& band(T* A, int64_t ncol, int W, int bw, int r, int q, int64_t c) {
+    return A[(int64_t(r) * W + (q - r + bw)) * ncol + c];
+}
+
+template <typename T>
+__global__ void col_factor_kernel(ColSolveArgs a) {
+    const int64_t c = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (c >= a.ncol) return;
+    T* A = static_cast<T*>(a.A);
+    const int bw = a.bw, W = 2 * bw + 1;
+    const int n = 3 * a.col_len[c];
+    const int b = a.col_basal[c];
+    if (b >= 0) {
+        // the lowest node of the column carries the nodal projector P:
+        // K <- P K P + (I - P) on its rows and columns
+        const double* p6 = a.basal_P + 6 * int64_t(b);
+        const T P[3][3] = {{T(p6[0]), T(p6[3]), T(p6[4])}, {T(p6[3]), T(p6[1]), T(p6[5])}, {T(p6[4]), T(p6[5]), T(p6[2])}};
+        const int qmax = min(n - 1, 2 + bw);
+        for (int q = 0; q <= qmax; ++q) {          // rows 0..2: P K
+            T v[3];
+            for (int r = 0; r < 3; ++r) v[r] = (q - r <= bw) ? band(A, a.ncol, W, bw, r, q, c) : T(0);
+            for (int r = 0; r < 3; ++r)
+                if (q - r <= bw) band(A, a.ncol, W, bw, r, q, c) = P[r][0] * v[0] + P[r][1] * v[1] + P[r][2] * v[2];
+        }
+        for (int r = 0; r <= qmax; ++r) {          // columns 0..2: K P
+            T v[3];
+            for (int q = 0; q < 3; ++q) v[q] = (r - q <= bw) ? band(A, a.ncol, W, bw, r, q, c) : T(0);
+            for (int q = 0; q < 3; ++q)
+                if (r - q <= bw) band(A, a.ncol, W, bw, r, q, c) = v[0] * P[0][q] + v[1] * P[1][q] + v[2] * P[2][q];
+        }
+        for (int r = 0; r < 3; ++r)
+            for (int q = 0; q < 3; ++q) band(A, a.ncol, W, bw, r, q, c) += (r == q ? T(1) : T(0)) - P[r][q];
+    }
+    for (int p = 0; p < n; ++p) {
+        const T piv = band(A, a.ncol, W, bw, p, p, c);
+        const T ipiv = T(1) / piv;
+        const int rmax = min(n - 1, p + bw);
+        for (int r = p + 1; r <= rmax; ++r) {
+            T& lrp = band(A, a.ncol, W, bw, r, p, c);
+            const T l = lrp * ipiv;
+            lrp = l;
+            if (l != T(0))
+                for (int q = p + 1; q <= rmax; ++q) band(A, a.ncol, W, bw, r, q, c) -= l * band(A, a.ncol, W, bw, p, q, c);
+        }
+    }
+}
+
+template <typename T>
+__global__ void col_solve_kernel(ColSolveArgs a, const T* __restrict__ rhs, T* __restrict__ z) {
+    extern __shared__ unsigned char smraw[];
+    T* zc = reinterpret_cast<T*>(smraw);       // [3 colmax][blockDim.x]
+    const int64_t c = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int nt = blockDim.x, t = threadIdx.x;
+    if (c >= a.ncol) return;
+    const T* A = static_cast<const T*>(a.A);
+    const int bw = a.bw, W = 2 * bw + 1;
+    const int len = a.col_len[c], n = 3 * len;
+    for (int p = 0; p < len; ++p) {
+        const int64_t g = a.col_nodes[int64_t(p) * a.ncol + c];
+        for (int k = 0; k < 3; ++k) zc[(3 * p + k) * nt + t] = rhs[3 * g + k];
+    }
+    for (int r = 1; r < n; ++r) {                // L y = r (unit lower)
+        T s = zc[r * nt + t];
+        for (int q = max(0, r - bw); q < r; ++q) s -= A[(int64_t(r) * W + (q - r + bw)) * a.ncol + c] * zc[q * nt + t];
+        zc[r * nt + t] = s;
+    }
+    for (int r = n - 1; r >= 0; --r) {           // U x = y
+        T s = zc[r * nt + t];
+        const int qmax = min(n - 1, r + bw);
+        for (int q = r + 1; q <= qmax; ++q) s -= A[(int64_t(r) * W + (q - r + bw)) * a.ncol + c] * zc[q * nt + t];
+        zc[r * nt + t] = s / A[(int64_t(r) * W + bw) * a.ncol + c];
+    }
+    for (int p = 0; p < len; ++p) {
+        const int64_t g = a.col_nodes[int64_t(p) * a.ncol + c];
+        for (int k = 0; k < 3; ++k) z[3 * g + k] = zc[(3 * p + k) * nt + t];
+    }
+}
+
+template <typename T>
+__global__ void schur_apply_kernel(int64_t Nv, int64_t Np, const T* __restrict__ md, const T* __restrict__ r,
+                                   T* __restrict__ z) {
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < Np; i += int64_t(gridDim.x) * blockDim.x)
+        z[3 * Nv + i] = -r[3 * Nv + i] / md[i];
+}
+
+int solve_threads(int colmax, int bytes) {
+    int nt = 128;
+    while (nt > 32 && int64_t(3) * colmax * nt * bytes > 96 * 1024) nt /= 2;
+    return nt;
+}
+
+}  // namespace
+
+int launch_col_factor(int prec, const ColSolveArgs& a, cudaStream_t s) {
+    if (a.ncol == 0) return 0;
+    const unsigned blocks = unsigned((a.ncol + 127) / 128);
+    if (prec == 1) col_factor_kernel<float><<<blocks, 128, 0, s>>>(a);
+    else col_factor_kernel<double><<<blocks, 128, 0, s>>>(a);
+    return int(cudaGetLastError());
+}
+
+int launch_col_solve(int prec, const ColSolveArgs& a, const void* r, void* z, cudaStream_t s) {
+    if (a.ncol == 0) return 0;
+    const int bytes = prec == 1 ? 4 : 8;
+    const int nt = solve_threads(a.colmax, bytes);
+    const size_t sm = size_t(3) * a.colmax * nt * bytes;
+    const unsigned blocks = unsigned((a.ncol + nt - 1) / nt);
+    cudaError_t e;
+    if (prec == 1) {
+        e = cudaFuncSetAttribute(col_solve_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+        if (e != cudaSuccess) return int(e);
+        col_solve_kernel<float><<<blocks, nt, sm, s>>>(a, static_cast<const float*>(r), static_cast<float*>(z));
+    } else {
+        e = cudaFuncSetAttribute(col_solve_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+        if (e != cudaSuccess) return int(e);
+        col_solve_kernel<double><<<blocks, nt, sm, s>>>(a, static_cast<const double*>(r), static_cast<double*>(z));
+    }
+    return int(cudaGetLastError());
+}
+
+int launch_schur_apply(int prec, int64_t Nv, int64_t Np, const void* md, const void* r, void* z, cudaStream_t s) {
+    if (Np == 0) return 0;
+    int64_t blocks = (Np + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    if (prec == 1)
+        schur_apply_kernel<float><<<unsigned(blocks), 256, 0, s>>>(Nv, Np, static_cast<const float*>(md),
+                                                                   static_cast<const float*>(r), static_cast<float*>(z));
+    else
+        schur_apply_kernel<double><<<unsigned(blocks), 256, 0, s>>>(Nv, Np, static_cast<const double*>(md),
+                                                                    static_cast<const double*>(r), static_cast<double*>(z));
+    return int(cudaGetLastError());
+}
+
+}  // namespace stokes

@@ -1,0 +1,156 @@
+// Degree-dependent parts of the block preconditioner (Section 4.2, Eq. 4.1):
+// assembly of the vertical-column blocks of the velocity block F from the
+// linearised state, and the diagonal of the 1/mu-weighted pressure mass
+// matrix (the Schur approximation -M(1/mu) of Section 6).
+// Included by k2.cu, k3.cu, k4.cu after elem_body.cuh.
+#pragma once
+
+#include "precond.h"
+
+namespace stokes {
+namespace dev {
+namespace STOKES_NS {
+
+// derivative of the GLL Lagrange polynomial i at Gauss point iq: (Dg B)[iq][i]
+template <typename T>
+__device__ __forceinline__ T Bd(int iq, int i) {
+    T s = 0;
+    #pragma unroll
+    for (int m = 0; m < Q; ++m) s += Tab<T>::Dg(iq, m) * Tab<T>::B(m, i);
+    return s;
+}
+
+// One thread per (element, slot a = (i, j, l)): the three rows of slot a
+// against every slot b = (i, j, l2) of the same element column, i.e. the
+// in-column couplings of the element velocity matrix
+//   K[(a,c),(b,c')] = sum_qp  muw/2 (delta_cc' grad phi_a . grad phi_b
+//                     + d_c' phi_a d_c phi_b) - (Dhat grad phi_a)_c (Dhat grad phi_b)_c'
+// (the bilinear form of Eq. 2.6 with the tensor of Eq. 2.7), plus the basal
+// Robin block of slot a with itself; accumulated into the banded column
+// matrices.  Hanging slots are skipped (the preconditioner ignores the
+// hanging-node couplings).
+template <typename T>
+__global__ void __launch_bounds__(256) colblock_kernel(ColArgs a) {
+    const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int64_t e = t / N3;
+    if (e >= a.E) return;
+    const int sl = int(t - e * N3);
+    const int i = sl % N1, j = (sl / N1) % N1, l = sl / N2;
+    const uint32_t h = a.hang[e];
+    const int idx[3] = {i, j, l};
+    if (slot_on_hanging_entity(h, idx, K)) return;
+    const int64_t na = a.nodes[e * N3 + sl];
+    const int col = a.col_of[na], pa = a.pos_of[na];
+    const T* st = static_cast<const T*>(a.state) + e * SSTRIDE;
+    const T ia = st[0], ib = st[1];
+    const int bw = a.bw, W = 2 * a.bw + 1;
+    T* A = static_cast<T*>(a.A);
+    for (int l2 = 0; l2 < N1; ++l2) {
+        const int idx2[3] = {i, j, l2};
+        if (slot_on_hanging_entity(h, idx2, K)) continue;
+        const int64_t nb = a.nodes[e * N3 + sidx(i, j, l2)];
+        if (a.col_of[nb] != col) continue;
+        const int pb = a.pos_of[nb];
+        T Kab[3][3] = {};
+        for (int lq = 0; lq < Q; ++lq)
+            for (int jq = 0; jq < Q; ++jq)
+                for (int iq = 0; iq < Q; ++iq) {
+                    const int qp = iq + Q * (jq + Q * lq);
+                    const T* f = st + 2 + qp;
+                    const T g0 = f[0], g1 = f[Q3], g2 = f[2 * Q3], muw = f[4 * Q3];
+                    const T D00 = f[5 * Q3], D11 = f[6 * Q3], D22 = f[7 * Q3];
+                    const T D01 = f[8 * Q3], D02 = f[9 * Q3], D12 = f[10 * Q3];
+                    const T bi = Tab<T>::B(iq, i), bj = Tab<T>::B(jq, j);
+                    const T dbi = Bd<T>(iq, i), dbj = Bd<T>(jq, j);
+                    const T ra[3] = {dbi * bj * Tab<T>::B(lq, l), bi * dbj * Tab<T>::B(lq, l), bi * bj * Bd<T>(lq, l)};
+                    const T rb[3] = {dbi * bj * Tab<T>::B(lq, l2), bi * dbj * Tab<T>::B(lq, l2), bi * bj * Bd<T>(lq, l2)};
+                    const T pa3[3] = {ra[0] * ia + ra[2] * g0, ra[1] * ib + ra[2] * g1, ra[2] * g2};
+                    const T pb3[3] = {rb[0] * ia + rb[2] * g0, rb[1] * ib + rb[2] * g1, rb[2] * g2};
+                    const T dot = pa3[0] * pb3[0] + pa3[1] * pb3[1] + pa3[2] * pb3[2];
+                    const T Da[3] = {D00 * pa3[0] + D01 * pa3[1] + D02 * pa3[2],
+                                     D01 * pa3[0] + D11 * pa3[1] + D12 * pa3[2],
+                                     D02 * pa3[0] + D12 * pa3[1] + D22 * pa3[2]};
+                    const T Db[3] = {D00 * pb3[0] + D01 * pb3[1] + D02 * pb3[2],
+                                     D01 * pb3[0] + D11 * pb3[1] + D12 * pb3[2],
+                                     D02 * pb3[0] + D12 * pb3[1] + D22 * pb3[2]};
+                    const T hm = T(0.5) * muw;
+                    #pragma unroll
+                    for (int c = 0; c < 3; ++c)
+                        #pragma unroll
+                        for (int c2 = 0; c2 < 3; ++c2)
+                            Kab[c][c2] += hm * ((c == c2 ? dot : T(0)) + pa3[c2] * pb3[c]) - Da[c] * Db[c2];
+                }
+        // basal Robin term of slot a with itself
+        if (l == 0 && l2 == 0 && a.robin && a.fidx[e] >= 0) {
+            const int64_t fcs = a.fidx[e];
+            for (int jq = 0; jq < Q; ++jq)
+                for (int iq = 0; iq < Q; ++iq) {
+                    const int fq = iq + Q * jq;
+                    T lbq = 0;
+                    for (int j2 = 0; j2 < N1; ++j2)
+                        for (int i2 = 0; i2 < N1; ++i2)
+                            lbq += Tab<T>::B(iq, i2) * Tab<T>::B(jq, j2) * T(a.logbeta[a.fmap[fcs * N2 + i2 + N1 * j2]]);
+                    const double* fg = a.fgeo + fcs * 4 * Q * Q + fq;
+                    const T phi = Tab<T>::B(iq, i) * Tab<T>::B(jq, j);
+                    const T w = exp(lbq) * T(fg[0]) * phi * phi;
+                    const T n[3] = {T(fg[Q * Q]), T(fg[2 * Q * Q]), T(fg[3 * Q * Q])};
+                    #pragma unroll
+                    for (int c = 0; c < 3; ++c)
+                        #pragma unroll
+                        for (int c2 = 0; c2 < 3; ++c2) Kab[c][c2] += w * ((c == c2 ? T(1) : T(0)) - n[c] * n[c2]);
+                }
+        }
+        #pragma unroll
+        for (int c = 0; c < 3; ++c)
+            #pragma unroll
+            for (int c2 = 0; c2 < 3; ++c2) {
+                const int r = 3 * pa + c, q = 3 * pb + c2;
+                atomic_add(A + (int64_t(r) * W + (q - r + bw)) * a.ncol + col, Kab[c][c2]);
+            }
+    }
+}
+
+// md[e npr + b] = sum_qp psi_b(qp)^2 w detJ / mu   (diagonal of M(1/mu))
+template <typename T>
+__global__ void __launch_bounds__(256) schur_diag_kernel(ColArgs a) {
+    const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int64_t e = t / a.npr;
+    if (e >= a.E) return;
+    const int b = int(t - e * a.npr);
+    const int ps = a.pspace;
+    const int m0 = cPm[ps][b][0], m1 = cPm[ps][b][1], m2 = cPm[ps][b][2];
+    const T* st = static_cast<const T*>(a.state) + e * SSTRIDE;
+    T s = 0;
+    for (int lq = 0; lq < Q; ++lq)
+        for (int jq = 0; jq < Q; ++jq)
+            for (int iq = 0; iq < Q; ++iq) {
+                const int qp = iq + Q * (jq + Q * lq);
+                const T wdj = st[2 + 3 * Q3 + qp], muw = st[2 + 4 * Q3 + qp];
+                const T psi = Tab<T>::P1(ps, iq, m0) * Tab<T>::P1(ps, jq, m1) * Tab<T>::P1(ps, lq, m2);
+                s += psi * psi * wdj * wdj / muw;
+            }
+    static_cast<T*>(a.md)[t] = s;
+}
+
+template <typename T>
+int launch_precond_assembly_t(const ColArgs& a, cudaStream_t s) {
+    if (a.E == 0) return int(cudaSuccess);
+    const int64_t n1 = a.E * N3, n2 = a.E * a.npr;
+    colblock_kernel<T><<<unsigned((n1 + 255) / 256), 256, 0, s>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return int(e);
+    schur_diag_kernel<T><<<unsigned((n2 + 255) / 256), 256, 0, s>>>(a);
+    return int(cudaGetLastError());
+}
+
+}  // namespace STOKES_NS
+}  // namespace dev
+}  // namespace stokes
+
+#define STOKES_DEFINE_PRECOND(KK)                                                              \
+    namespace stokes {                                                                         \
+    int launch_precond_assembly_k##KK(int prec, const ColArgs& a, cudaStream_t s) {            \
+        return prec == 1 ? dev::STOKES_NS::launch_precond_assembly_t<float>(a, s)              \
+                         : dev::STOKES_NS::launch_precond_assembly_t<double>(a, s);            \
+    }                                                                                          \
+    }

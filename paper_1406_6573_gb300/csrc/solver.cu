@@ -1,0 +1,392 @@
+// Inexact Newton-Krylov driver on device vectors (Section 4).
+//
+//  * Newton (Section 4.1): the FP64 residual of Eq. 2.5, the Jacobian of
+//    Eqs. 2.6-2.7 from the linearised state, backtracking on ||r||_2 so that
+//    the residual decreases, Eisenstat-Walker forcing (choice 2) for the
+//    inexact linear solves.
+//  * Krylov (Section 4.2): right-preconditioned flexible GMRES(m) with the
+//    block upper-triangular preconditioner of Eq. 4.1, F~ = vertical-column
+//    blocks of F, S~ = -diag M(1/mu) (Section 6).  Classical Gram-Schmidt
+//    with FP64 accumulation, one reorthogonalisation pass when the norm drops
+//    by more than a factor 0.7.
+//  * Mixed precision: with inner precision FP32 the Krylov vectors, the
+//    operator applies and the preconditioner run in FP32; every restart
+//    recomputes the linear residual in FP64 with the FP64 state (iterative
+//    refinement), so the FP64 Newton update can be resolved below FP32
+//    round-off.  With inner precision FP64 the same loop is plain FP64.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "handles.h"
+#include "vec.h"
+
+using namespace stokes;
+
+struct stokes_solver {
+    const stokes_mesh* mesh = nullptr;
+    stokes_solver_opts o{};
+    int inner = STOKES_F32;
+    stokes_state* st_in = nullptr;
+    stokes_state* st64 = nullptr;
+    int64_t n = 0, nu = 0;
+    size_t isz = 4;
+    double *r = nullptr, *dl = nullptr, *rl = nullptr, *trial = nullptr, *rt = nullptr, *tmp64 = nullptr;
+    void *V = nullptr, *Z = nullptr, *tin = nullptr, *tz = nullptr;
+    void *A = nullptr, *md = nullptr;
+    double* dsc = nullptr;             // device scalars
+    size_t band_elems = 0;
+    int bw = 0;
+};
+
+namespace {
+
+template <typename T>
+void dfree(T*& p) {
+    if (p) cudaFree(reinterpret_cast<void*>(p));
+    p = nullptr;
+}
+
+void free_solver(stokes_solver* s) {
+    dfree(s->r); dfree(s->dl); dfree(s->rl); dfree(s->trial); dfree(s->rt); dfree(s->tmp64);
+    dfree(s->V); dfree(s->Z); dfree(s->tin); dfree(s->tz); dfree(s->A); dfree(s->md); dfree(s->dsc);
+    if (s->st_in) stokes_state_destroy(s->st_in);
+    if (s->st64 && s->st64 != s->st_in) stokes_state_destroy(s->st64);
+    s->st_in = s->st64 = nullptr;
+}
+
+#define CK(call)                                                    \
+    do {                                                            \
+        int rc_ = (call);                                           \
+        if (rc_) return rc_;                                        \
+    } while (0)
+#define CU(call, what)                                              \
+    do {                                                            \
+        int e_ = int(call);                                         \
+        if (e_) return cuda_fail(cudaError_t(e_), what);            \
+    } while (0)
+
+// ||x||_2 of an FP64 device vector (synchronises)
+int norm64(stokes_solver* S, const double* x, int64_t n, double& out, cudaStream_t st) {
+    CU(vec_multidot(n, STOKES_F64, x, 0, 1, STOKES_F64, x, S->dsc, st), "norm");
+    double h = 0;
+    CU(cudaMemcpyAsync(&h, S->dsc, sizeof(double), cudaMemcpyDeviceToHost, st), "norm readback");
+    CU(cudaStreamSynchronize(st), "norm sync");
+    out = std::sqrt(h);
+    return STOKES_OK;
+}
+
+int op_inner(stokes_solver* S, const void* x, void* y, bool trans, cudaStream_t st) {
+    return trans ? stokes_state_apply_transpose(S->st_in, x, y, st) : stokes_state_apply(S->st_in, x, y, st);
+}
+
+int op64(stokes_solver* S, const double* x, double* y, bool trans, cudaStream_t st) {
+    return trans ? stokes_state_apply_transpose(S->st64, x, y, st) : stokes_state_apply(S->st64, x, y, st);
+}
+
+ColSolveArgs colsolve_args(stokes_solver* S) {
+    const stokes_mesh* m = S->mesh;
+    ColSolveArgs c{};
+    c.ncol = m->h.ncol; c.Nv = m->h.Nv; c.colmax = m->h.colmax; c.bw = S->bw;
+    c.col_nodes = m->d_col_nodes; c.col_len = m->d_col_len; c.col_basal = m->d_col_basal;
+    c.basal_P = m->d_basal_P; c.A = S->A;
+    return c;
+}
+
+// preconditioner set-up from the inner state: column blocks of F, their
+// factorisation, and the Schur diagonal
+int precond_setup(stokes_solver* S, const stokes_params* p, cudaStream_t st) {
+    const stokes_mesh* m = S->mesh;
+    CU(cudaMemsetAsync(S->A, 0, S->band_elems * S->isz, st), "clearing column blocks");
+    ColArgs a{};
+    a.E = m->h.E; a.ncol = m->h.ncol; a.npr = m->h.npr; a.pspace = m->h.pspace; a.bw = S->bw;
+    a.robin = p->robin && m->h.nF > 0;
+    a.nodes = m->d_nodes; a.hang = m->d_hang; a.col_of = m->d_col_of; a.pos_of = m->d_pos_of;
+    a.fidx = m->d_fidx; a.fmap = m->d_fmap; a.fgeo = m->d_fgeo; a.logbeta = p->logbeta;
+    a.state = S->st_in->d_state; a.A = S->A; a.md = S->md;
+    CU(launch_precond_assembly(m->h.k, S->inner, a, st), "preconditioner assembly");
+    CU(launch_col_factor(S->inner, colsolve_args(S), st), "column factorisation");
+    return STOKES_OK;
+}
+
+// z = M^{-1} v  (inner precision):  z_p = -v_p / md,  z_u = F~^{-1}(v_u - B^T z_p)
+int precond_apply(stokes_solver* S, const void* v, void* z, cudaStream_t st) {
+    const stokes_mesh* m = S->mesh;
+    CU(launch_schur_apply(S->inner, m->h.Nv, m->h.Np, S->md, v, z, st), "Schur apply");
+    CK(state_gradp(S->st_in, z, S->tz, st));
+    CU(vec_axpby(S->nu, 1.0, nullptr, S->inner, v, -1.0, S->inner, S->tz, st), "preconditioner update");
+    CU(launch_col_solve(S->inner, colsolve_args(S), S->tz, z, st), "column solve");
+    return STOKES_OK;
+}
+
+// One FGMRES(m) cycle on A x = b with b = tin (inner precision), x0 = 0.
+// Adds Z y to the FP64 vector dl.  Returns the number of iterations in its.
+int fgmres_cycle(stokes_solver* S, bool trans, double tol_rel, int max_its, int& its, cudaStream_t st) {
+    const int64_t n = S->n;
+    const int m = std::min(S->o.restart, max_its);
+    const int ip = S->inner;
+    const size_t isz = S->isz;
+    auto Vj = [&](int j) { return static_cast<char*>(S->V) + size_t(j) * n * isz; };
+    auto Zj = [&](int j) { return static_cast<char*>(S->Z) + size_t(j) * n * isz; };
+    std::vector<double> H(size_t(m + 1) * m, 0.0), cs(m, 0.0), sn(m, 0.0), g(m + 1, 0.0), h(m + 2, 0.0);
+    // V_0 = b / ||b||
+    CU(vec_axpby(n, 1.0, nullptr, ip, S->tin, 0.0, ip, Vj(0), st), "copy");
+    CU(vec_multidot(n, ip, Vj(0), 0, 1, ip, Vj(0), S->dsc, st), "dot");
+    CU(cudaMemcpyAsync(h.data(), S->dsc, sizeof(double), cudaMemcpyDeviceToHost, st), "readback");
+    CU(cudaStreamSynchronize(st), "sync");
+    const double beta = std::sqrt(h[0]);
+    its = 0;
+    if (!(beta > 0)) return STOKES_OK;
+    CU(vec_normalize(n, ip, Vj(0), S->dsc, st), "normalize");
+    g[0] = beta;
+    int k = 0;
+    for (; k < m; ++k) {
+        CK(precond_apply(S, Vj(k), Zj(k), st));
+        CK(op_inner(S, Zj(k), Vj(k + 1), trans, st));
+        // classical Gram-Schmidt, FP64 accumulation: h = V^T w and ||w||^2
+        CU(vec_multidot(n, ip, S->V, n, k + 1, ip, Vj(k + 1), S->dsc, st), "orthogonalisation dots");
+        CU(vec_multidot(n, ip, Vj(k + 1), 0, 1, ip, Vj(k + 1), S->dsc + (k + 1), st), "norm");
+        CU(cudaMemcpyAsync(h.data(), S->dsc, sizeof(double) * (k + 2), cudaMemcpyDeviceToHost, st), "readback");
+        CU(cudaStreamSynchronize(st), "sync");
+        const double wn0 = std::sqrt(h[k + 1]);
+        CU(vec_multiaxpy(n, ip, Vj(k + 1), S->V, n, k + 1, S->dsc, S->dsc + (m + 1), st), "orthogonalisation");
+        double hn2 = 0;
+        CU(cudaMemcpyAsync(&hn2, S->dsc + (m + 1), sizeof(double), cudaMemcpyDeviceToHost, st), "readback");
+        CU(cudaStreamSynchronize(st), "sync");
+        for (int i = 0; i <= k; ++i) H[size_t(i) * m + k] = h[i];
+        if (std::sqrt(hn2) < 0.7 * wn0) {
+            // second Gram-Schmidt pass
+            CU(vec_multidot(n, ip, S->V, n, k + 1, ip, Vj(k + 1), S->dsc, st), "reorthogonalisation dots");
+            CU(cudaMemcpyAsync(h.data(), S->dsc, sizeof(double) * (k + 1), cudaMemcpyDeviceToHost, st), "readback");
+            CU(vec_multiaxpy(n, ip, Vj(k + 1), S->V, n, k + 1, S->dsc, S->dsc + (m + 1), st), "reorthogonalisation");
+            CU(cudaMemcpyAsync(&hn2, S->dsc + (m + 1), sizeof(double), cudaMemcpyDeviceToHost, st), "readback");
+            CU(cudaStreamSynchronize(st), "sync");
+            for (int i = 0; i <= k; ++i) H[size_t(i) * m + k] += h[i];
+        }
+        const double hk1 = std::sqrt(hn2);
+        if (hk1 > 0) CU(vec_normalize(n, ip, Vj(k + 1), S->dsc + (m + 1), st), "normalize");
+        // Givens rotations on column k
+        for (int i = 0; i < k; ++i) {
+            const double a = H[size_t(i) * m + k], b = H[size_t(i + 1) * m + k];
+            H[size_t(i) * m + k] = cs[i] * a + sn[i] * b;
+            H[size_t(i + 1) * m + k] = -sn[i] * a + cs[i] * b;
+        }
+        const double a = H[size_t(k) * m + k];
+        const double rr = std::hypot(a, hk1);
+        cs[k] = rr > 0 ? a / rr : 1.0;
+        sn[k] = rr > 0 ? hk1 / rr : 0.0;
+        H[size_t(k) * m + k] = rr;
+        g[k + 1] = -sn[k] * g[k];
+        g[k] = cs[k] * g[k];
+        ++its;
+        if (std::fabs(g[k + 1]) <= tol_rel * beta || hk1 == 0) { ++k; break; }
+    }
+    // y = H^{-1} g (upper triangular k x k), dl += Z y
+    std::vector<double> y(k, 0.0);
+    for (int i = k - 1; i >= 0; --i) {
+        double s = g[i];
+        for (int j = i + 1; j < k; ++j) s -= H[size_t(i) * m + j] * y[j];
+        y[i] = s / H[size_t(i) * m + i];
+    }
+    CU(cudaMemcpyAsync(S->dsc, y.data(), sizeof(double) * k, cudaMemcpyHostToDevice, st), "coefficients");
+    CU(vec_combine(n, ip, S->Z, n, k, S->dsc, STOKES_F64, S->dl, st), "update");
+    CU(cudaStreamSynchronize(st), "sync");
+    return STOKES_OK;
+}
+
+// Solve J dl = rhs (FP64 device rhs) to ||rhs - J dl|| <= eta ||rhs||; dl and rl
+// (final linear residual) are FP64.  Operators/preconditioner from the
+// current states.
+int linear_solve(stokes_solver* S, const double* rhs, double nrhs, double eta, bool trans, int& its_total,
+                 cudaStream_t st) {
+    const int64_t n = S->n;
+    CU(cudaMemsetAsync(S->dl, 0, sizeof(double) * n, st), "clear");
+    CU(vec_axpby(n, 1.0, nullptr, STOKES_F64, rhs, 0.0, STOKES_F64, S->rl, st), "copy");
+    double nrl = nrhs;
+    its_total = 0;
+    const double floor_rel = S->inner == STOKES_F32 ? 1e-5 : 1e-13;
+    while (its_total < S->o.max_krylov && nrl > eta * nrhs) {
+        CU(vec_axpby(n, 1.0, nullptr, STOKES_F64, S->rl, 0.0, S->inner, S->tin, st), "to inner precision");
+        const double tol = std::max(eta * nrhs / nrl, floor_rel);
+        int its = 0;
+        CK(fgmres_cycle(S, trans, tol, S->o.max_krylov - its_total, its, st));
+        its_total += its;
+        // FP64 residual of the accumulated update (iterative refinement)
+        CK(op64(S, S->dl, S->tmp64, trans, st));
+        CU(vec_axpby(n, 1.0, nullptr, STOKES_F64, rhs, 0.0, STOKES_F64, S->rl, st), "residual");
+        CU(vec_axpby(n, -1.0, nullptr, STOKES_F64, S->tmp64, 1.0, STOKES_F64, S->rl, st), "residual");
+        CK(norm64(S, S->rl, n, nrl, st));
+        if (its == 0) break;
+    }
+    return STOKES_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int stokes_solver_create(const stokes_mesh* mesh, const stokes_solver_opts* opts, stokes_solver** out) {
+    int rc = check_common(mesh, STOKES_F64);
+    if (rc) return rc;
+    if (!out) return fail(STOKES_E_INVAL, "out is NULL");
+    *out = nullptr;
+    stokes_solver* S = new (std::nothrow) stokes_solver();
+    if (!S) return fail(STOKES_E_NOMEM, "host allocation failed");
+    S->mesh = mesh;
+    stokes_solver_opts o{STOKES_F32, 30, 1000, 50, 1e-10, 0.1};
+    if (opts) o = *opts;
+    if (o.restart < 1) o.restart = 30;
+    if (o.max_krylov < 1) o.max_krylov = 1000;
+    if (o.max_newton < 1) o.max_newton = 50;
+    if (!(o.rtol > 0)) o.rtol = 1e-10;
+    if (!(o.eta_max > 0)) o.eta_max = 0.1;
+    if (o.inner_prec != STOKES_F32 && o.inner_prec != STOKES_F64) { delete S; return fail(STOKES_E_INVAL, "inner_prec"); }
+    S->o = o;
+    S->inner = o.inner_prec;
+    S->isz = S->inner == STOKES_F32 ? 4 : 8;
+    S->n = 3 * mesh->h.Nv + mesh->h.Np;
+    S->nu = 3 * mesh->h.Nv;
+    S->bw = 3 * mesh->h.bnode + 2;
+    DeviceGuard g(mesh->device);
+    if (g.err != cudaSuccess) { delete S; return cuda_fail(g.err, "selecting the device"); }
+    rc = stokes_state_create(mesh, S->inner, &S->st_in);
+    if (rc == STOKES_OK) {
+        if (S->inner == STOKES_F64) S->st64 = S->st_in;
+        else rc = stokes_state_create(mesh, STOKES_F64, &S->st64);
+    }
+    const size_t n = size_t(S->n);
+    S->band_elems = size_t(3) * mesh->h.colmax * size_t(2 * S->bw + 1) * size_t(mesh->h.ncol);
+    auto alloc = [&](void** p, size_t bytes) {
+        if (rc) return;
+        if (cudaMalloc(p, bytes) != cudaSuccess) { *p = nullptr; rc = fail(STOKES_E_NOMEM, "solver workspace"); }
+    };
+    alloc(reinterpret_cast<void**>(&S->r), n * 8);
+    alloc(reinterpret_cast<void**>(&S->dl), n * 8);
+    alloc(reinterpret_cast<void**>(&S->rl), n * 8);
+    alloc(reinterpret_cast<void**>(&S->trial), n * 8);
+    alloc(reinterpret_cast<void**>(&S->rt), n * 8);
+    alloc(reinterpret_cast<void**>(&S->tmp64), n * 8);
+    alloc(&S->V, n * S->isz * size_t(o.restart + 1));
+    alloc(&S->Z, n * S->isz * size_t(o.restart));
+    alloc(&S->tin, n * S->isz);
+    alloc(&S->tz, n * S->isz);
+    alloc(&S->A, S->band_elems * S->isz);
+    alloc(&S->md, std::max<size_t>(1, size_t(mesh->h.Np)) * S->isz);
+    alloc(reinterpret_cast<void**>(&S->dsc), sizeof(double) * size_t(o.restart + 8));
+    if (rc) { free_solver(S); delete S; return rc; }
+    *out = S;
+    return STOKES_OK;
+}
+
+int stokes_solver_destroy(stokes_solver* solver) {
+    if (!solver) return STOKES_OK;
+    DeviceGuard g(solver->mesh->device);
+    free_solver(solver);
+    delete solver;
+    return STOKES_OK;
+}
+
+int stokes_newton_solve(stokes_solver* S, const stokes_params* params, double* up, stokes_solve_report* rep,
+                        void* stream) {
+    if (!S) return fail(STOKES_E_INVAL, "solver is NULL");
+    const stokes_mesh* mesh = S->mesh;
+    int rc = check_params(mesh, params);
+    if (rc) return rc;
+    if (!up) return fail(STOKES_E_INVAL, "up is NULL");
+    DeviceGuard g(mesh->device);
+    if (g.err != cudaSuccess) return cuda_fail(g.err, "selecting the device");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int64_t n = S->n;
+    stokes_solve_report R{};
+    auto t0 = std::chrono::steady_clock::now();
+    CK(stokes_residual(mesh, params, up, S->r, STOKES_F64, st));
+    double nr = 0;
+    CK(norm64(S, S->r, n, nr, st));
+    const double nr0 = nr;
+    R.res0 = nr0;
+    R.history[0] = nr0;
+    double eta = S->o.eta_max, nr_prev = nr;
+    int k = 0;
+    for (; k < S->o.max_newton; ++k) {
+        if (nr <= S->o.rtol * nr0) { R.converged = 1; break; }
+        if (k > 0) {   // Eisenstat-Walker choice 2 with safeguards
+            const double ratio = nr / nr_prev;
+            double e2 = 0.9 * ratio * ratio;
+            const double safe = 0.9 * eta * eta;
+            if (safe > 0.1) e2 = std::max(e2, safe);
+            eta = std::min(e2, S->o.eta_max);
+            eta = std::max(eta, 0.5 * S->o.rtol * nr0 / nr);
+        }
+        CK(stokes_linearize(S->st_in, params, up, st));
+        if (S->st64 != S->st_in) CK(stokes_linearize(S->st64, params, up, st));
+        CK(precond_setup(S, params, st));
+        // rhs = -r
+        CU(vec_axpby(n, -1.0, nullptr, STOKES_F64, S->r, 0.0, STOKES_F64, S->trial, st), "rhs");
+        int its = 0;
+        CK(linear_solve(S, S->trial, nr, eta, false, its, st));
+        R.krylov_its += its;
+        if (k < 64) R.krylov_per_newton[k] = its;
+        // backtracking line search on ||r||
+        double alpha = 1.0, nrt = 0;
+        for (int cut = 0;; ++cut) {
+            CU(vec_axpby(n, 1.0, nullptr, STOKES_F64, up, 0.0, STOKES_F64, S->trial, st), "trial");
+            CU(vec_axpby(n, alpha, nullptr, STOKES_F64, S->dl, 1.0, STOKES_F64, S->trial, st), "trial");
+            CK(stokes_residual(mesh, params, S->trial, S->rt, STOKES_F64, st));
+            CK(norm64(S, S->rt, n, nrt, st));
+            if (nrt <= (1.0 - 1e-4 * alpha) * nr || cut >= 12) break;
+            alpha *= 0.5;
+            R.line_search_cuts++;
+        }
+        CU(cudaMemcpyAsync(up, S->trial, sizeof(double) * n, cudaMemcpyDeviceToDevice, st), "update");
+        CU(cudaMemcpyAsync(S->r, S->rt, sizeof(double) * n, cudaMemcpyDeviceToDevice, st), "update");
+        nr_prev = nr;
+        nr = nrt;
+        if (k + 1 < 64) R.history[k + 1] = nr;
+    }
+    if (nr <= S->o.rtol * nr0) R.converged = 1;
+    CU(cudaStreamSynchronize(st), "sync");
+    R.newton_its = k;
+    R.res_final = nr;
+    R.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (rep) *rep = R;
+    return R.converged ? STOKES_OK : fail(STOKES_E_NOCONV, "Newton did not reach rtol");
+}
+
+int stokes_linear_solve(stokes_solver* S, const stokes_params* params, const double* up_lin, const double* b,
+                        double* x, int transpose, double rtol, stokes_solve_report* rep, void* stream) {
+    if (!S) return fail(STOKES_E_INVAL, "solver is NULL");
+    const stokes_mesh* mesh = S->mesh;
+    int rc = check_params(mesh, params);
+    if (rc) return rc;
+    if (!up_lin || !b || !x) return fail(STOKES_E_INVAL, "up_lin, b and x must be non-NULL");
+    DeviceGuard g(mesh->device);
+    if (g.err != cudaSuccess) return cuda_fail(g.err, "selecting the device");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int64_t n = S->n;
+    stokes_solve_report R{};
+    auto t0 = std::chrono::steady_clock::now();
+    CK(stokes_linearize(S->st_in, params, up_lin, st));
+    if (S->st64 != S->st_in) CK(stokes_linearize(S->st64, params, up_lin, st));
+    CK(precond_setup(S, params, st));
+    double nb = 0;
+    CK(norm64(S, b, n, nb, st));
+    int its = 0;
+    CK(linear_solve(S, b, nb, rtol, transpose != 0, its, st));
+    CU(cudaMemcpyAsync(x, S->dl, sizeof(double) * n, cudaMemcpyDeviceToDevice, st), "solution");
+    double nrl = 0;
+    CK(norm64(S, S->rl, n, nrl, st));
+    R.krylov_its = its;
+    R.res0 = nb;
+    R.res_final = nrl;
+    R.converged = nrl <= rtol * nb;
+    R.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (rep) *rep = R;
+    return R.converged ? STOKES_OK : fail(STOKES_E_NOCONV, "Krylov solve did not reach rtol");
+}
+
+}  // extern "C"

@@ -1,0 +1,77 @@
+"""GPU Newton-Krylov solver (Section 4) against the oracle.
+
+The discrete solution is unique (Appendix A), so the end points must agree:
+the oracle's own residual evaluated at the GPU solution must be below 1e-10
+of the oracle's initial residual (the Newton stopping rule), for the plain
+FP64 and the FP32-inner / FP64-outer solver.  Linear solves are checked with
+the oracle's Jacobian: ||b - J x|| <= rtol ||b||, for J and J^T.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import stokes_synth as synth
+from oracle import OracleMesh, stokes as ostokes
+from paper_1406_6573_gb300 import capi
+from paper_1406_6573_gb300.mesh import Mesh, params
+
+
+def _setup(name):
+    wl = synth.workload(name)
+    o = OracleMesh(wl)
+    m = Mesh(wl, device=0)
+    lb = np.zeros(o.Nb) if wl.phys.logbeta is None else wl.phys.logbeta(*o.basal_coords()[:, :2].T)
+    return wl, o, m, lb
+
+
+def _opts(inner, rtol=1e-11):
+    op = capi.stokes_solver_opts()
+    op.inner_prec = inner
+    op.restart = 30
+    op.max_krylov = 3000
+    op.max_newton = 60
+    op.rtol = rtol
+    op.eta_max = 0.1
+    return op
+
+
+@pytest.mark.parametrize("name", ["box_4x4x2_q2p1", "slab_5x3x3_q2p1", "cforest_3x3x2_q2p1"])
+@pytest.mark.parametrize("inner", [capi.STOKES_F64, capi.STOKES_F32])
+def test_newton_reaches_oracle_solution(name, inner):
+    wl, o, m, lb = _setup(name)
+    lbd = torch.as_tensor(lb, dtype=torch.float64, device="cuda")
+    p = params(wl.phys, lbd)
+    s = capi.stokes_solver_create(m.handle, _opts(inner))
+    try:
+        up = torch.zeros(o.ndof, dtype=torch.float64, device="cuda")
+        rc, rep = capi.stokes_newton_solve(s, p, up)
+        assert rc == 0 and rep["converged"], rep
+        r0 = np.linalg.norm(ostokes.residual(o, wl.phys, np.zeros(o.ndof), lb))
+        r = np.linalg.norm(ostokes.residual(o, wl.phys, up.cpu().numpy(), lb))
+        assert r <= 1e-10 * r0, (r / r0, rep)
+    finally:
+        capi.stokes_solver_destroy(s)
+
+
+@pytest.mark.parametrize("transpose", [False, True])
+@pytest.mark.parametrize("inner,rtol", [(capi.STOKES_F64, 1e-10), (capi.STOKES_F32, 1e-9)])
+def test_linear_solve(transpose, inner, rtol):
+    wl, o, m, lb = _setup("slab_8x8x2_q2p1")
+    lbd = torch.as_tensor(lb, dtype=torch.float64, device="cuda")
+    p = params(wl.phys, lbd)
+    up = synth.uniform_vector(21, o.ndof) * np.concatenate([np.full(3 * o.Nv, 100.0), np.full(o.Np, 1e5)])
+    b = synth.uniform_vector(21, o.ndof, stream=1)
+    s = capi.stokes_solver_create(m.handle, _opts(inner))
+    try:
+        x = torch.zeros(o.ndof, dtype=torch.float64, device="cuda")
+        rc, rep = capi.stokes_linear_solve(s, p, torch.as_tensor(up, device="cuda"),
+                                           torch.as_tensor(b, device="cuda"), x, transpose, rtol)
+        assert rc == 0, rep
+        xx = x.cpu().numpy()
+        # J is symmetric (Section 4.1), so J^T x = J x in the oracle
+        res = b - ostokes.jacobian_apply(o, wl.phys, up, xx, lb)
+        assert np.linalg.norm(res) <= 1.01 * rtol * np.linalg.norm(b), (np.linalg.norm(res) / np.linalg.norm(b), rep)
+    finally:
+        capi.stokes_solver_destroy(s)
