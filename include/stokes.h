@@ -41,8 +41,9 @@
  *     crosses the ABI.
  *   - Constraints: basal nodes carry the nodal projector P (P = 0 for no-slip;
  *     P = I - n n^T for u . n = 0, n the normalised area-weighted nodal normal).
- *     The residual evaluated is r_c(u) = P r(P u) + (I - P) u and the Jacobian
- *     P J(P u) P + (I - P), its exact derivative.
+ *     The residual evaluated is r_c(u) = P r(P u) + s (I - P) u and the
+ *     Jacobian P J(P u) P + s (I - P), its exact derivative
+ *     (s = params->constraint_scale).
  */
 #ifndef STOKES_GB300_H
 #define STOKES_GB300_H
@@ -109,6 +110,12 @@ typedef struct {
     const double* logbeta;        /* DEVICE, [Nb] FP64 nodal log(beta) at the
                                      basal nodes (ascending global node order);
                                      required when robin = 1                   */
+    double constraint_scale;      /* s > 0 of the constraint rows: the operator
+                                     is P J P + s (I - P) and the residual
+                                     P r(P u) + s (I - P) u; the solution does
+                                     not depend on s.  1 = plain projector;
+                                     the solver picks s ~ the diagonal of J so
+                                     that FP32 arithmetic resolves these rows. */
 } stokes_params;
 
 typedef struct {
@@ -206,6 +213,7 @@ typedef struct {
 typedef struct {
     int converged, newton_its, krylov_its, line_search_cuts;
     double res0, res_final, seconds;
+    double constraint_scale;     /* s used by stokes_newton_solve (see stokes_params) */
     double history[64];          /* ||r_j||, j = 0 .. newton_its (first 64)          */
     int krylov_per_newton[64];
 } stokes_solve_report;
@@ -213,6 +221,9 @@ typedef struct {
 int stokes_solver_create(const stokes_mesh* mesh, const stokes_solver_opts* opts, stokes_solver** out);
 int stokes_solver_destroy(stokes_solver* solver);
 /* Solve r_c(up) = 0 starting from the device FP64 state up (overwritten).
+ * The solver replaces params->constraint_scale by the mean diagonal of the
+ * velocity block at the first linearisation (reported in the report); the
+ * residual norms it reports use that scale.
  * Returns STOKES_E_NOCONV (report filled) if rtol is not reached. */
 int stokes_newton_solve(stokes_solver* solver, const stokes_params* params, double* up,
                         stokes_solve_report* report, void* stream);

@@ -73,7 +73,7 @@ def projector_matrix(mesh):
 
 
 def assemble_jacobian(mesh, phys, up, logbeta=None):
-    """Constrained global Jacobian P (sum_i R_i^T A_i R_i) P + (I - P), sparse."""
+    """Constrained global Jacobian P (sum_i R_i^T A_i R_i) P + s (I - P), sparse."""
     K = element_matrices(mesh, phys, up, logbeta)
     E, nde = K.shape[0], K.shape[1]
     e, i, j = np.meshgrid(np.arange(E), np.arange(nde), np.arange(nde), indexing="ij")
@@ -83,7 +83,7 @@ def assemble_jacobian(mesh, phys, up, logbeta=None):
     J = (Rf.T @ Kb @ Rf).tocsr()
     P = projector_matrix(mesh)
     I = sp.identity(mesh.ndof, format="csr")
-    return (P @ J @ P + (I - P)).tocsr()
+    return (P @ J @ P + phys.constraint_scale * (I - P)).tocsr()
 
 
 def newton_solve(mesh, phys, logbeta=None, rtol=1e-10, maxit=60, up0=None, verbose=False):

@@ -17,8 +17,9 @@ factorisation, no fusion):
       mu'(u) E = mu (E + 2 gamma p_n (D(u):E) / (gamma D(u):D(u) + delta) D(u)),
       p_n = (1 - n) / (2n)
   constraints at the basal nodes (no-slip or u . n = 0, Eq. 2.4b): nodal
-  projector P, constrained residual r_c(u) = P r(P u) + (I - P) u and its
-  exact Jacobian P J(P u) P + (I - P).
+  projector P, constrained residual r_c(u) = P r(P u) + s (I - P) u and its
+  exact Jacobian P J(P u) P + s (I - P), s = phys.constraint_scale > 0 (the
+  solution does not depend on s).
   beta = exp(log beta) with log beta the basal nodal field interpolated by
   the face basis.
 
@@ -172,18 +173,18 @@ def _logbeta(mesh, phys, logbeta):
 
 
 def residual(mesh, phys, up, logbeta=None):
-    """Constrained residual r_c(u, p) = [P r_u(P u, p) + (I - P) u ; r_p(P u)]."""
+    """Constrained residual r_c(u, p) = [P r_u(P u, p) + s (I - P) u ; r_p(P u)]."""
     logbeta = _logbeta(mesh, phys, logbeta)
     u, p = split(mesh, up)
     uP = project(mesh, u)
     rv, rp = element_residual(mesh, phys, gather(mesh, uP), p, logbeta)
     ru = scatter(mesh, rv)
-    ru = project(mesh, ru, transpose=True) + (u - project(mesh, u))
+    ru = project(mesh, ru, transpose=True) + phys.constraint_scale * (u - project(mesh, u))
     return np.concatenate([ru.ravel(), rp.ravel()])
 
 
 def jacobian_apply(mesh, phys, up, x, logbeta=None):
-    """Constrained Newton Jacobian action  (P J(P u) P + (I - P)) x."""
+    """Constrained Newton Jacobian action  (P J(P u) P + s (I - P)) x."""
     logbeta = _logbeta(mesh, phys, logbeta)
     u, _ = split(mesh, up)
     w, qv = split(mesh, x)
@@ -191,7 +192,7 @@ def jacobian_apply(mesh, phys, up, x, logbeta=None):
     wP = project(mesh, w)
     yv, yp = element_jacobian(mesh, phys, gather(mesh, uP), gather(mesh, wP), qv, logbeta)
     yu = scatter(mesh, yv)
-    yu = project(mesh, yu, transpose=True) + (w - project(mesh, w))
+    yu = project(mesh, yu, transpose=True) + phys.constraint_scale * (w - project(mesh, w))
     return np.concatenate([yu.ravel(), yp.ravel()])
 
 

@@ -45,7 +45,7 @@ class stokes_mesh_desc(C.Structure):
 class stokes_params(C.Structure):
     _fields_ = [("n", C.c_double), ("A", C.c_double), ("C0", C.c_double),
                 ("gamma", C.c_double), ("delta", C.c_double), ("body", C.c_double * 3),
-                ("robin", C.c_int), ("logbeta", C.c_void_p)]
+                ("robin", C.c_int), ("logbeta", C.c_void_p), ("constraint_scale", C.c_double)]
 
 
 class stokes_sizes(C.Structure):
@@ -70,13 +70,15 @@ class stokes_solver_opts(C.Structure):
 class stokes_solve_report(C.Structure):
     _fields_ = [("converged", C.c_int), ("newton_its", C.c_int), ("krylov_its", C.c_int),
                 ("line_search_cuts", C.c_int), ("res0", C.c_double), ("res_final", C.c_double),
-                ("seconds", C.c_double), ("history", C.c_double * 64), ("krylov_per_newton", C.c_int * 64)]
+                ("seconds", C.c_double), ("constraint_scale", C.c_double), ("history", C.c_double * 64),
+                ("krylov_per_newton", C.c_int * 64)]
 
     def as_dict(self):
         n = min(self.newton_its + 1, 64)
         return {"converged": bool(self.converged), "newton_its": self.newton_its,
                 "krylov_its": self.krylov_its, "line_search_cuts": self.line_search_cuts,
                 "res0": self.res0, "res_final": self.res_final, "seconds": self.seconds,
+                "constraint_scale": self.constraint_scale,
                 "history": list(self.history[:n]),
                 "krylov_per_newton": list(self.krylov_per_newton[:max(n - 1, 0)])}
 

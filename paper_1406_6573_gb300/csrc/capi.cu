@@ -134,6 +134,7 @@ int check_params(const stokes_mesh* m, const stokes_params* p) {
     if (!(p->n >= 1.0) || !(p->A > 0) || !(p->C0 > 0) || !(p->gamma > 0) || !(p->delta > 0))
         return fail(STOKES_E_INVAL, "params: need n >= 1, A > 0, C0 > 0, gamma > 0, delta > 0");
     if (p->robin && !p->logbeta && m->h.Nb > 0) return fail(STOKES_E_INVAL, "params: robin = 1 needs logbeta");
+    if (!(p->constraint_scale > 0)) return fail(STOKES_E_INVAL, "params: constraint_scale must be > 0");
     return STOKES_OK;
 }
 
@@ -143,6 +144,9 @@ ElemArgs elem_args(const stokes_mesh* m, const stokes_params* p) {
     a.any_hang = m->h.n_hang > 0;
     a.nodes = m->d_nodes; a.hang = m->d_hang; a.geo = m->d_geo; a.pidx = m->d_pidx; a.pel = m->d_pel;
     a.err = m->d_err;
+    if (m->h.lattice) {
+        a.lat_nx = m->h.nx; a.lat_ny = m->h.ny; a.lat_NX = m->h.latNX; a.lat_NY = m->h.latNY;
+    }
     if (p) {
         a.C = p->C0 * std::pow(p->A, -1.0 / p->n);
         a.gamma = p->gamma; a.delta = p->delta;
@@ -182,7 +186,7 @@ int operator_sequence(const stokes_mesh* m, const stokes_params* p, int mode, in
         if (e) return cuda_fail(cudaError_t(e), "basal face kernel launch");
     }
     e = timed(m, 3, s, [&] {
-        return launch_constraint(prec, m->h.Nb, m->d_basal_nodes, m->d_basal_P, x, y, s);
+        return launch_constraint(prec, m->h.Nb, m->d_basal_nodes, m->d_basal_P, p->constraint_scale, x, y, s);
     });
     if (e) return cuda_fail(cudaError_t(e), "constraint kernel launch");
     return STOKES_OK;

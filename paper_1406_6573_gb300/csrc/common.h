@@ -46,6 +46,8 @@ struct HostMesh {
     double Lx = 1, Ly = 1;
     int basal_bc = 0;
     int64_t E = 0, Nv = 0, Np = 0, Nb = 0, n_hang = 0;
+    bool lattice = false;              // conforming lattice numbering (no refinement input)
+    int64_t latNX = 0, latNY = 0;      // node lattice extents in x, y
     Tables1D tab;
     std::vector<int32_t> elem_nodes;   // [E][n1^3] node gathered into each local slot
     std::vector<uint32_t> elem_hang;   // [E] hanging code

@@ -54,17 +54,17 @@ __device__ __forceinline__ void sym6(const T (&g)[3][3], T& E00, T& E11, T& E22,
 // ============================================================ volume kernel
 // Generic element kernel (residual, fused Jacobian, linearisation, A-gradient).
 // T: arithmetic type.  S: element type of the stored state (linearize).
+// exchange scratch of one element slot: 9 buffers (3 per velocity component)
+template <typename T> constexpr int SLOT = 9 * BUFLEN<T>;
+
 template <typename T, typename S, int MODE, bool TRANS>
 __global__ void __launch_bounds__(32 * GW<T>) elem_kernel(ElemArgs a) {
-    __shared__ __align__(16) T sbuf[GW<T>][EPW + 1][3][BUFLEN<T>];
+    extern __shared__ __align__(16) unsigned char smem_dyn[];
     const LaneMap L;
     const int i = L.i, j = L.j, ij = L.ij, es = L.es;
     const int64_t e = int64_t(blockIdx.x) * (GW<T> * EPW) + L.warp * EPW + es;
     const bool active = (es < EPW) && (e < a.E);
-    T* b0 = sbuf[L.warp][es][0];
-    T* b1 = sbuf[L.warp][es][1];
-    T* b2 = sbuf[L.warp][es][2];
-    T* sb = &sbuf[L.warp][es][0][0];
+    T* sb = reinterpret_cast<T*>(smem_dyn) + (L.warp * (EPW + 1) + es) * SLOT<T>;
     const uint32_t h = active ? a.hang[e] : 0u;
     const bool any_h = a.any_hang ? (__any_sync(0xffffffffu, (h & ((1u << HANG_CHILD0) - 1)) != 0) != 0) : false;
     const int ps = a.pspace;
@@ -80,8 +80,7 @@ __global__ void __launch_bounds__(32 * GW<T>) elem_kernel(ElemArgs a) {
         if (any_h) hanging_forward<T, 3>(v, h, active, i, j, sb);
         T pc[N1];
         pressure_fold<T, T>(a, static_cast<const T*>(a.x), e, active, i, j, pc);
-        #pragma unroll
-        for (int c = 0; c < 3; ++c) ref_gradient<T>(R, v[c], G[c][0], G[c][1], G[c][2], i, j, b0, b1, b2);
+        ref_gradient<T, 3>(R, v, G, i, j, sb);
         T Sv[3][Q];
         #pragma unroll
         for (int lq = 0; lq < Q; ++lq) {
@@ -107,8 +106,7 @@ __global__ void __launch_bounds__(32 * GW<T>) elem_kernel(ElemArgs a) {
             ref_stress(G, lq, Ji, tau);
         }
         T out[3][N1];
-        #pragma unroll
-        for (int c = 0; c < 3; ++c) ref_gradient_T<T, true>(R, G[c][0], G[c][1], G[c][2], Sv[c], out[c], i, j, b0, b1, b2);
+        ref_gradient_T<T, 3, true>(R, G, Sv, out, i, j, sb);
         pressure_rows<T>(gq, a.npr, ps, i, j, ij, active, sb, static_cast<T*>(a.y) + 3 * a.Nv + e * a.npr);
         if (any_h) hanging_transpose<T, 3>(out, h, active, i, j, sb);
         scatter_velocity<T>(a, static_cast<T*>(a.y), e, active, ij, out);
@@ -119,8 +117,7 @@ __global__ void __launch_bounds__(32 * GW<T>) elem_kernel(ElemArgs a) {
             T v[3][N1];
             gather_velocity<T, T>(a, static_cast<const T*>(a.u), e, active, ij, v);
             if (any_h) hanging_forward<T, 3>(v, h, active, i, j, sb);
-            #pragma unroll
-            for (int c = 0; c < 3; ++c) ref_gradient<T>(R, v[c], G[c][0], G[c][1], G[c][2], i, j, b0, b1, b2);
+            ref_gradient<T, 3>(R, v, G, i, j, sb);
             #pragma unroll
             for (int lq = 0; lq < Q; ++lq) {
                 T Ji[9], wdj;
@@ -142,8 +139,7 @@ __global__ void __launch_bounds__(32 * GW<T>) elem_kernel(ElemArgs a) {
         if (any_h) hanging_forward<T, 3>(v, h, active, i, j, sb);
         T pc[N1];
         pressure_fold<T, T>(a, static_cast<const T*>(a.x), e, active, i, j, pc);
-        #pragma unroll
-        for (int c = 0; c < 3; ++c) ref_gradient<T>(R, v[c], G[c][0], G[c][1], G[c][2], i, j, b0, b1, b2);
+        ref_gradient<T, 3>(R, v, G, i, j, sb);
         #pragma unroll
         for (int lq = 0; lq < Q; ++lq) {
             T Ji[9], wdj;
@@ -170,9 +166,8 @@ __global__ void __launch_bounds__(32 * GW<T>) elem_kernel(ElemArgs a) {
             ref_stress(G, lq, Ji, tau);
         }
         T out[3][N1];
-        T dummy[Q];
-        #pragma unroll
-        for (int c = 0; c < 3; ++c) ref_gradient_T<T, false>(R, G[c][0], G[c][1], G[c][2], dummy, out[c], i, j, b0, b1, b2);
+        T dummy[3][Q];
+        ref_gradient_T<T, 3, false>(R, G, dummy, out, i, j, sb);
         pressure_rows<T>(gq, a.npr, ps, i, j, ij, active, sb, static_cast<T*>(a.y) + 3 * a.Nv + e * a.npr);
         if (any_h) hanging_transpose<T, 3>(out, h, active, i, j, sb);
         scatter_velocity<T>(a, static_cast<T*>(a.y), e, active, ij, out);
@@ -180,8 +175,7 @@ __global__ void __launch_bounds__(32 * GW<T>) elem_kernel(ElemArgs a) {
         T v[3][N1];
         gather_velocity<T, double>(a, a.ud, e, active, ij, v);
         if (any_h) hanging_forward<T, 3>(v, h, active, i, j, sb);
-        #pragma unroll
-        for (int c = 0; c < 3; ++c) ref_gradient<T>(R, v[c], G[c][0], G[c][1], G[c][2], i, j, b0, b1, b2);
+        ref_gradient<T, 3>(R, v, G, i, j, sb);
         S* st = static_cast<S*>(a.state) + e * SSTRIDE;
         #pragma unroll
         for (int lq = 0; lq < Q; ++lq) {
@@ -220,14 +214,12 @@ __global__ void __launch_bounds__(32 * GW<T>) elem_kernel(ElemArgs a) {
             T v[3][N1];
             gather_velocity<T, double>(a, a.lam, e, active, ij, v);
             if (any_h) hanging_forward<T, 3>(v, h, active, i, j, sb);
-            #pragma unroll
-            for (int c = 0; c < 3; ++c) ref_gradient<T>(R, v[c], Gl[c][0], Gl[c][1], Gl[c][2], i, j, b0, b1, b2);
+            ref_gradient<T, 3>(R, v, Gl, i, j, sb);
         }
         T v[3][N1];
         gather_velocity<T, double>(a, a.ud, e, active, ij, v);
         if (any_h) hanging_forward<T, 3>(v, h, active, i, j, sb);
-        #pragma unroll
-        for (int c = 0; c < 3; ++c) ref_gradient<T>(R, v[c], G[c][0], G[c][1], G[c][2], i, j, b0, b1, b2);
+        ref_gradient<T, 3>(R, v, G, i, j, sb);
         #pragma unroll
         for (int lq = 0; lq < Q; ++lq) {
             T Ji[9], wdj;
@@ -265,7 +257,7 @@ template <typename T>
 struct StateApplyCfg {
     static constexpr int W = sizeof(T) == 8 ? 4 : 8;        // warps per block
     static constexpr int BUF = EPW * SSTRIDE;                // values per stage buffer
-    static constexpr int SCR = (EPW + 1) * 3 * BUFLEN<T>;    // scratch per warp
+    static constexpr int SCR = (EPW + 1) * SLOT<T>;          // scratch per warp
     static constexpr int PER_WARP = ((2 * BUF + SCR) * int(sizeof(T)) + 127) / 128 * 128;
     static constexpr int SMEM = W * PER_WARP + W * 2 * 8;
 };
@@ -282,10 +274,7 @@ __global__ void __launch_bounds__(32 * StateApplyCfg<T>::W) state_apply_kernel(E
     T* stage[2] = {reinterpret_cast<T*>(wbase), reinterpret_cast<T*>(wbase) + C::BUF};
     T* scratch = reinterpret_cast<T*>(wbase) + 2 * C::BUF;
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + C::W * C::PER_WARP) + 2 * L.warp;
-    T* sb = scratch + es * 3 * BUFLEN<T>;
-    T* b0 = sb;
-    T* b1 = sb + BUFLEN<T>;
-    T* b2 = sb + 2 * BUFLEN<T>;
+    T* sb = scratch + es * SLOT<T>;
     const int ps = a.pspace;
     const T* S = static_cast<const T*>(a.cstate);
     const T* x = static_cast<const T*>(a.x);
@@ -334,8 +323,7 @@ __global__ void __launch_bounds__(32 * StateApplyCfg<T>::W) state_apply_kernel(E
             T v[3][N1];
             gather_velocity<T, T>(a, x, e, active, ij, v);
             if (any_h) hanging_forward<T, 3>(v, h, active, i, j, sb);
-            #pragma unroll
-            for (int c = 0; c < 3; ++c) ref_gradient<T>(R, v[c], G[c][0], G[c][1], G[c][2], i, j, b0, b1, b2);
+            ref_gradient<T, 3>(R, v, G, i, j, sb);
         } else {
             #pragma unroll
             for (int c = 0; c < 3; ++c)
@@ -393,9 +381,8 @@ __global__ void __launch_bounds__(32 * StateApplyCfg<T>::W) state_apply_kernel(E
         }
         __syncwarp();
         T out[3][N1];
-        T dummy[Q];
-        #pragma unroll
-        for (int c = 0; c < 3; ++c) ref_gradient_T<T, false>(R, G[c][0], G[c][1], G[c][2], dummy, out[c], i, j, b0, b1, b2);
+        T dummy[3][Q];
+        ref_gradient_T<T, 3, false>(R, G, dummy, out, i, j, sb);
         if constexpr (!PONLY) pressure_rows<T>(gq, a.npr, ps, i, j, ij, active, sb, y + 3 * a.Nv + e * a.npr);
         if (any_h) hanging_transpose<T, 3>(out, h, active, i, j, sb);
         scatter_velocity<T>(a, y, e, active, ij, out);
@@ -585,7 +572,17 @@ int launch_elem_t(const ElemArgs& a, cudaStream_t s) {
     const int64_t epb = GW<T> * EPW;
     const int64_t blocks = (a.E + epb - 1) / epb;
     if (blocks == 0) return int(cudaSuccess);
-    elem_kernel<T, S, MODE, TRANS><<<unsigned(blocks), 32 * GW<T>, 0, s>>>(a);
+    const int smem = GW<T> * (EPW + 1) * SLOT<T> * int(sizeof(T));
+    static int configured_device = -1;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (configured_device != dev) {
+        cudaError_t e = cudaFuncSetAttribute(elem_kernel<T, S, MODE, TRANS>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return int(e);
+        configured_device = dev;
+    }
+    elem_kernel<T, S, MODE, TRANS><<<unsigned(blocks), 32 * GW<T>, smem, s>>>(a);
     return int(cudaGetLastError());
 }
 

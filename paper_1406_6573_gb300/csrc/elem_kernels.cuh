@@ -287,109 +287,145 @@ __device__ __forceinline__ void load_line(const T* p, T (&o)[N1]) {
     }
 }
 
-// Reference gradient at the Gauss points (iq = i, jq = j, lq) of the field
-// whose nodal column the thread holds in vin:
+// Reference gradients at the Gauss points (iq = i, jq = j, lq) of the NC
+// fields whose nodal columns the thread holds in vin, all fields advancing
+// through each stage together (independent chains between warp syncs):
 //   zeta: interpolate (registers);  eta: interpolate and differentiate the
 //   same line;  xi: interpolate and differentiate the interpolated line, and
 //   interpolate the eta-derivative line;  zeta derivative by collocation.
-template <typename T>
-__device__ __forceinline__ void ref_gradient(const Rows<T>& R, const T (&vin)[N1], T (&gx)[Q], T (&gy)[Q],
-                                             T (&gz)[Q], int i, int j, T* b0, T* b1, T* b2) {
-    T a[Q];
+// buf: 3 NC exchange buffers of BUFLEN values.
+template <typename T, int NC>
+__device__ __forceinline__ void ref_gradient(const Rows<T>& R, const T (&vin)[NC][N1], T (&G)[NC][3][Q],
+                                             int i, int j, T* buf) {
     #pragma unroll
-    for (int lq = 0; lq < Q; ++lq) {
-        T s = 0;
+    for (int c = 0; c < NC; ++c) {
+        T* b0 = buf + (3 * c) * BUFLEN<T>;
         #pragma unroll
-        for (int l = 0; l < N1; ++l) s += Tab<T>::B(lq, l) * vin[l];
-        b0[yl<T>(i, j, lq)] = s;
+        for (int lq = 0; lq < Q; ++lq) {
+            T s = 0;
+            #pragma unroll
+            for (int l = 0; l < N1; ++l) s += Tab<T>::B(lq, l) * vin[c][l];
+            b0[yl<T>(i, j, lq)] = s;
+        }
     }
     wsync();
     #pragma unroll
-    for (int lq = 0; lq < Q; ++lq) {            // eta: thread (node i, jq = j)
-        T ln[N1];
-        load_line<T>(b0 + yl<T>(i, 0, lq), ln);
-        T si = 0, sd = 0;
+    for (int c = 0; c < NC; ++c) {              // eta: thread (node i, jq = j)
+        const T* b0 = buf + (3 * c) * BUFLEN<T>;
+        T* b1 = buf + (3 * c + 1) * BUFLEN<T>;
+        T* b2 = buf + (3 * c + 2) * BUFLEN<T>;
         #pragma unroll
-        for (int m = 0; m < N1; ++m) { si += R.Bj[m] * ln[m]; sd += R.Tj[m] * ln[m]; }
-        b1[xl<T>(i, j, lq)] = si;
-        b2[xl<T>(i, j, lq)] = sd;
+        for (int lq = 0; lq < Q; ++lq) {
+            T ln[N1];
+            load_line<T>(b0 + yl<T>(i, 0, lq), ln);
+            T si = 0, sd = 0;
+            #pragma unroll
+            for (int m = 0; m < N1; ++m) { si += R.Bj[m] * ln[m]; sd += R.Tj[m] * ln[m]; }
+            b1[xl<T>(i, j, lq)] = si;
+            b2[xl<T>(i, j, lq)] = sd;
+        }
     }
     wsync();
     #pragma unroll
-    for (int lq = 0; lq < Q; ++lq) {            // xi: thread (iq = i, jq = j)
-        T l1[N1], l2[N1];
-        load_line<T>(b1 + xl<T>(0, j, lq), l1);
-        load_line<T>(b2 + xl<T>(0, j, lq), l2);
-        T sv = 0, sx = 0, sy = 0;
+    for (int c = 0; c < NC; ++c) {              // xi: thread (iq = i, jq = j)
+        const T* b1 = buf + (3 * c + 1) * BUFLEN<T>;
+        const T* b2 = buf + (3 * c + 2) * BUFLEN<T>;
+        T a[Q];
         #pragma unroll
-        for (int m = 0; m < N1; ++m) { sv += R.Bi[m] * l1[m]; sx += R.Ti[m] * l1[m]; sy += R.Bi[m] * l2[m]; }
-        a[lq] = sv; gx[lq] = sx; gy[lq] = sy;
-    }
-    #pragma unroll
-    for (int lq = 0; lq < Q; ++lq) {            // zeta derivative, collocated
-        T s = 0;
+        for (int lq = 0; lq < Q; ++lq) {
+            T l1[N1], l2[N1];
+            load_line<T>(b1 + xl<T>(0, j, lq), l1);
+            load_line<T>(b2 + xl<T>(0, j, lq), l2);
+            T sv = 0, sx = 0, sy = 0;
+            #pragma unroll
+            for (int m = 0; m < N1; ++m) { sv += R.Bi[m] * l1[m]; sx += R.Ti[m] * l1[m]; sy += R.Bi[m] * l2[m]; }
+            a[lq] = sv; G[c][0][lq] = sx; G[c][1][lq] = sy;
+        }
         #pragma unroll
-        for (int m = 0; m < Q; ++m) s += Tab<T>::Dg(lq, m) * a[m];
-        gz[lq] = s;
+        for (int lq = 0; lq < Q; ++lq) {        // zeta derivative, collocated
+            T s = 0;
+            #pragma unroll
+            for (int m = 0; m < Q; ++m) s += Tab<T>::Dg(lq, m) * a[m];
+            G[c][2][lq] = s;
+        }
     }
     wsync();
 }
 
-// Transposed gradient: nodal column out[l] of
-//   sum_qp (d phi/d xi) Sx + (d phi/d eta) Sy + (d phi/d zeta) Sz + phi Sv
+// Transposed gradients: nodal columns out[c][l] of
+//   sum_qp (d phi/d xi) S[c][0] + (d phi/d eta) S[c][1] + (d phi/d zeta) S[c][2] + phi Sv[c]
 // (collocated derivative transposes at the Gauss points, then the three
-// transposed interpolations).
-template <typename T, bool HAS_VAL>
-__device__ __forceinline__ void ref_gradient_T(const Rows<T>& R, const T (&Sx)[Q], const T (&Sy)[Q],
-                                               const T (&Sz)[Q], const T (&Sv)[Q], T (&out)[N1], int i, int j,
-                                               T* b0, T* b1, T* b2) {
-    T t[Q];
+// transposed interpolations), NC fields advancing together.
+template <typename T, int NC, bool HAS_VAL>
+__device__ __forceinline__ void ref_gradient_T(const Rows<T>& R, const T (&S)[NC][3][Q], const T (&Sv)[NC][Q],
+                                               T (&out)[NC][N1], int i, int j, T* buf) {
+    T t[NC][Q];
     #pragma unroll
-    for (int lq = 0; lq < Q; ++lq) {
-        b0[xl<T>(i, j, lq)] = Sx[lq];
-        b1[yl<T>(i, j, lq)] = Sy[lq];
-        T s = HAS_VAL ? Sv[lq] : T(0);
+    for (int c = 0; c < NC; ++c) {
+        T* b0 = buf + (3 * c) * BUFLEN<T>;
+        T* b1 = buf + (3 * c + 1) * BUFLEN<T>;
         #pragma unroll
-        for (int m = 0; m < Q; ++m) s += Tab<T>::Dg(m, lq) * Sz[m];
-        t[lq] = s;
+        for (int lq = 0; lq < Q; ++lq) {
+            b0[xl<T>(i, j, lq)] = S[c][0][lq];
+            b1[yl<T>(i, j, lq)] = S[c][1][lq];
+            T s = HAS_VAL ? Sv[c][lq] : T(0);
+            #pragma unroll
+            for (int m = 0; m < Q; ++m) s += Tab<T>::Dg(m, lq) * S[c][2][m];
+            t[c][lq] = s;
+        }
     }
     wsync();
     #pragma unroll
-    for (int lq = 0; lq < Q; ++lq) {
-        T lx[N1], ly[N1];
-        load_line<T>(b0 + xl<T>(0, j, lq), lx);
-        load_line<T>(b1 + yl<T>(i, 0, lq), ly);
-        T s = t[lq];
+    for (int c = 0; c < NC; ++c) {
+        const T* b0 = buf + (3 * c) * BUFLEN<T>;
+        const T* b1 = buf + (3 * c + 1) * BUFLEN<T>;
+        T* b2 = buf + (3 * c + 2) * BUFLEN<T>;
         #pragma unroll
-        for (int m = 0; m < Q; ++m) s += R.DTi[m] * lx[m] + R.DTj[m] * ly[m];
-        b2[xl<T>(i, j, lq)] = s;
+        for (int lq = 0; lq < Q; ++lq) {
+            T lx[N1], ly[N1];
+            load_line<T>(b0 + xl<T>(0, j, lq), lx);
+            load_line<T>(b1 + yl<T>(i, 0, lq), ly);
+            T s = t[c][lq];
+            #pragma unroll
+            for (int m = 0; m < Q; ++m) s += R.DTi[m] * lx[m] + R.DTj[m] * ly[m];
+            b2[xl<T>(i, j, lq)] = s;
+        }
     }
     wsync();
     #pragma unroll
-    for (int lq = 0; lq < Q; ++lq) {            // xi^T: thread (node i, jq = j)
-        T ln[N1];
-        load_line<T>(b2 + xl<T>(0, j, lq), ln);
-        T s = 0;
+    for (int c = 0; c < NC; ++c) {              // xi^T: thread (node i, jq = j)
+        const T* b2 = buf + (3 * c + 2) * BUFLEN<T>;
+        T* b0 = buf + (3 * c) * BUFLEN<T>;
         #pragma unroll
-        for (int m = 0; m < Q; ++m) s += R.BTi[m] * ln[m];
-        b0[yl<T>(i, j, lq)] = s;
+        for (int lq = 0; lq < Q; ++lq) {
+            T ln[N1];
+            load_line<T>(b2 + xl<T>(0, j, lq), ln);
+            T s = 0;
+            #pragma unroll
+            for (int m = 0; m < Q; ++m) s += R.BTi[m] * ln[m];
+            b0[yl<T>(i, j, lq)] = s;
+        }
     }
     wsync();
     #pragma unroll
-    for (int lq = 0; lq < Q; ++lq) {            // eta^T: thread (node i, node j)
-        T ln[N1];
-        load_line<T>(b0 + yl<T>(i, 0, lq), ln);
-        T s = 0;
+    for (int c = 0; c < NC; ++c) {              // eta^T then zeta^T
+        const T* b0 = buf + (3 * c) * BUFLEN<T>;
         #pragma unroll
-        for (int m = 0; m < Q; ++m) s += R.BTj[m] * ln[m];
-        t[lq] = s;
-    }
-    #pragma unroll
-    for (int l = 0; l < N1; ++l) {              // zeta^T (registers)
-        T s = 0;
+        for (int lq = 0; lq < Q; ++lq) {
+            T ln[N1];
+            load_line<T>(b0 + yl<T>(i, 0, lq), ln);
+            T s = 0;
+            #pragma unroll
+            for (int m = 0; m < Q; ++m) s += R.BTj[m] * ln[m];
+            t[c][lq] = s;
+        }
         #pragma unroll
-        for (int lq = 0; lq < Q; ++lq) s += Tab<T>::B(lq, l) * t[lq];
-        out[l] = s;
+        for (int l = 0; l < N1; ++l) {
+            T s = 0;
+            #pragma unroll
+            for (int lq = 0; lq < Q; ++lq) s += Tab<T>::B(lq, l) * t[c][lq];
+            out[c][l] = s;
+        }
     }
     wsync();
 }
@@ -405,6 +441,21 @@ __device__ __forceinline__ void project3(const double* P, T& x0, T& x1, T& x2) {
     x2 = p02 * a + p12 * b + p22 * c;
 }
 
+// Global node of slot (ij, l) of element e: from the element map, or computed
+// from the lattice on conforming meshes (no map read).
+__device__ __forceinline__ int64_t node_of(const ElemArgs& a, int64_t e, int ij, int l) {
+    if (a.lat_nx > 0) {
+        const int64_t ex = e % a.lat_nx, r = e / a.lat_nx;
+        const int64_t ey = r % a.lat_ny, ez = r / a.lat_ny;
+        int64_t I = ex * K + ij % N1, J = ey * K + ij / N1;
+        const int64_t Lz = ez * K + l;
+        if (I >= a.lat_NX) I -= a.lat_NX;
+        if (J >= a.lat_NY) J -= a.lat_NY;
+        return I + a.lat_NX * (J + a.lat_NY * Lz);
+    }
+    return a.nodes[e * N3 + ij + N2 * l];
+}
+
 // Velocity columns of element e (3 components) from a state vector x,
 // with the basal projector applied at bottom-plane slots.
 template <typename T, typename TIN>
@@ -413,7 +464,7 @@ __device__ __forceinline__ void gather_velocity(const ElemArgs& a, const TIN* x,
     #pragma unroll
     for (int l = 0; l < N1; ++l) {
         if (active) {
-            const int64_t g = a.nodes[e * N3 + ij + N2 * l];
+            const int64_t g = node_of(a, e, ij, l);
             v[0][l] = T(ld(x + 3 * g));
             v[1][l] = T(ld(x + 3 * g + 1));
             v[2][l] = T(ld(x + 3 * g + 2));
@@ -435,7 +486,7 @@ __device__ __forceinline__ void scatter_velocity(const ElemArgs& a, T* y, int64_
     if (pi >= 0) project3<T>(a.pel + int64_t(pi) * 6 * N2 + ij, v[0][0], v[1][0], v[2][0]);
     #pragma unroll
     for (int l = 0; l < N1; ++l) {
-        const int64_t g = a.nodes[e * N3 + ij + N2 * l];
+        const int64_t g = node_of(a, e, ij, l);
         atomic_add(y + 3 * g, v[0][l]);
         atomic_add(y + 3 * g + 1, v[1][l]);
         atomic_add(y + 3 * g + 2, v[2][l]);

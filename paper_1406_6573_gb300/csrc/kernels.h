@@ -43,6 +43,8 @@ struct ElemArgs {
     double body[3];
     double* gA;                // gradient output (accumulated)
     double gA_scale;
+    int64_t lat_nx, lat_ny, lat_NX, lat_NY;   // conforming lattice (lat_nx > 0): node index
+                               // computed as I + NX (J + NY L) instead of read from nodes
     int* err;                  // device status word (bounded waits that expired)
     int persistent_blocks;     // grid size of the persistent state-apply kernel
 };
@@ -80,7 +82,7 @@ STOKES_DECLARE_DEGREE(4)
 #undef STOKES_DECLARE_DEGREE
 
 // Degree-independent kernels (misc.cu).
-int launch_constraint(int prec, int64_t Nb, const int32_t* basal_nodes, const double* basal_P,
+int launch_constraint(int prec, int64_t Nb, const int32_t* basal_nodes, const double* basal_P, double scale,
                       const void* x, void* y, cudaStream_t s);
 
 }  // namespace stokes

@@ -185,6 +185,9 @@ int build_host_mesh(const stokes_mesh_desc& d, HostMesh& m, std::string& err) {
         const int64_t NY = m.periodic ? int64_t(m.ny) * k : int64_t(m.ny) * k + 1;
         const int64_t NZ = int64_t(m.nz) * k + 1;
         m.Nv = NX * NY * NZ;
+        m.lattice = true;
+        m.latNX = NX;
+        m.latNY = NY;
         #pragma omp parallel for schedule(static)
         for (int64_t e = 0; e < E; ++e) {
             int cc[3], b[3];

@@ -29,7 +29,7 @@ __global__ void col_factor_kernel(ColSolveArgs a) {
     const int b = a.col_basal[c];
     if (b >= 0) {
         // the lowest node of the column carries the nodal projector P:
-        // K <- P K P + (I - P) on its rows and columns
+        // K <- P K P + s (I - P) on its rows and columns
         const double* p6 = a.basal_P + 6 * int64_t(b);
         const T P[3][3] = {{T(p6[0]), T(p6[3]), T(p6[4])}, {T(p6[3]), T(p6[1]), T(p6[5])}, {T(p6[4]), T(p6[5]), T(p6[2])}};
         const int qmax = min(n - 1, 2 + bw);
@@ -45,8 +45,9 @@ __global__ void col_factor_kernel(ColSolveArgs a) {
             for (int q = 0; q < 3; ++q)
                 if (r - q <= bw) band(A, a.ncol, W, bw, r, q, c) = v[0] * P[0][q] + v[1] * P[1][q] + v[2] * P[2][q];
         }
+        const T sc = T(a.scale);
         for (int r = 0; r < 3; ++r)
-            for (int q = 0; q < 3; ++q) band(A, a.ncol, W, bw, r, q, c) += (r == q ? T(1) : T(0)) - P[r][q];
+            for (int q = 0; q < 3; ++q) band(A, a.ncol, W, bw, r, q, c) += sc * ((r == q ? T(1) : T(0)) - P[r][q]);
     }
     for (int p = 0; p < n; ++p) {
         const T piv = band(A, a.ncol, W, bw, p, p, c);
@@ -100,6 +101,27 @@ __global__ void schur_apply_kernel(int64_t Nv, int64_t Np, const T* __restrict__
         z[3 * Nv + i] = -r[3 * Nv + i] / md[i];
 }
 
+// mean |diagonal| of the assembled (unconstrained) column blocks
+template <typename T>
+__global__ void col_diag_kernel(ColSolveArgs a, double* out) {
+    __shared__ double red[8];
+    const int64_t c = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    double s = 0;
+    if (c < a.ncol) {
+        const T* A = static_cast<const T*>(a.A);
+        const int W = 2 * a.bw + 1, n = 3 * a.col_len[c];
+        for (int r = 0; r < n; ++r) s += fabs(double(A[(int64_t(r) * W + a.bw) * a.ncol + c]));
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0;
+        for (int w = 0; w < int(blockDim.x >> 5); ++w) t += red[w];
+        atomicAdd(out, t);
+    }
+}
+
 int solve_threads(int colmax, int bytes) {
     int nt = 128;
     while (nt > 32 && int64_t(3) * colmax * nt * bytes > 96 * 1024) nt /= 2;
@@ -113,6 +135,16 @@ int launch_col_factor(int prec, const ColSolveArgs& a, cudaStream_t s) {
     const unsigned blocks = unsigned((a.ncol + 127) / 128);
     if (prec == 1) col_factor_kernel<float><<<blocks, 128, 0, s>>>(a);
     else col_factor_kernel<double><<<blocks, 128, 0, s>>>(a);
+    return int(cudaGetLastError());
+}
+
+int launch_col_diag_sum(int prec, const ColSolveArgs& a, double* out, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(double), s);
+    if (e != cudaSuccess) return int(e);
+    if (a.ncol == 0) return 0;
+    const unsigned blocks = unsigned((a.ncol + 255) / 256);
+    if (prec == 1) col_diag_kernel<float><<<blocks, 256, 0, s>>>(a, out);
+    else col_diag_kernel<double><<<blocks, 256, 0, s>>>(a, out);
     return int(cudaGetLastError());
 }
 

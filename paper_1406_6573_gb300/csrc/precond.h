@@ -37,11 +37,14 @@ struct ColSolveArgs {
     const int32_t* col_len;    // [ncol]
     const int32_t* col_basal;  // [ncol] basal index of the column's lowest node, or -1
     const double* basal_P;     // [Nb][6]
+    double scale;              // constraint-row scale s of P F P + s (I - P)
     void* A;                   // banded matrices (factored in place)
 };
 
 // constraints (P F P + I - P on the basal node block) + banded LU per column
 int launch_col_factor(int prec, const ColSolveArgs& a, cudaStream_t s);
+// out[0] = sum over all columns of |diag| of the assembled blocks
+int launch_col_diag_sum(int prec, const ColSolveArgs& a, double* out, cudaStream_t s);
 // z_u = F~^{-1} r_u on the velocity part (z, r: state vectors of type prec)
 int launch_col_solve(int prec, const ColSolveArgs& a, const void* r, void* z, cudaStream_t s);
 // z_p = -r_p / md (pressure part)

@@ -89,18 +89,19 @@ int op64(stokes_solver* S, const double* x, double* y, bool trans, cudaStream_t 
     return trans ? stokes_state_apply_transpose(S->st64, x, y, st) : stokes_state_apply(S->st64, x, y, st);
 }
 
-ColSolveArgs colsolve_args(stokes_solver* S) {
+ColSolveArgs colsolve_args(stokes_solver* S, double scale) {
     const stokes_mesh* m = S->mesh;
     ColSolveArgs c{};
     c.ncol = m->h.ncol; c.Nv = m->h.Nv; c.colmax = m->h.colmax; c.bw = S->bw;
     c.col_nodes = m->d_col_nodes; c.col_len = m->d_col_len; c.col_basal = m->d_col_basal;
-    c.basal_P = m->d_basal_P; c.A = S->A;
+    c.basal_P = m->d_basal_P; c.scale = scale; c.A = S->A;
     return c;
 }
 
 // preconditioner set-up from the inner state: column blocks of F, their
-// factorisation, and the Schur diagonal
-int precond_setup(stokes_solver* S, const stokes_params* p, cudaStream_t st) {
+// factorisation, and the Schur diagonal.  With scale_out, the mean
+// |diagonal| of the velocity block is returned before factorisation.
+int precond_setup(stokes_solver* S, const stokes_params* p, cudaStream_t st, double* scale_out = nullptr) {
     const stokes_mesh* m = S->mesh;
     CU(cudaMemsetAsync(S->A, 0, S->band_elems * S->isz, st), "clearing column blocks");
     ColArgs a{};
@@ -110,7 +111,17 @@ int precond_setup(stokes_solver* S, const stokes_params* p, cudaStream_t st) {
     a.fidx = m->d_fidx; a.fmap = m->d_fmap; a.fgeo = m->d_fgeo; a.logbeta = p->logbeta;
     a.state = S->st_in->d_state; a.A = S->A; a.md = S->md;
     CU(launch_precond_assembly(m->h.k, S->inner, a, st), "preconditioner assembly");
-    CU(launch_col_factor(S->inner, colsolve_args(S), st), "column factorisation");
+    double scale = p->constraint_scale;
+    if (scale_out) {
+        CU(launch_col_diag_sum(S->inner, colsolve_args(S, scale), S->dsc, st), "diagonal scale");
+        double sum = 0;
+        CU(cudaMemcpyAsync(&sum, S->dsc, sizeof(double), cudaMemcpyDeviceToHost, st), "readback");
+        CU(cudaStreamSynchronize(st), "sync");
+        scale = sum / double(3 * m->h.Nv);
+        if (!(scale > 0)) scale = 1.0;
+        *scale_out = scale;
+    }
+    CU(launch_col_factor(S->inner, colsolve_args(S, scale), st), "column factorisation");
     return STOKES_OK;
 }
 
@@ -120,7 +131,7 @@ int precond_apply(stokes_solver* S, const void* v, void* z, cudaStream_t st) {
     CU(launch_schur_apply(S->inner, m->h.Nv, m->h.Np, S->md, v, z, st), "Schur apply");
     CK(state_gradp(S->st_in, z, S->tz, st));
     CU(vec_axpby(S->nu, 1.0, nullptr, S->inner, v, -1.0, S->inner, S->tz, st), "preconditioner update");
-    CU(launch_col_solve(S->inner, colsolve_args(S), S->tz, z, st), "column solve");
+    CU(launch_col_solve(S->inner, colsolve_args(S, 1.0), S->tz, z, st), "column solve");
     return STOKES_OK;
 }
 
@@ -304,6 +315,15 @@ int stokes_newton_solve(stokes_solver* S, const stokes_params* params, double* u
     const int64_t n = S->n;
     stokes_solve_report R{};
     auto t0 = std::chrono::steady_clock::now();
+    // The constraint rows s (I - P) are scaled to the mean diagonal of the
+    // velocity block at the first linearisation, so that FP32 arithmetic
+    // resolves them next to rows of very different magnitude (SI units);
+    // the solution does not depend on s.
+    stokes_params P = *params;
+    CK(stokes_linearize(S->st_in, &P, up, st));
+    CK(precond_setup(S, &P, st, &P.constraint_scale));
+    R.constraint_scale = P.constraint_scale;
+    params = &P;
     CK(stokes_residual(mesh, params, up, S->r, STOKES_F64, st));
     double nr = 0;
     CK(norm64(S, S->r, n, nr, st));

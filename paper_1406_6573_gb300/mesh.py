@@ -74,7 +74,7 @@ class Mesh:
             pass
 
 
-def params(phys, logbeta=None):
+def params(phys, logbeta=None, constraint_scale=None):
     """stokes_params from stokes_synth.PhysParams; logbeta: device FP64 tensor [Nb] or None."""
     p = capi.stokes_params()
     p.n, p.A, p.C0, p.gamma, p.delta = phys.n, phys.A, phys.C0, phys.gamma, phys.delta
@@ -82,6 +82,7 @@ def params(phys, logbeta=None):
         p.body[c] = phys.body[c]
     p.robin = 1 if phys.robin else 0
     p.logbeta = C.c_void_p(logbeta.data_ptr()) if logbeta is not None else None
+    p.constraint_scale = phys.constraint_scale if constraint_scale is None else constraint_scale
     return p
 
 

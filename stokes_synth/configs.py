@@ -29,6 +29,7 @@ class PhysParams:
     basal_bc: str = "slip"    # 'noslip' (Dirichlet) or 'slip' (u.n = 0 plus Robin)
     robin: bool = True        # basal Robin term  int beta T v . T u
     logbeta: ModalField = None
+    constraint_scale: float = 1.0   # s of the constraint rows s (I - P)
 
     def viscosity_prefactor(self):
         return self.C0 * self.A ** (-1.0 / self.n)

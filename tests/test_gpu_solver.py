@@ -6,6 +6,8 @@ of the oracle's initial residual (the Newton stopping rule), for the plain
 FP64 and the FP32-inner / FP64-outer solver.  Linear solves are checked with
 the oracle's Jacobian: ||b - J x|| <= rtol ||b||, for J and J^T.
 """
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -13,7 +15,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 import stokes_synth as synth
-from oracle import OracleMesh, stokes as ostokes
+from oracle import OracleMesh, newton as onewton, stokes as ostokes
 from paper_1406_6573_gb300 import capi
 from paper_1406_6573_gb300.mesh import Mesh, params
 
@@ -55,13 +57,26 @@ def test_newton_reaches_oracle_solution(name, inner):
         capi.stokes_solver_destroy(s)
 
 
+_LIN = {}
+
+
+def _lin_point(name):
+    """A Newton iterate of the oracle (residual reduced 100x): a physical linearisation point."""
+    if name not in _LIN:
+        wl, o, m, lb = _setup(name)
+        up, _ = onewton.newton_solve(o, wl.phys, lb, rtol=1e-2)
+        _LIN[name] = (wl, o, m, lb, up)
+    return _LIN[name]
+
+
 @pytest.mark.parametrize("transpose", [False, True])
 @pytest.mark.parametrize("inner,rtol", [(capi.STOKES_F64, 1e-10), (capi.STOKES_F32, 1e-9)])
 def test_linear_solve(transpose, inner, rtol):
-    wl, o, m, lb = _setup("slab_8x8x2_q2p1")
+    wl, o, m, lb, up = _lin_point("slab_8x8x2_q2p1")
+    # constraint rows scaled to the velocity-block magnitude (SI units)
+    phys = dataclasses.replace(wl.phys, constraint_scale=1e10)
     lbd = torch.as_tensor(lb, dtype=torch.float64, device="cuda")
-    p = params(wl.phys, lbd)
-    up = synth.uniform_vector(21, o.ndof) * np.concatenate([np.full(3 * o.Nv, 100.0), np.full(o.Np, 1e5)])
+    p = params(phys, lbd)
     b = synth.uniform_vector(21, o.ndof, stream=1)
     s = capi.stokes_solver_create(m.handle, _opts(inner))
     try:
@@ -71,7 +86,7 @@ def test_linear_solve(transpose, inner, rtol):
         assert rc == 0, rep
         xx = x.cpu().numpy()
         # J is symmetric (Section 4.1), so J^T x = J x in the oracle
-        res = b - ostokes.jacobian_apply(o, wl.phys, up, xx, lb)
+        res = b - ostokes.jacobian_apply(o, phys, up, xx, lb)
         assert np.linalg.norm(res) <= 1.01 * rtol * np.linalg.norm(b), (np.linalg.norm(res) / np.linalg.norm(b), rep)
     finally:
         capi.stokes_solver_destroy(s)
