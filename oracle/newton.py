@@ -43,7 +43,7 @@ def element_matrices(mesh, phys, up, logbeta=None):
     ue = stokes.gather(mesh, stokes.project(mesh, u))
     E, A, npr = mesh.E, mesh.A, mesh.npr
     nde = 3 * A + npr
-    K = np.zeros((E, nde, nde))
+    K = np.zeros((E, nde, nde), dtype=np.result_type(up, logbeta, np.float64))
     for j in range(nde):
         we = np.zeros((E, A, 3)); qe = np.zeros((E, npr))
         if j < 3 * A:
@@ -72,13 +72,18 @@ def projector_matrix(mesh):
     return P + sp.csr_matrix((vals, (rows, cols)), shape=(n, n))
 
 
+def assemble_jacobian_complex(mesh, phys, up, logbeta=None):
+    """Same as assemble_jacobian for complex states / parameters."""
+    return assemble_jacobian(mesh, phys, up, logbeta)
+
+
 def assemble_jacobian(mesh, phys, up, logbeta=None):
     """Constrained global Jacobian P (sum_i R_i^T A_i R_i) P + s (I - P), sparse."""
     K = element_matrices(mesh, phys, up, logbeta)
     E, nde = K.shape[0], K.shape[1]
     e, i, j = np.meshgrid(np.arange(E), np.arange(nde), np.arange(nde), indexing="ij")
     Kb = sp.csr_matrix((K.ravel(), ((e * nde + i).ravel(), (e * nde + j).ravel())),
-                       shape=(E * nde, E * nde))
+                       shape=(E * nde, E * nde), dtype=K.dtype)
     Rf = _restriction_full(mesh)
     J = (Rf.T @ Kb @ Rf).tocsr()
     P = projector_matrix(mesh)

@@ -54,8 +54,11 @@ __device__ __forceinline__ void sym6(const T (&g)[3][3], T& E00, T& E11, T& E22,
 // ============================================================ volume kernel
 // Generic element kernel (residual, fused Jacobian, linearisation, A-gradient).
 // T: arithmetic type.  S: element type of the stored state (linearize).
-// exchange scratch of one element slot: 9 buffers (3 per velocity component)
-template <typename T> constexpr int SLOT = 9 * BUFLEN<T>;
+// exchange scratch of one element slot: 9 buffers (3 per velocity component),
+// padded so that consecutive slots start 12 banks apart (fewer shared-memory
+// bank conflicts between the elements of a warp); a multiple of 16 bytes
+template <typename T> constexpr int SLOT =
+    sizeof(T) == 4 ? (9 * BUFLEN<T> + 31 - 12) / 32 * 32 + 12 : 9 * BUFLEN<T> + 2;
 
 template <typename T, typename S, int MODE, bool TRANS>
 __global__ void __launch_bounds__(32 * GW<T>) elem_kernel(ElemArgs a) {
@@ -70,13 +73,15 @@ __global__ void __launch_bounds__(32 * GW<T>) elem_kernel(ElemArgs a) {
     const int ps = a.pspace;
     Rows<T> R;
     R.load(i, j);
+    ColNodes cn;
+    col_nodes(a, e, ij, active, cn);
 
     T G[3][3][Q];     // reference gradients, then reference stresses
     T gq[Q];          // pressure-row integrand  -w detJ div(.)
 
     if constexpr (MODE == MODE_RESIDUAL) {
         T v[3][N1];
-        gather_velocity<T, T>(a, static_cast<const T*>(a.x), e, active, ij, v);
+        gather_velocity<T, T>(a, static_cast<const T*>(a.x), cn, e, active, ij, v);
         if (any_h) hanging_forward<T, 3>(v, h, active, i, j, sb);
         T pc[N1];
         pressure_fold<T, T>(a, static_cast<const T*>(a.x), e, active, i, j, pc);
@@ -109,13 +114,13 @@ __global__ void __launch_bounds__(32 * GW<T>) elem_kernel(ElemArgs a) {
         ref_gradient_T<T, 3, true>(R, G, Sv, out, i, j, sb);
         pressure_rows<T>(gq, a.npr, ps, i, j, ij, active, sb, static_cast<T*>(a.y) + 3 * a.Nv + e * a.npr);
         if (any_h) hanging_transpose<T, 3>(out, h, active, i, j, sb);
-        scatter_velocity<T>(a, static_cast<T*>(a.y), e, active, ij, out);
+        scatter_velocity<T>(a, static_cast<T*>(a.y), cn, e, active, ij, out);
     } else if constexpr (MODE == MODE_APPLY) {
         // linearisation at u, recomputed at every quadrature point
         T lin[8][Q];     // mu w detJ, kappa w detJ, D(u) (6)
         {
             T v[3][N1];
-            gather_velocity<T, T>(a, static_cast<const T*>(a.u), e, active, ij, v);
+            gather_velocity<T, T>(a, static_cast<const T*>(a.u), cn, e, active, ij, v);
             if (any_h) hanging_forward<T, 3>(v, h, active, i, j, sb);
             ref_gradient<T, 3>(R, v, G, i, j, sb);
             #pragma unroll
@@ -135,7 +140,7 @@ __global__ void __launch_bounds__(32 * GW<T>) elem_kernel(ElemArgs a) {
             }
         }
         T v[3][N1];
-        gather_velocity<T, T>(a, static_cast<const T*>(a.x), e, active, ij, v);
+        gather_velocity<T, T>(a, static_cast<const T*>(a.x), cn, e, active, ij, v);
         if (any_h) hanging_forward<T, 3>(v, h, active, i, j, sb);
         T pc[N1];
         pressure_fold<T, T>(a, static_cast<const T*>(a.x), e, active, i, j, pc);
@@ -170,10 +175,10 @@ __global__ void __launch_bounds__(32 * GW<T>) elem_kernel(ElemArgs a) {
         ref_gradient_T<T, 3, false>(R, G, dummy, out, i, j, sb);
         pressure_rows<T>(gq, a.npr, ps, i, j, ij, active, sb, static_cast<T*>(a.y) + 3 * a.Nv + e * a.npr);
         if (any_h) hanging_transpose<T, 3>(out, h, active, i, j, sb);
-        scatter_velocity<T>(a, static_cast<T*>(a.y), e, active, ij, out);
+        scatter_velocity<T>(a, static_cast<T*>(a.y), cn, e, active, ij, out);
     } else if constexpr (MODE == MODE_LINEARIZE) {
         T v[3][N1];
-        gather_velocity<T, double>(a, a.ud, e, active, ij, v);
+        gather_velocity<T, double>(a, a.ud, cn, e, active, ij, v);
         if (any_h) hanging_forward<T, 3>(v, h, active, i, j, sb);
         ref_gradient<T, 3>(R, v, G, i, j, sb);
         S* st = static_cast<S*>(a.state) + e * SSTRIDE;
@@ -212,12 +217,12 @@ __global__ void __launch_bounds__(32 * GW<T>) elem_kernel(ElemArgs a) {
         T Gl[3][3][Q];
         {
             T v[3][N1];
-            gather_velocity<T, double>(a, a.lam, e, active, ij, v);
+            gather_velocity<T, double>(a, a.lam, cn, e, active, ij, v);
             if (any_h) hanging_forward<T, 3>(v, h, active, i, j, sb);
             ref_gradient<T, 3>(R, v, Gl, i, j, sb);
         }
         T v[3][N1];
-        gather_velocity<T, double>(a, a.ud, e, active, ij, v);
+        gather_velocity<T, double>(a, a.ud, cn, e, active, ij, v);
         if (any_h) hanging_forward<T, 3>(v, h, active, i, j, sb);
         ref_gradient<T, 3>(R, v, G, i, j, sb);
         #pragma unroll
@@ -313,6 +318,8 @@ __global__ void __launch_bounds__(32 * StateApplyCfg<T>::W) state_apply_kernel(E
         }
         const int64_t e = g * EPW + es;
         const bool active = (es < EPW) && (e < a.E);
+        ColNodes cn;
+        col_nodes(a, e, ij, active, cn);
         const uint32_t h = active ? a.hang[e] : 0u;
         const bool any_h = a.any_hang ? (__any_sync(0xffffffffu, (h & ((1u << HANG_CHILD0) - 1)) != 0) != 0) : false;
 
@@ -321,7 +328,7 @@ __global__ void __launch_bounds__(32 * StateApplyCfg<T>::W) state_apply_kernel(E
         T G[3][3][Q];
         if constexpr (!PONLY) {
             T v[3][N1];
-            gather_velocity<T, T>(a, x, e, active, ij, v);
+            gather_velocity<T, T>(a, x, cn, e, active, ij, v);
             if (any_h) hanging_forward<T, 3>(v, h, active, i, j, sb);
             ref_gradient<T, 3>(R, v, G, i, j, sb);
         } else {
@@ -385,7 +392,7 @@ __global__ void __launch_bounds__(32 * StateApplyCfg<T>::W) state_apply_kernel(E
         ref_gradient_T<T, 3, false>(R, G, dummy, out, i, j, sb);
         if constexpr (!PONLY) pressure_rows<T>(gq, a.npr, ps, i, j, ij, active, sb, y + 3 * a.Nv + e * a.npr);
         if (any_h) hanging_transpose<T, 3>(out, h, active, i, j, sb);
-        scatter_velocity<T>(a, y, e, active, ij, out);
+        scatter_velocity<T>(a, y, cn, e, active, ij, out);
         __syncwarp();
     }
 }

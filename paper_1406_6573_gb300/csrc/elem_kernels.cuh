@@ -441,30 +441,47 @@ __device__ __forceinline__ void project3(const double* P, T& x0, T& x1, T& x2) {
     x2 = p02 * a + p12 * b + p22 * c;
 }
 
-// Global node of slot (ij, l) of element e: from the element map, or computed
-// from the lattice on conforming meshes (no map read).
-__device__ __forceinline__ int64_t node_of(const ElemArgs& a, int64_t e, int ij, int l) {
-    if (a.lat_nx > 0) {
-        const int64_t ex = e % a.lat_nx, r = e / a.lat_nx;
-        const int64_t ey = r % a.lat_ny, ez = r / a.lat_ny;
-        int64_t I = ex * K + ij % N1, J = ey * K + ij / N1;
-        const int64_t Lz = ez * K + l;
-        if (I >= a.lat_NX) I -= a.lat_NX;
-        if (J >= a.lat_NY) J -= a.lat_NY;
-        return I + a.lat_NX * (J + a.lat_NY * Lz);
+// Global nodes of the thread's column of slots (ij, l = 0..N1-1) of element e:
+// read from the element map, or computed from the lattice on conforming
+// meshes (node I + NX (J + NY L); no map read).  Filled once per element and
+// shared by the gather and the scatter.
+struct ColNodes {
+    int32_t g[N1];
+};
+
+__device__ __forceinline__ void col_nodes(const ElemArgs& a, int64_t e, int ij, bool active, ColNodes& cn) {
+    if (!active) {
+        #pragma unroll
+        for (int l = 0; l < N1; ++l) cn.g[l] = 0;
+        return;
     }
-    return a.nodes[e * N3 + ij + N2 * l];
+    if (a.lat_nx > 0) {
+        const int e32 = int(e), nx = int(a.lat_nx), ny = int(a.lat_ny);
+        const int ex = e32 % nx, r = e32 / nx;
+        const int ey = r % ny, ez = r / ny;
+        int I = ex * K + ij % N1, J = ey * K + ij / N1;
+        const int NX = int(a.lat_NX), NY = int(a.lat_NY);
+        if (I >= NX) I -= NX;
+        if (J >= NY) J -= NY;
+        const int g0 = I + NX * (J + NY * (ez * K));
+        const int step = NX * NY;
+        #pragma unroll
+        for (int l = 0; l < N1; ++l) cn.g[l] = g0 + l * step;
+    } else {
+        #pragma unroll
+        for (int l = 0; l < N1; ++l) cn.g[l] = a.nodes[e * N3 + ij + N2 * l];
+    }
 }
 
 // Velocity columns of element e (3 components) from a state vector x,
 // with the basal projector applied at bottom-plane slots.
 template <typename T, typename TIN>
-__device__ __forceinline__ void gather_velocity(const ElemArgs& a, const TIN* x, int64_t e, bool active,
-                                                int ij, T (&v)[3][N1]) {
+__device__ __forceinline__ void gather_velocity(const ElemArgs& a, const TIN* x, const ColNodes& cn, int64_t e,
+                                                bool active, int ij, T (&v)[3][N1]) {
     #pragma unroll
     for (int l = 0; l < N1; ++l) {
         if (active) {
-            const int64_t g = node_of(a, e, ij, l);
+            const int64_t g = cn.g[l];
             v[0][l] = T(ld(x + 3 * g));
             v[1][l] = T(ld(x + 3 * g + 1));
             v[2][l] = T(ld(x + 3 * g + 2));
@@ -479,14 +496,14 @@ __device__ __forceinline__ void gather_velocity(const ElemArgs& a, const TIN* x,
 }
 
 template <typename T>
-__device__ __forceinline__ void scatter_velocity(const ElemArgs& a, T* y, int64_t e, bool active, int ij,
-                                                 T (&v)[3][N1]) {
+__device__ __forceinline__ void scatter_velocity(const ElemArgs& a, T* y, const ColNodes& cn, int64_t e, bool active,
+                                                 int ij, T (&v)[3][N1]) {
     if (!active) return;
     const int pi = a.pidx[e];
     if (pi >= 0) project3<T>(a.pel + int64_t(pi) * 6 * N2 + ij, v[0][0], v[1][0], v[2][0]);
     #pragma unroll
     for (int l = 0; l < N1; ++l) {
-        const int64_t g = node_of(a, e, ij, l);
+        const int64_t g = cn.g[l];
         atomic_add(y + 3 * g, v[0][l]);
         atomic_add(y + 3 * g + 1, v[1][l]);
         atomic_add(y + 3 * g + 2, v[2][l]);
