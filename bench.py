@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-solve", action="store_true",
+                    help="skip the time-to-1e-10 Newton solves (FP32-inner vs FP64)")
     return ap.parse_args()
 
 
@@ -314,6 +316,41 @@ def run_ours(args):
         variants = {k: {"ms": round(val, 4), "MDoF/s": round(ndof / (val / 1e3) / 1e6, 1)} for k, val in v.items()}
         del st64
 
+    # time to a 1e-10 relative residual from u = 0: FP32-inner / FP64-outer vs plain FP64
+    solve = None
+    if not args.no_solve:
+        solve = {}
+        for tag, inner in (("fp32_inner", capi.STOKES_F32), ("fp64", capi.STOKES_F64)):
+            op = capi.stokes_solver_opts()
+            op.inner_prec = inner
+            op.restart = 30
+            op.max_krylov = 4000
+            op.max_newton = 60
+            op.rtol = 1e-10
+            op.eta_max = 0.1
+            sv = capi.stokes_solver_create(mesh.handle, op)
+            u0 = torch.zeros(ndof, dtype=torch.float64, device="cuda")
+            barrier()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rc, rep = capi.stokes_newton_solve(sv, p, u0, stream)
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t0
+            if world > 1:
+                t = torch.tensor([wall], device="cuda")
+                dist.all_reduce(t, op=dist.ReduceOp.MAX)
+                wall = float(t.item())
+            capi.stokes_solver_destroy(sv)
+            solve[tag] = {"seconds": round(wall, 4), "converged": rep["converged"],
+                          "newton_its": rep["newton_its"], "krylov_its": rep["krylov_its"],
+                          "final_rel_residual": rep["res_final"] / rep["res0"]}
+            if tag == "fp32_inner":
+                u_fp32 = u0
+            else:
+                du = (u0 - u_fp32).norm() / u0.norm()
+                solve["rel_diff_fp32_vs_fp64_solution"] = float(du)
+        solve["speedup_fp32_inner"] = round(solve["fp64"]["seconds"] / solve["fp32_inner"]["seconds"], 3)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, text, n, dt = cpu_oracle_rate(wl, args.cpu_seconds)
@@ -340,11 +377,12 @@ def run_ours(args):
             "gpu_launches": int(prof["element"][0] + prof["face"][0] + prof["constraint"][0]),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                          "frac": achieved / hbm_peak, "traffic": None,
-                         "kernel": "state_apply_kernel<float>",
+                         "kernel": "state_apply_cpt_kernel<float>" if wl.k == 2 else "state_apply_kernel<float>",
                          "bytes_per_launch": bytes_alg, "avg_launch_ms": el_avg_s * 1e3,
                          "peak_source": f"{peak_src} hbm_gbs"},
             "kernel_time_share": {k: round(v / tot, 4) for k, v in shares.items()} if tot > 0 else {},
             "e2e": e2e,
+            "time_to_1e-10": solve,
             "variants": variants,
             "cpu_baseline": cpu,
         }

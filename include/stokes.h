@@ -203,7 +203,7 @@ typedef struct stokes_solver stokes_solver;
 
 typedef struct {
     int inner_prec;      /* STOKES_F32 (mixed precision) or STOKES_F64               */
-    int restart;         /* FGMRES restart length m (default 30)                      */
+    int restart;         /* FGMRES restart length m (default 30, at most 31)          */
     int max_krylov;      /* Krylov iterations per linear solve (default 1000)         */
     int max_newton;      /* Newton steps (default 50)                                 */
     double rtol;         /* Newton stop: ||r|| <= rtol ||r_0|| (default 1e-10)        */

@@ -4,6 +4,9 @@
 
 #include "elem_kernels.cuh"
 #include "tma.cuh"
+#if STOKES_K == 2
+#include "cpt_kernel.cuh"
+#endif
 
 namespace stokes {
 namespace dev {
@@ -181,7 +184,8 @@ __global__ void __launch_bounds__(32 * GW<T>) elem_kernel(ElemArgs a) {
         gather_velocity<T, double>(a, a.ud, cn, e, active, ij, v);
         if (any_h) hanging_forward<T, 3>(v, h, active, i, j, sb);
         ref_gradient<T, 3>(R, v, G, i, j, sb);
-        S* st = static_cast<S*>(a.state) + e * SSTRIDE;
+        S* st = static_cast<S*>(a.state);
+        const bool soa = a.state_soa != 0;
         #pragma unroll
         for (int lq = 0; lq < Q; ++lq) {
             const int qp = sidx(i, j, lq);
@@ -197,19 +201,19 @@ __global__ void __launch_bounds__(32 * GW<T>) elem_kernel(ElemArgs a) {
             const T mk = -T(2) * T(a.gamma) * T(a.pexp) * mu * wdj / (T(a.gamma) * DD + T(a.delta));
             const T sq = sqrt(mk > T(0) ? mk : T(0));
             if (active) {
-                if (qp == 0) { st[0] = S(Ji[0]); st[1] = S(Ji[4]); }
-                S* q = st + 2 + qp;
-                q[0 * Q3] = S(Ji[6]);
-                q[1 * Q3] = S(Ji[7]);
-                q[2 * Q3] = S(Ji[8]);
-                q[3 * Q3] = S(wdj);
-                q[4 * Q3] = S(mu * wdj);
-                q[5 * Q3] = S(sq * E00);
-                q[6 * Q3] = S(sq * E11);
-                q[7 * Q3] = S(sq * E22);
-                q[8 * Q3] = S(sq * E01);
-                q[9 * Q3] = S(sq * E02);
-                q[10 * Q3] = S(sq * E12);
+                auto put = [&](int slot, T v) { st[state_index(soa, a.E, e, slot)] = S(v); };
+                if (qp == 0) { put(0, Ji[0]); put(1, Ji[4]); }
+                put(2 + 0 * Q3 + qp, Ji[6]);
+                put(2 + 1 * Q3 + qp, Ji[7]);
+                put(2 + 2 * Q3 + qp, Ji[8]);
+                put(2 + 3 * Q3 + qp, wdj);
+                put(2 + 4 * Q3 + qp, mu * wdj);
+                put(2 + 5 * Q3 + qp, sq * E00);
+                put(2 + 6 * Q3 + qp, sq * E11);
+                put(2 + 7 * Q3 + qp, sq * E22);
+                put(2 + 8 * Q3 + qp, sq * E01);
+                put(2 + 9 * Q3 + qp, sq * E02);
+                put(2 + 10 * Q3 + qp, sq * E12);
             }
         }
     } else if constexpr (MODE == MODE_GRAD_A) {
@@ -644,8 +648,14 @@ inline int launch_elem_any(int mode, int prec, int state_prec, bool trans, const
         case MODE_STATE_APPLY:
             // the pointwise map of Eq. 2.7 is symmetric: the transposed apply
             // runs the same kernel
+#if STOKES_K == 2
+            if (f32 && a.state_soa) return launch_state_apply_cpt<float, false>(a, s);
+#endif
             return f32 ? launch_state_apply_t<float, false>(a, s) : launch_state_apply_t<double, false>(a, s);
         case MODE_STATE_GRADP:
+#if STOKES_K == 2
+            if (f32 && a.state_soa) return launch_state_apply_cpt<float, true>(a, s);
+#endif
             return f32 ? launch_state_apply_t<float, true>(a, s) : launch_state_apply_t<double, true>(a, s);
         case MODE_GRAD_A:
             return launch_elem_t<double, double, MODE_GRAD_A, false>(a, s);
@@ -662,8 +672,8 @@ inline int launch_face_any(int mode, int prec, const FaceArgs& a, cudaStream_t s
 // Upload the degree-K tables (host struct Tables1D for each pressure space).
 inline int upload_tables_any(const void* p) {
     const Tables1D* t = static_cast<const Tables1D*>(p);   // t[0]: P space, t[1]: Q space
-    double B[Q][N1], Dg[Q][Q], I[2][N1][N1], P1[2][Q][N1];
-    float fb[Q][N1], fd[Q][Q], fi[2][N1][N1], fp[2][Q][N1];
+    double B[Q][N1], Dg[Q][Q], I[2][N1][N1], P1[2][Q][N1], Bdv[Q][N1];
+    float fb[Q][N1], fd[Q][Q], fi[2][N1][N1], fp[2][Q][N1], fbd[Q][N1];
     int pm[2][NPRK > 0 ? NPRK : 1][3] = {};
     int np[2];
     for (int a = 0; a < Q; ++a)
@@ -673,6 +683,13 @@ inline int upload_tables_any(const void* p) {
     for (int hh = 0; hh < 2; ++hh)
         for (int a = 0; a < N1; ++a)
             for (int b = 0; b < N1; ++b) { I[hh][a][b] = t[0].I[hh][a][b]; fi[hh][a][b] = float(I[hh][a][b]); }
+    for (int a = 0; a < Q; ++a)
+        for (int b = 0; b < N1; ++b) {
+            double sum = 0;
+            for (int m = 0; m < Q; ++m) sum += Dg[a][m] * B[m][b];
+            Bdv[a][b] = sum;
+            fbd[a][b] = float(sum);
+        }
     for (int sp = 0; sp < 2; ++sp) {
         np[sp] = t[sp].npr;
         for (int a = 0; a < Q; ++a)
@@ -691,6 +708,8 @@ inline int upload_tables_any(const void* p) {
     if (e == cudaSuccess) e = cudaMemcpyToSymbol(fDg, fd, sizeof(fd));
     if (e == cudaSuccess) e = cudaMemcpyToSymbol(fI, fi, sizeof(fi));
     if (e == cudaSuccess) e = cudaMemcpyToSymbol(fP1, fp, sizeof(fp));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(cBd, Bdv, sizeof(Bdv));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(fBd, fbd, sizeof(fbd));
     return int(e);
 }
 

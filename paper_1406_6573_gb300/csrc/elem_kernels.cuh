@@ -76,6 +76,8 @@ __constant__ float fB[Q][N1];
 __constant__ float fDg[Q][Q];
 __constant__ float fI[2][N1][N1];
 __constant__ float fP1[2][Q][N1];
+__constant__ double cBd[Q][N1];       // (Dg B)[iq][i]: derivative of GLL Lagrange i at Gauss point iq
+__constant__ float fBd[Q][N1];
 
 template <typename T> struct Tab;
 template <> struct Tab<double> {
@@ -83,12 +85,14 @@ template <> struct Tab<double> {
     static __device__ __forceinline__ double Dg(int a, int b) { return cDg[a][b]; }
     static __device__ __forceinline__ double I(int h, int a, int b) { return cI[h][a][b]; }
     static __device__ __forceinline__ double P1(int s, int a, int b) { return cP1[s][a][b]; }
+    static __device__ __forceinline__ double Bd(int a, int b) { return cBd[a][b]; }
 };
 template <> struct Tab<float> {
     static __device__ __forceinline__ float B(int a, int b) { return fB[a][b]; }
     static __device__ __forceinline__ float Dg(int a, int b) { return fDg[a][b]; }
     static __device__ __forceinline__ float I(int h, int a, int b) { return fI[h][a][b]; }
     static __device__ __forceinline__ float P1(int s, int a, int b) { return fP1[s][a][b]; }
+    static __device__ __forceinline__ float Bd(int a, int b) { return fBd[a][b]; }
 };
 
 // Table entries whose index depends on the thread's (i, j): loaded once into
@@ -114,6 +118,13 @@ template <typename T> struct Rows {
         }
     }
 };
+
+// Linearised-state slot s of element e: element-major ([E][SSTRIDE]) or, for
+// the lane-per-component kernel, slot-major ([slot][E], coalesced across
+// consecutive elements).
+__device__ __forceinline__ int64_t state_index(bool soa, int64_t E, int64_t e, int s) {
+    return soa ? int64_t(s) * E + e : e * SSTRIDE + s;
+}
 
 // --------------------------------------------------------------- helpers
 template <typename T> __device__ __forceinline__ T ld(const T* p) { return __ldg(p); }

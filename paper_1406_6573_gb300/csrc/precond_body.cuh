@@ -41,8 +41,9 @@ __global__ void __launch_bounds__(256) colblock_kernel(ColArgs a) {
     if (slot_on_hanging_entity(h, idx, K)) return;
     const int64_t na = a.nodes[e * N3 + sl];
     const int col = a.col_of[na], pa = a.pos_of[na];
-    const T* st = static_cast<const T*>(a.state) + e * SSTRIDE;
-    const T ia = st[0], ib = st[1];
+    const T* st0 = static_cast<const T*>(a.state);
+    auto stv = [&](int slot) { return st0[state_index(a.state_soa != 0, a.E, e, slot)]; };
+    const T ia = stv(0), ib = stv(1);
     const int bw = a.bw, W = 2 * a.bw + 1;
     T* A = static_cast<T*>(a.A);
     for (int l2 = 0; l2 < N1; ++l2) {
@@ -56,10 +57,10 @@ __global__ void __launch_bounds__(256) colblock_kernel(ColArgs a) {
             for (int jq = 0; jq < Q; ++jq)
                 for (int iq = 0; iq < Q; ++iq) {
                     const int qp = iq + Q * (jq + Q * lq);
-                    const T* f = st + 2 + qp;
-                    const T g0 = f[0], g1 = f[Q3], g2 = f[2 * Q3], muw = f[4 * Q3];
-                    const T D00 = f[5 * Q3], D11 = f[6 * Q3], D22 = f[7 * Q3];
-                    const T D01 = f[8 * Q3], D02 = f[9 * Q3], D12 = f[10 * Q3];
+                    const int f = 2 + qp;
+                    const T g0 = stv(f), g1 = stv(f + Q3), g2 = stv(f + 2 * Q3), muw = stv(f + 4 * Q3);
+                    const T D00 = stv(f + 5 * Q3), D11 = stv(f + 6 * Q3), D22 = stv(f + 7 * Q3);
+                    const T D01 = stv(f + 8 * Q3), D02 = stv(f + 9 * Q3), D12 = stv(f + 10 * Q3);
                     const T bi = Tab<T>::B(iq, i), bj = Tab<T>::B(jq, j);
                     const T dbi = Bd<T>(iq, i), dbj = Bd<T>(jq, j);
                     const T ra[3] = {dbi * bj * Tab<T>::B(lq, l), bi * dbj * Tab<T>::B(lq, l), bi * bj * Bd<T>(lq, l)};
@@ -119,13 +120,14 @@ __global__ void __launch_bounds__(256) schur_diag_kernel(ColArgs a) {
     const int b = int(t - e * a.npr);
     const int ps = a.pspace;
     const int m0 = cPm[ps][b][0], m1 = cPm[ps][b][1], m2 = cPm[ps][b][2];
-    const T* st = static_cast<const T*>(a.state) + e * SSTRIDE;
+    const T* st0 = static_cast<const T*>(a.state);
+    auto stv = [&](int slot) { return st0[state_index(a.state_soa != 0, a.E, e, slot)]; };
     T s = 0;
     for (int lq = 0; lq < Q; ++lq)
         for (int jq = 0; jq < Q; ++jq)
             for (int iq = 0; iq < Q; ++iq) {
                 const int qp = iq + Q * (jq + Q * lq);
-                const T wdj = st[2 + 3 * Q3 + qp], muw = st[2 + 4 * Q3 + qp];
+                const T wdj = stv(2 + 3 * Q3 + qp), muw = stv(2 + 4 * Q3 + qp);
                 const T psi = Tab<T>::P1(ps, iq, m0) * Tab<T>::P1(ps, jq, m1) * Tab<T>::P1(ps, lq, m2);
                 s += psi * psi * wdj * wdj / muw;
             }

@@ -110,6 +110,7 @@ int precond_setup(stokes_solver* S, const stokes_params* p, cudaStream_t st, dou
     a.nodes = m->d_nodes; a.hang = m->d_hang; a.col_of = m->d_col_of; a.pos_of = m->d_pos_of;
     a.fidx = m->d_fidx; a.fmap = m->d_fmap; a.fgeo = m->d_fgeo; a.logbeta = p->logbeta;
     a.state = S->st_in->d_state; a.A = S->A; a.md = S->md;
+    a.state_soa = state_is_soa(m->h.k, S->inner);
     CU(launch_precond_assembly(m->h.k, S->inner, a, st), "preconditioner assembly");
     double scale = p->constraint_scale;
     if (scale_out) {
@@ -252,6 +253,7 @@ int stokes_solver_create(const stokes_mesh* mesh, const stokes_solver_opts* opts
     stokes_solver_opts o{STOKES_F32, 30, 1000, 50, 1e-10, 0.1};
     if (opts) o = *opts;
     if (o.restart < 1) o.restart = 30;
+    if (o.restart > 31) o.restart = 31;   // multi-dot / multi-axpy handle at most 32 vectors
     if (o.max_krylov < 1) o.max_krylov = 1000;
     if (o.max_newton < 1) o.max_newton = 50;
     if (!(o.rtol > 0)) o.rtol = 1e-10;

@@ -1,0 +1,71 @@
+"""GPU adjoint gradient (torch.autograd.Function over the C-ABI) against the
+oracle's adjoint gradient (itself pinned by a complex-step derivative of the
+forward solve) and against central finite differences of GPU forward solves."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import stokes_synth as synth
+from oracle import OracleMesh, adjoint as oadjoint
+from paper_1406_6573_gb300 import capi
+from paper_1406_6573_gb300.adjoint import StokesForward, StokesProblem, misfit, top_nodes
+from paper_1406_6573_gb300.mesh import Mesh
+
+
+def _problem(name):
+    wl = synth.workload(name)
+    o = OracleMesh(wl)
+    lb_ref = wl.phys.logbeta(*o.basal_coords()[:, :2].T)
+    lb_true = lb_ref + 0.3 * np.cos(2 * np.pi * o.basal_coords()[:, 0] / wl.Lx)
+    top_o = oadjoint.top_nodes(o)
+    _, _, _, up_true = oadjoint.gradient(o, wl.phys, lb_true, np.zeros((top_o.size, 3)), top_o)
+    u_obs = up_true[: 3 * o.Nv].reshape(o.Nv, 3)[top_o]
+    return wl, o, lb_ref, u_obs, top_o
+
+
+@pytest.mark.parametrize("inner", [capi.STOKES_F64, capi.STOKES_F32])
+def test_adjoint_gradient_matches_oracle(inner):
+    wl, o, lb_ref, u_obs, top_o = _problem("cbox_3x3x2_q2p1")
+    J_o, g_o, gA_o, _ = oadjoint.gradient(o, wl.phys, lb_ref, u_obs, top_o)
+    m = Mesh(wl, device=0)
+    prob = StokesProblem(m, wl.phys, inner_prec=inner, rtol=1e-12, adjoint_rtol=1e-11)
+    top = top_nodes(m)
+    assert np.array_equal(top.cpu().numpy(), top_o)
+    lb = torch.as_tensor(lb_ref, dtype=torch.float64, device="cuda").requires_grad_(True)
+    A = torch.tensor(wl.phys.A, dtype=torch.float64, device="cuda", requires_grad=True)
+    up = StokesForward.apply(lb, A, prob)
+    J = misfit(up, torch.as_tensor(u_obs, device="cuda"), m, top)
+    J.backward()
+    assert abs(J.item() - J_o) <= 1e-9 * J_o
+    g = lb.grad.cpu().numpy()
+    assert np.linalg.norm(g - g_o) <= 1e-7 * np.linalg.norm(g_o), np.linalg.norm(g - g_o) / np.linalg.norm(g_o)
+    assert abs(A.grad.item() - gA_o) <= 1e-7 * abs(gA_o)
+    prob.close()
+
+
+def test_adjoint_gradient_central_differences():
+    wl, o, lb_ref, u_obs, top_o = _problem("cbox_3x3x2_q2p1")
+    m = Mesh(wl, device=0)
+    prob = StokesProblem(m, wl.phys, inner_prec=capi.STOKES_F32, rtol=1e-13, adjoint_rtol=1e-11)
+    top = top_nodes(m)
+    uo = torch.as_tensor(u_obs, device="cuda")
+    A = torch.tensor(wl.phys.A, dtype=torch.float64, device="cuda")
+    lb = torch.as_tensor(lb_ref, dtype=torch.float64, device="cuda").requires_grad_(True)
+    J = misfit(StokesForward.apply(lb, A, prob), uo, m, top)
+    J.backward()
+    g = lb.grad.clone()
+    rng = np.random.default_rng(3)
+    h = 1e-6
+    for _ in range(3):
+        d = torch.as_tensor(rng.uniform(-1, 1, size=m.Nb), device="cuda")
+        with torch.no_grad():
+            Jp = misfit(StokesForward.apply(lb + h * d, A, prob), uo, m, top).item()
+            Jm = misfit(StokesForward.apply(lb - h * d, A, prob), uo, m, top).item()
+        fd = (Jp - Jm) / (2 * h)
+        ad = float((g * d).sum())
+        assert abs(fd - ad) <= 1e-5 * abs(ad), (fd, ad)
+    prob.close()
