@@ -199,8 +199,8 @@ class OracleMesh:
     def _phys(self, Pref):
         """Exact map of reference positions (unwrapped) of coarse cells."""
         wl = self.wl
-        x = wl.Lx * Pref[..., 0] / wl.nx
-        y = wl.Ly * Pref[..., 1] / wl.ny
+        x = wl.x0 + wl.Lx * Pref[..., 0] / wl.nx
+        y = wl.y0 + wl.Ly * Pref[..., 1] / wl.ny
         b = wl.bed(x, y)
         s = wl.surface(x, y)
         z = b + (Pref[..., 2] / wl.nz) * (s - b)

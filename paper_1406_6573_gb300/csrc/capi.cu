@@ -124,8 +124,6 @@ int launch_precond_assembly(int k, int prec, const ColArgs& a, cudaStream_t s) {
 
 // Linearised states of degree 2 in FP32 are stored slot-major for the
 // lane-per-component apply; all others element-major.
-bool state_is_soa(int k, int prec) { return k == 2 && prec == STOKES_F32; }
-
 int check_common(const stokes_mesh* m, int prec) {
     if (!m) return fail(STOKES_E_INVAL, "mesh is NULL");
     if (!m->on_device) return fail(STOKES_E_INVAL, "mesh was built for the host only (device = -1)");
@@ -180,7 +178,6 @@ int operator_sequence(const stokes_mesh* m, const stokes_params* p, int mode, in
     if (e) return cuda_fail(cudaError_t(e), "clearing the output");
     ElemArgs a = elem_args(m, p);
     a.x = x; a.y = y; a.u = u; a.cstate = cstate;
-    a.state_soa = state_is_soa(m->h.k, state_prec);
     e = timed(m, 1, s, [&] { return launch_elem(m->h.k, mode, prec, state_prec, trans, a, s); });
     if (e) return cuda_fail(cudaError_t(e), "element kernel launch");
     if (mode == MODE_STATE_GRADP) return STOKES_OK;   // zero velocity input: no Robin or (I - P) term
@@ -444,7 +441,6 @@ int stokes_linearize(stokes_state* state, const stokes_params* params, const dou
     ElemArgs a = elem_args(mesh, params);
     a.ud = up_lin;
     a.state = state->d_state;
-    a.state_soa = state_is_soa(mesh->h.k, state->prec);
     int e = launch_elem(mesh->h.k, MODE_LINEARIZE, STOKES_F64, state->prec, false, a,
                         static_cast<cudaStream_t>(stream));
     if (e) return cuda_fail(cudaError_t(e), "linearize kernel launch");

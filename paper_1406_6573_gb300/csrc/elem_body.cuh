@@ -4,9 +4,6 @@
 
 #include "elem_kernels.cuh"
 #include "tma.cuh"
-#if STOKES_K == 2
-#include "cpt_kernel.cuh"
-#endif
 
 namespace stokes {
 namespace dev {
@@ -185,7 +182,6 @@ __global__ void __launch_bounds__(32 * GW<T>) elem_kernel(ElemArgs a) {
         if (any_h) hanging_forward<T, 3>(v, h, active, i, j, sb);
         ref_gradient<T, 3>(R, v, G, i, j, sb);
         S* st = static_cast<S*>(a.state);
-        const bool soa = a.state_soa != 0;
         #pragma unroll
         for (int lq = 0; lq < Q; ++lq) {
             const int qp = sidx(i, j, lq);
@@ -201,7 +197,7 @@ __global__ void __launch_bounds__(32 * GW<T>) elem_kernel(ElemArgs a) {
             const T mk = -T(2) * T(a.gamma) * T(a.pexp) * mu * wdj / (T(a.gamma) * DD + T(a.delta));
             const T sq = sqrt(mk > T(0) ? mk : T(0));
             if (active) {
-                auto put = [&](int slot, T v) { st[state_index(soa, a.E, e, slot)] = S(v); };
+                auto put = [&](int slot, T v) { st[state_index(e, slot)] = S(v); };
                 if (qp == 0) { put(0, Ji[0]); put(1, Ji[4]); }
                 put(2 + 0 * Q3 + qp, Ji[6]);
                 put(2 + 1 * Q3 + qp, Ji[7]);
@@ -648,14 +644,8 @@ inline int launch_elem_any(int mode, int prec, int state_prec, bool trans, const
         case MODE_STATE_APPLY:
             // the pointwise map of Eq. 2.7 is symmetric: the transposed apply
             // runs the same kernel
-#if STOKES_K == 2
-            if (f32 && a.state_soa) return launch_state_apply_cpt<float, false>(a, s);
-#endif
             return f32 ? launch_state_apply_t<float, false>(a, s) : launch_state_apply_t<double, false>(a, s);
         case MODE_STATE_GRADP:
-#if STOKES_K == 2
-            if (f32 && a.state_soa) return launch_state_apply_cpt<float, true>(a, s);
-#endif
             return f32 ? launch_state_apply_t<float, true>(a, s) : launch_state_apply_t<double, true>(a, s);
         case MODE_GRAD_A:
             return launch_elem_t<double, double, MODE_GRAD_A, false>(a, s);

@@ -119,12 +119,8 @@ template <typename T> struct Rows {
     }
 };
 
-// Linearised-state slot s of element e: element-major ([E][SSTRIDE]) or, for
-// the lane-per-component kernel, slot-major ([slot][E], coalesced across
-// consecutive elements).
-__device__ __forceinline__ int64_t state_index(bool soa, int64_t E, int64_t e, int s) {
-    return soa ? int64_t(s) * E + e : e * SSTRIDE + s;
-}
+// Linearised-state slot s of element e (element-major, [E][SSTRIDE]).
+__device__ __forceinline__ int64_t state_index(int64_t e, int s) { return e * SSTRIDE + s; }
 
 // --------------------------------------------------------------- helpers
 template <typename T> __device__ __forceinline__ T ld(const T* p) { return __ldg(p); }

@@ -90,7 +90,6 @@ struct stokes_state {
 namespace stokes {
 
 int check_common(const stokes_mesh* m, int prec);
-bool state_is_soa(int k, int prec);
 int check_params(const stokes_mesh* m, const stokes_params* p);
 ElemArgs elem_args(const stokes_mesh* m, const stokes_params* p);
 FaceArgs face_args(const stokes_mesh* m, const stokes_params* p);

@@ -45,7 +45,6 @@ struct ElemArgs {
     double gA_scale;
     int64_t lat_nx, lat_ny, lat_NX, lat_NY;   // conforming lattice (lat_nx > 0): node index
                                // computed as I + NX (J + NY L) instead of read from nodes
-    int state_soa;             // linearised state stored slot-major ([slot][E])
     int* err;                  // device status word (bounded waits that expired)
     int persistent_blocks;     // grid size of the persistent state-apply kernel
 };

@@ -22,7 +22,6 @@ struct ColArgs {
     const double* fgeo;        // [nF][4][q^2]
     const double* logbeta;     // [Nb]
     const void* state;         // linearised state (element type = prec)
-    int state_soa;             // slot-major layout ([slot][E])
     void* A;                   // [3 colmax][2 bw + 1][ncol] banded column matrices
     void* md;                  // [E npr] diagonal of M(1/mu)
 };

@@ -42,7 +42,7 @@ __global__ void __launch_bounds__(256) colblock_kernel(ColArgs a) {
     const int64_t na = a.nodes[e * N3 + sl];
     const int col = a.col_of[na], pa = a.pos_of[na];
     const T* st0 = static_cast<const T*>(a.state);
-    auto stv = [&](int slot) { return st0[state_index(a.state_soa != 0, a.E, e, slot)]; };
+    auto stv = [&](int slot) { return st0[state_index(e, slot)]; };
     const T ia = stv(0), ib = stv(1);
     const int bw = a.bw, W = 2 * a.bw + 1;
     T* A = static_cast<T*>(a.A);
@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(256) schur_diag_kernel(ColArgs a) {
     const int ps = a.pspace;
     const int m0 = cPm[ps][b][0], m1 = cPm[ps][b][1], m2 = cPm[ps][b][2];
     const T* st0 = static_cast<const T*>(a.state);
-    auto stv = [&](int slot) { return st0[state_index(a.state_soa != 0, a.E, e, slot)]; };
+    auto stv = [&](int slot) { return st0[state_index(e, slot)]; };
     T s = 0;
     for (int lq = 0; lq < Q; ++lq)
         for (int jq = 0; jq < Q; ++jq)

@@ -73,7 +73,7 @@ void free_solver(stokes_solver* s) {
 
 // ||x||_2 of an FP64 device vector (synchronises)
 int norm64(stokes_solver* S, const double* x, int64_t n, double& out, cudaStream_t st) {
-    CU(vec_multidot(n, STOKES_F64, x, 0, 1, STOKES_F64, x, S->dsc, st), "norm");
+    CU(vec_multidot(n, STOKES_F64, x, 0, 0, STOKES_F64, x, S->dsc, 1, st), "norm");
     double h = 0;
     CU(cudaMemcpyAsync(&h, S->dsc, sizeof(double), cudaMemcpyDeviceToHost, st), "norm readback");
     CU(cudaStreamSynchronize(st), "norm sync");
@@ -110,7 +110,6 @@ int precond_setup(stokes_solver* S, const stokes_params* p, cudaStream_t st, dou
     a.nodes = m->d_nodes; a.hang = m->d_hang; a.col_of = m->d_col_of; a.pos_of = m->d_pos_of;
     a.fidx = m->d_fidx; a.fmap = m->d_fmap; a.fgeo = m->d_fgeo; a.logbeta = p->logbeta;
     a.state = S->st_in->d_state; a.A = S->A; a.md = S->md;
-    a.state_soa = state_is_soa(m->h.k, S->inner);
     CU(launch_precond_assembly(m->h.k, S->inner, a, st), "preconditioner assembly");
     double scale = p->constraint_scale;
     if (scale_out) {
@@ -148,7 +147,7 @@ int fgmres_cycle(stokes_solver* S, bool trans, double tol_rel, int max_its, int&
     std::vector<double> H(size_t(m + 1) * m, 0.0), cs(m, 0.0), sn(m, 0.0), g(m + 1, 0.0), h(m + 2, 0.0);
     // V_0 = b / ||b||
     CU(vec_axpby(n, 1.0, nullptr, ip, S->tin, 0.0, ip, Vj(0), st), "copy");
-    CU(vec_multidot(n, ip, Vj(0), 0, 1, ip, Vj(0), S->dsc, st), "dot");
+    CU(vec_multidot(n, ip, Vj(0), 0, 0, ip, Vj(0), S->dsc, 1, st), "dot");
     CU(cudaMemcpyAsync(h.data(), S->dsc, sizeof(double), cudaMemcpyDeviceToHost, st), "readback");
     CU(cudaStreamSynchronize(st), "sync");
     const double beta = std::sqrt(h[0]);
@@ -160,28 +159,35 @@ int fgmres_cycle(stokes_solver* S, bool trans, double tol_rel, int max_its, int&
     for (; k < m; ++k) {
         CK(precond_apply(S, Vj(k), Zj(k), st));
         CK(op_inner(S, Zj(k), Vj(k + 1), trans, st));
-        // classical Gram-Schmidt, FP64 accumulation: h = V^T w and ||w||^2
-        CU(vec_multidot(n, ip, S->V, n, k + 1, ip, Vj(k + 1), S->dsc, st), "orthogonalisation dots");
-        CU(vec_multidot(n, ip, Vj(k + 1), 0, 1, ip, Vj(k + 1), S->dsc + (k + 1), st), "norm");
+        // Classical Gram-Schmidt with FP64-accurate sums.  Pass 1 gives
+        // h = V^T w and ||w||^2 together; when the projection removes less
+        // than about half of w the new norm follows from Pythagoras,
+        // ||w - V h||^2 = ||w||^2 - ||h||^2, and pass 2 subtracts and
+        // normalises at once.  Otherwise (cancellation) a second sweep
+        // subtracts V h and returns V^T w' and ||w'||^2 from the same read of
+        // V, and pass 3 subtracts the correction and normalises.
+        CU(vec_multidot(n, ip, S->V, n, k + 1, ip, Vj(k + 1), S->dsc, 1, st), "orthogonalisation dots");
         CU(cudaMemcpyAsync(h.data(), S->dsc, sizeof(double) * (k + 2), cudaMemcpyDeviceToHost, st), "readback");
         CU(cudaStreamSynchronize(st), "sync");
-        const double wn0 = std::sqrt(h[k + 1]);
-        CU(vec_multiaxpy(n, ip, Vj(k + 1), S->V, n, k + 1, S->dsc, S->dsc + (m + 1), st), "orthogonalisation");
-        double hn2 = 0;
-        CU(cudaMemcpyAsync(&hn2, S->dsc + (m + 1), sizeof(double), cudaMemcpyDeviceToHost, st), "readback");
-        CU(cudaStreamSynchronize(st), "sync");
-        for (int i = 0; i <= k; ++i) H[size_t(i) * m + k] = h[i];
-        if (std::sqrt(hn2) < 0.7 * wn0) {
-            // second Gram-Schmidt pass
-            CU(vec_multidot(n, ip, S->V, n, k + 1, ip, Vj(k + 1), S->dsc, st), "reorthogonalisation dots");
-            CU(cudaMemcpyAsync(h.data(), S->dsc, sizeof(double) * (k + 1), cudaMemcpyDeviceToHost, st), "readback");
-            CU(vec_multiaxpy(n, ip, Vj(k + 1), S->V, n, k + 1, S->dsc, S->dsc + (m + 1), st), "reorthogonalisation");
-            CU(cudaMemcpyAsync(&hn2, S->dsc + (m + 1), sizeof(double), cudaMemcpyDeviceToHost, st), "readback");
+        const double w2 = h[k + 1];
+        double hh = 0;
+        for (int i = 0; i <= k; ++i) { H[size_t(i) * m + k] = h[i]; hh += h[i] * h[i]; }
+        double hn2 = w2 - hh;
+        const double* hdev = S->dsc;
+        if (hn2 < 0.49 * w2) {
+            CU(vec_multiaxpy(n, ip, Vj(k + 1), S->V, n, k + 1, S->dsc, 1.0, S->dsc + (m + 1), st),
+               "orthogonalisation");
+            CU(cudaMemcpyAsync(h.data(), S->dsc + (m + 1), sizeof(double) * (k + 2), cudaMemcpyDeviceToHost, st),
+               "readback");
             CU(cudaStreamSynchronize(st), "sync");
-            for (int i = 0; i <= k; ++i) H[size_t(i) * m + k] += h[i];
+            hh = 0;
+            for (int i = 0; i <= k; ++i) { H[size_t(i) * m + k] += h[i]; hh += h[i] * h[i]; }
+            hn2 = std::max(h[k + 1] - hh, 0.0);
+            hdev = S->dsc + (m + 1);
         }
-        const double hk1 = std::sqrt(hn2);
-        if (hk1 > 0) CU(vec_normalize(n, ip, Vj(k + 1), S->dsc + (m + 1), st), "normalize");
+        const double hk1 = std::sqrt(std::max(hn2, 0.0));
+        CU(vec_multiaxpy(n, ip, Vj(k + 1), S->V, n, k + 1, hdev, hk1 > 0 ? 1.0 / hk1 : 1.0, nullptr, st),
+           "orthogonalisation");
         // Givens rotations on column k
         for (int i = 0; i < k; ++i) {
             const double a = H[size_t(i) * m + k], b = H[size_t(i + 1) * m + k];
@@ -290,7 +296,7 @@ int stokes_solver_create(const stokes_mesh* mesh, const stokes_solver_opts* opts
     alloc(&S->tz, n * S->isz);
     alloc(&S->A, S->band_elems * S->isz);
     alloc(&S->md, std::max<size_t>(1, size_t(mesh->h.Np)) * S->isz);
-    alloc(reinterpret_cast<void**>(&S->dsc), sizeof(double) * size_t(o.restart + 8));
+    alloc(reinterpret_cast<void**>(&S->dsc), sizeof(double) * size_t(2 * o.restart + 8));
     if (rc) { free_solver(S); delete S; return rc; }
     *out = S;
     return STOKES_OK;

@@ -8,7 +8,10 @@
 // error-free two-sums: GB300 runs FP32 at many times its FP64 rate, so this
 // keeps the reductions memory-bound.  Per-thread partial sums are combined
 // in FP64.  FP64 vectors use FP64 arithmetic.
+#include <mutex>
 #include <type_traits>
+#include <utility>
+#include <vector>
 
 #include <cuda_runtime.h>
 
@@ -41,7 +44,6 @@ struct DF {
     __device__ __forceinline__ double value() const { return double(hi) + double(lo); }
 };
 
-template <typename T>
 __device__ __forceinline__ void block_add(double v, double* out, double* red) {
     v = warp_sum(v);
     __syncthreads();
@@ -54,77 +56,120 @@ __device__ __forceinline__ void block_add(double v, double* out, double* red) {
     }
 }
 
-// out[j] += sum_i V[j*ld + i] * w[i], j < m: one pass reading w once and every
-// V_j once.
+// out[j] += sum_i V[j*ld + i] * w[i], j < m, and with SELF also out[m] +=
+// ||w||^2: one pass reading w once and every V_j once.
+template <bool SELF>
 __global__ void __launch_bounds__(VT) multidot_f32(int64_t n, const float* __restrict__ V, int64_t ld, int m,
                                                    const float* __restrict__ w, double* __restrict__ out) {
     __shared__ double red[VT / 32];
-    DF acc[MAXV];
+    DF acc[MAXV], an;
     for (int64_t i = int64_t(blockIdx.x) * VT + threadIdx.x; i < n; i += int64_t(gridDim.x) * VT) {
         const float wi = w[i];
         #pragma unroll
         for (int j = 0; j < MAXV; ++j)
             if (j < m) acc[j].add_prod(__ldcs(V + ld * j + i), wi);
+        if (SELF) an.add_prod(wi, wi);
     }
     #pragma unroll
     for (int j = 0; j < MAXV; ++j)
-        if (j < m) block_add<float>(acc[j].value(), out + j, red);
+        if (j < m) block_add(acc[j].value(), out + j, red);
+    if (SELF) block_add(an.value(), out + m, red);
 }
 
+template <bool SELF>
 __global__ void __launch_bounds__(VT) multidot_f64(int64_t n, const double* __restrict__ V, int64_t ld, int m,
                                                    const double* __restrict__ w, double* __restrict__ out) {
     __shared__ double red[VT / 32];
-    double acc[MAXV];
+    double acc[MAXV], an = 0.0;
     #pragma unroll
     for (int j = 0; j < MAXV; ++j) acc[j] = 0.0;
     for (int64_t i = int64_t(blockIdx.x) * VT + threadIdx.x; i < n; i += int64_t(gridDim.x) * VT) {
         const double wi = w[i];
         #pragma unroll
         for (int j = 0; j < MAXV; ++j)
-            if (j < m) acc[j] = fma(V[ld * j + i], wi, acc[j]);
+            if (j < m) acc[j] = fma(__ldcs(V + ld * j + i), wi, acc[j]);
+        if (SELF) an = fma(wi, wi, an);
     }
     #pragma unroll
     for (int j = 0; j < MAXV; ++j)
-        if (j < m) block_add<double>(acc[j], out + j, red);
+        if (j < m) block_add(acc[j], out + j, red);
+    if (SELF) block_add(an, out + m, red);
 }
 
-// w[i] -= sum_j h[j] V[j*ld + i];  nrm2 += ||w||^2 after the update
+// w[i] = scale (w[i] - sum_j h[j] V[j*ld + i]); with DOTS also
+// out[j] += V_j . w_new (j < m) and out[m] += ||w_new||^2 in the same pass
+// (the second classical Gram-Schmidt sweep reads every V_j once for both).
+template <bool DOTS>
 __global__ void __launch_bounds__(VT) multiaxpy_f32(int64_t n, float* __restrict__ w, const float* __restrict__ V,
-                                                    int64_t ld, int m, const double* __restrict__ h,
-                                                    double* __restrict__ nrm2) {
+                                                    int64_t ld, int m, const double* __restrict__ h, double scale,
+                                                    double* __restrict__ out) {
     __shared__ double red[VT / 32];
     __shared__ float hs[MAXV];
     if (threadIdx.x < MAXV) hs[threadIdx.x] = threadIdx.x < m ? float(h[threadIdx.x]) : 0.f;
     __syncthreads();
-    DF acc;
+    const float sc = float(scale);
+    DF acc[DOTS ? MAXV : 1], an;
     for (int64_t i = int64_t(blockIdx.x) * VT + threadIdx.x; i < n; i += int64_t(gridDim.x) * VT) {
+        float v[MAXV];
         float r = w[i];
         #pragma unroll
         for (int j = 0; j < MAXV; ++j)
-            if (j < m) r = fmaf(-hs[j], __ldcs(V + ld * j + i), r);
+            if (j < m) {
+                v[j] = __ldcs(V + ld * j + i);
+                r = fmaf(-hs[j], v[j], r);
+            }
+        r *= sc;
         w[i] = r;
-        acc.add_prod(r, r);
+        if (DOTS) {
+            #pragma unroll
+            for (int j = 0; j < MAXV; ++j)
+                if (j < m) acc[DOTS ? j : 0].add_prod(v[j], r);
+            an.add_prod(r, r);
+        }
     }
-    if (nrm2) block_add<float>(acc.value(), nrm2, red);
+    if (DOTS) {
+        #pragma unroll
+        for (int j = 0; j < MAXV; ++j)
+            if (j < m) block_add(acc[DOTS ? j : 0].value(), out + j, red);
+        block_add(an.value(), out + m, red);
+    }
 }
 
+template <bool DOTS>
 __global__ void __launch_bounds__(VT) multiaxpy_f64(int64_t n, double* __restrict__ w, const double* __restrict__ V,
-                                                    int64_t ld, int m, const double* __restrict__ h,
-                                                    double* __restrict__ nrm2) {
+                                                    int64_t ld, int m, const double* __restrict__ h, double scale,
+                                                    double* __restrict__ out) {
     __shared__ double red[VT / 32];
     __shared__ double hs[MAXV];
     if (threadIdx.x < MAXV) hs[threadIdx.x] = threadIdx.x < m ? h[threadIdx.x] : 0.0;
     __syncthreads();
-    double s = 0;
+    double acc[DOTS ? MAXV : 1], an = 0.0;
+    #pragma unroll
+    for (int j = 0; j < (DOTS ? MAXV : 1); ++j) acc[j] = 0.0;
     for (int64_t i = int64_t(blockIdx.x) * VT + threadIdx.x; i < n; i += int64_t(gridDim.x) * VT) {
+        double v[MAXV];
         double r = w[i];
         #pragma unroll
         for (int j = 0; j < MAXV; ++j)
-            if (j < m) r = fma(-hs[j], V[ld * j + i], r);
+            if (j < m) {
+                v[j] = __ldcs(V + ld * j + i);
+                r = fma(-hs[j], v[j], r);
+            }
+        r *= scale;
         w[i] = r;
-        s = fma(r, r, s);
+        if (DOTS) {
+            #pragma unroll
+            for (int j = 0; j < MAXV; ++j)
+                if (j < m) acc[DOTS ? j : 0] = fma(v[j], r, acc[DOTS ? j : 0]);
+            an = fma(r, r, an);
+        }
     }
-    if (nrm2) block_add<double>(s, nrm2, red);
+    if (DOTS) {
+        #pragma unroll
+        for (int j = 0; j < MAXV; ++j)
+            if (j < m) block_add(acc[DOTS ? j : 0], out + j, red);
+        block_add(an, out + m, red);
+    }
 }
 
 // y = a x + b y in the arithmetic of the narrower operand type
@@ -165,6 +210,34 @@ int grid_for(int64_t n) {
     return int(b);
 }
 
+// grid of a grid-stride reduction kernel: at most one wave of resident blocks
+// (SM count x blocks per SM at the kernel's register footprint), so that no
+// block starts after the others have finished their share.  The occupancy of
+// each kernel is queried once per process (first device seen).
+int resident_blocks(const void* kernel) {
+    static std::mutex mu;
+    static std::vector<std::pair<const void*, int>> cache;
+    std::lock_guard<std::mutex> lock(mu);
+    for (const auto& c : cache)
+        if (c.first == kernel) return c.second;
+    int dev = 0, sms = 0, b = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, VT, 0);
+    const int total = (b > 0 ? b : 1) * (sms > 0 ? sms : 1);
+    cache.emplace_back(kernel, total);
+    return total;
+}
+
+template <typename F>
+int grid_resident(F kernel, int64_t n) {
+    int64_t b = (n + VT - 1) / VT;
+    const int64_t cap = resident_blocks(reinterpret_cast<const void*>(kernel));
+    if (b > cap) b = cap;
+    if (b < 1) b = 1;
+    return int(b);
+}
+
 }  // namespace
 
 #define DISPATCH2(prec_a, prec_b, CALL)                                                        \
@@ -174,31 +247,44 @@ int grid_for(int64_t n) {
     else { using TA = double; using TB = double; CALL; }
 
 int vec_multidot(int64_t n, int vprec, const void* V, int64_t ld, int m, int wprec, const void* w,
-                 double* out, cudaStream_t s) {
-    if (m <= 0) return 0;
-    if (m > MAXV || vprec != wprec) return int(cudaErrorInvalidValue);
-    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(double) * m, s);
+                 double* out, int self_norm, cudaStream_t s) {
+    const int mo = m + (self_norm ? 1 : 0);
+    if (mo <= 0) return 0;
+    if (m < 0 || m > MAXV || vprec != wprec) return int(cudaErrorInvalidValue);
+    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(double) * mo, s);
     if (e != cudaSuccess) return int(e);
-    if (vprec == 1)
-        multidot_f32<<<grid_for(n), VT, 0, s>>>(n, static_cast<const float*>(V), ld, m, static_cast<const float*>(w), out);
-    else
-        multidot_f64<<<grid_for(n), VT, 0, s>>>(n, static_cast<const double*>(V), ld, m,
-                                                 static_cast<const double*>(w), out);
+    const float* vf = static_cast<const float*>(V);
+    const double* vd = static_cast<const double*>(V);
+    const float* wf = static_cast<const float*>(w);
+    const double* wd = static_cast<const double*>(w);
+    if (vprec == 1) {
+        if (self_norm) multidot_f32<true><<<grid_resident(multidot_f32<true>, n), VT, 0, s>>>(n, vf, ld, m, wf, out);
+        else multidot_f32<false><<<grid_resident(multidot_f32<false>, n), VT, 0, s>>>(n, vf, ld, m, wf, out);
+    } else {
+        if (self_norm) multidot_f64<true><<<grid_resident(multidot_f64<true>, n), VT, 0, s>>>(n, vd, ld, m, wd, out);
+        else multidot_f64<false><<<grid_resident(multidot_f64<false>, n), VT, 0, s>>>(n, vd, ld, m, wd, out);
+    }
     return int(cudaGetLastError());
 }
 
-int vec_multiaxpy(int64_t n, int prec, void* w, const void* V, int64_t ld, int m, const double* h,
-                  double* nrm2, cudaStream_t s) {
-    if (m > MAXV) return int(cudaErrorInvalidValue);
-    if (nrm2) {
-        cudaError_t e = cudaMemsetAsync(nrm2, 0, sizeof(double), s);
+int vec_multiaxpy(int64_t n, int prec, void* w, const void* V, int64_t ld, int m, const double* h, double scale,
+                  double* dots, cudaStream_t s) {
+    if (m < 0 || m > MAXV) return int(cudaErrorInvalidValue);
+    if (dots) {
+        cudaError_t e = cudaMemsetAsync(dots, 0, sizeof(double) * (m + 1), s);
         if (e != cudaSuccess) return int(e);
     }
-    if (prec == 1)
-        multiaxpy_f32<<<grid_for(n), VT, 0, s>>>(n, static_cast<float*>(w), static_cast<const float*>(V), ld, m, h, nrm2);
-    else
-        multiaxpy_f64<<<grid_for(n), VT, 0, s>>>(n, static_cast<double*>(w), static_cast<const double*>(V), ld, m, h,
-                                                  nrm2);
+    const float* vf = static_cast<const float*>(V);
+    const double* vd = static_cast<const double*>(V);
+    if (prec == 1) {
+        float* wf = static_cast<float*>(w);
+        if (dots) multiaxpy_f32<true><<<grid_resident(multiaxpy_f32<true>, n), VT, 0, s>>>(n, wf, vf, ld, m, h, scale, dots);
+        else multiaxpy_f32<false><<<grid_resident(multiaxpy_f32<false>, n), VT, 0, s>>>(n, wf, vf, ld, m, h, scale, nullptr);
+    } else {
+        double* wd = static_cast<double*>(w);
+        if (dots) multiaxpy_f64<true><<<grid_resident(multiaxpy_f64<true>, n), VT, 0, s>>>(n, wd, vd, ld, m, h, scale, dots);
+        else multiaxpy_f64<false><<<grid_resident(multiaxpy_f64<false>, n), VT, 0, s>>>(n, wd, vd, ld, m, h, scale, nullptr);
+    }
     return int(cudaGetLastError());
 }
 

@@ -8,12 +8,15 @@
 
 namespace stokes {
 
-// out[j] = sum_i V[j ld + i] w[i], j < m (FP64 accumulation; out overwritten)
+// out[j] = sum_i V[j ld + i] w[i], j < m, and out[m] = ||w||^2 if self_norm
+// (FP64-accurate accumulation; out overwritten; m <= 32)
 int vec_multidot(int64_t n, int vprec, const void* V, int64_t ld, int m, int wprec, const void* w,
-                 double* out, cudaStream_t s);
-// w -= sum_j h[j] V[j ld + .] (h on the device); nrm2 (device, may be NULL) = ||w||^2 after
-int vec_multiaxpy(int64_t n, int prec, void* w, const void* V, int64_t ld, int m, const double* h,
-                  double* nrm2, cudaStream_t s);
+                 double* out, int self_norm, cudaStream_t s);
+// w = scale (w - sum_j h[j] V[j ld + .]) (h on the device, m <= 32); if dots
+// (device, may be NULL): dots[j] = V_j . w (j < m) and dots[m] = ||w||^2 of
+// the updated w, from the same pass
+int vec_multiaxpy(int64_t n, int prec, void* w, const void* V, int64_t ld, int m, const double* h, double scale,
+                  double* dots, cudaStream_t s);
 // y = a (* da[0] if da) x + b y
 int vec_axpby(int64_t n, double a, const double* da, int xprec, const void* x, double b, int yprec, void* y,
               cudaStream_t s);

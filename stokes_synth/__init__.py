@@ -7,10 +7,10 @@ It contains none of the finite element arithmetic; both the oracle and the
 CUDA library evaluate these inputs with code of their own.
 """
 from .fields import ModalField, surface_field, bed_field, logbeta_field, flat_field
-from .configs import Workload, PhysParams, workload, WORKLOADS
+from .configs import Workload, PhysParams, workload, WORKLOADS, sub_block
 from .vectors import uniform_vector
 
 __all__ = [
     "ModalField", "surface_field", "bed_field", "logbeta_field", "flat_field",
-    "Workload", "PhysParams", "workload", "WORKLOADS", "uniform_vector",
+    "Workload", "PhysParams", "workload", "WORKLOADS", "sub_block", "uniform_vector",
 ]

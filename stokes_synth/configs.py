@@ -52,6 +52,8 @@ class Workload:
     refine_frac: float = 0.0
     refine_seed: int = 0
     seed: int = 0
+    x0: float = 0.0           # physical offset of the mesh origin (sub-blocks of a larger slab)
+    y0: float = 0.0
 
     @property
     def n_coarse(self):
@@ -146,3 +148,13 @@ WORKLOADS = _build()
 
 def workload(name):
     return WORKLOADS[name]
+
+
+def sub_block(wl, ox, oy, sx, sy):
+    """The sx x sy x nz column block of a conforming slab workload starting at
+    coarse cell (ox, oy): same element shapes and fields, not periodic."""
+    import dataclasses
+    hx, hy = wl.Lx / wl.nx, wl.Ly / wl.ny
+    return dataclasses.replace(wl, name=f"{wl.name}[{ox}:{ox + sx},{oy}:{oy + sy}]", nx=sx, ny=sy,
+                               Lx=sx * hx, Ly=sy * hy, periodic=False,
+                               x0=wl.x0 + ox * hx, y0=wl.y0 + oy * hy)
