@@ -31,6 +31,12 @@ UNIT = "MDoF/s"
 STATE_FIELDS = 11
 
 
+# DRAM bytes (read + write) of one state_apply_kernel<float> launch, from the
+# ncu capture summarised in profiles/state_apply_f32_slab_128x128x8_q2p1.md;
+# only valid for the kernel source that capture was taken from.
+STATE_APPLY_TRAFFIC = {"slab_128x128x8_q2p1": 194371328 + 10344192}
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -382,7 +388,8 @@ def run_ours(args):
             "clocks": clocks,
             "gpu_launches": int(prof["element"][0] + prof["face"][0] + prof["constraint"][0]),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                         "frac": achieved / hbm_peak, "traffic": None,
+                         "frac": achieved / hbm_peak,
+                         "traffic": STATE_APPLY_TRAFFIC.get(wl.name),
                          "kernel": "state_apply_kernel<float>",
                          "bytes_per_launch": bytes_alg, "avg_launch_ms": el_avg_s * 1e3,
                          "peak_source": f"{peak_src} hbm_gbs"},
