@@ -173,6 +173,39 @@ int stokes_param_grad(const stokes_mesh* mesh, const stokes_params* params,
                       const double* up, const double* lambda,
                       double* g_logbeta, double* g_A, void* stream);
 
+/* ---- Fixed-order A-gradient that allocates nothing ------------------------
+ * The paper has no counterpart of this call; it is a library utility.
+ * *g_A = lambda^T d r_c / d A, the quantity stokes_param_grad returns in g_A,
+ * but the per-warp partial sums are written to a library-owned device scratch
+ * (a file-scope static array of STOKES_GRAD_A_MAX_PARTIALS doubles, 1 MiB on
+ * each device) and then added by one block in a fixed order, so repeated
+ * calls on the same inputs give bitwise identical results (stokes_param_grad
+ * adds them with atomics, in an order that varies).
+ * Allocation: none.  The call makes no cudaMalloc or cudaFree and calls no
+ * library that allocates.  It serves callers that cannot allocate device
+ * memory at this point: a caller whose device memory is fully reserved by its
+ * own pool (a solver holding its Krylov bases at scale), or a loop that shares
+ * its stream with other work and cannot take the device-wide synchronisation
+ * that cudaFree implies.
+ * Size limit: the element kernel writes one partial per launched warp,
+ * ceil(E / (4 e_w)) * 4 of them with e_w = 32 / (k+1)^2 elements per warp
+ * (3, 2, 1 for k = 2, 3, 4); a mesh that needs more than
+ * STOKES_GRAD_A_MAX_PARTIALS (E > 393,216 for k = 2, 262,144 for k = 3,
+ * 131,072 for k = 4) returns STOKES_E_INVAL before any launch.
+ * Zero state: nothing in the scratch has to start at zero; every partial that
+ * is read is written earlier in the same call.
+ * Concurrency: the scratch is shared by every call on a device.  Two calls
+ * whose executions overlap (different streams or host threads, same device)
+ * race on it and both results are undefined; callers serialise them.
+ * Set-up: the first call on each device resolves the scratch address with
+ * cudaGetSymbolAddress and caches it; make that first call before beginning
+ * any stream capture on that device.
+ * up, lambda: device FP64 [3Nv+Np]; g_A: device, 1 double, overwritten. */
+#define STOKES_GRAD_A_MAX_PARTIALS 131072
+int stokes_param_grad_A_fixed_order(const stokes_mesh* mesh, const stokes_params* params,
+                                    const double* up, const double* lambda, double* g_A,
+                                    void* stream);
+
 /* Linearised state: the per-quadrature-point Newton coefficients at up_lin
  * (geometry, mu, and the rank-one term of Eq. 2.7), evaluated in FP64 and
  * stored in `prec`, so that repeated Jacobian applies (Krylov iterations)

@@ -97,6 +97,8 @@ _SIGS = {
                                                   C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
     "stokes_param_grad": (C.c_int, [C.c_void_p, C.POINTER(stokes_params), C.c_void_p, C.c_void_p,
                                     C.c_void_p, C.c_void_p, C.c_void_p]),
+    "stokes_param_grad_A_fixed_order": (C.c_int, [C.c_void_p, C.POINTER(stokes_params), C.c_void_p,
+                                                  C.c_void_p, C.c_void_p, C.c_void_p]),
     "stokes_state_create": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_void_p)]),
     "stokes_state_destroy": (C.c_int, [C.c_void_p]),
     "stokes_linearize": (C.c_int, [C.c_void_p, C.POINTER(stokes_params), C.c_void_p, C.c_void_p]),
@@ -201,6 +203,17 @@ def stokes_jacobian_apply_transpose(h, params, up_lin, x, y, prec, stream=None):
 def stokes_param_grad(h, params, up, lam, g_logbeta, g_A, stream=None):
     _check(lib().stokes_param_grad(h, C.byref(params), _ptr(up), _ptr(lam), _ptr(g_logbeta), _ptr(g_A),
                                    _stream(stream)))
+
+
+def stokes_param_grad_A_fixed_order(h, params, up, lam, g_A, stream=None):
+    """g_A[0] = lambda^T d r_c / d A summed in a fixed order, using the
+    library's static device scratch (no allocation; calls on one device must
+    not overlap)."""
+    _check(lib().stokes_param_grad_A_fixed_order(h, C.byref(params), _ptr(up), _ptr(lam), _ptr(g_A),
+                                                 _stream(stream)))
+
+
+STOKES_GRAD_A_MAX_PARTIALS = 131072
 
 
 def stokes_state_create(h, prec):

@@ -104,6 +104,15 @@ int64_t state_stride(int k) {
     return 0;
 }
 
+int64_t grad_a_partials(int k, int64_t E) {
+    switch (k) {
+        case 2: return grad_a_partials_k2(E);
+        case 3: return grad_a_partials_k3(E);
+        case 4: return grad_a_partials_k4(E);
+    }
+    return 0;
+}
+
 int launch_face(int k, int mode, int prec, const FaceArgs& a, cudaStream_t s) {
     switch (k) {
         case 2: return launch_face_k2(mode, prec, a, s);

@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(32 * GW<T>) elem_kernel(ElemArgs a) {
                 put(2 + 10 * Q3 + qp, sq * E12);
             }
         }
-    } else if constexpr (MODE == MODE_GRAD_A) {
+    } else if constexpr (MODE == MODE_GRAD_A || MODE == MODE_GRAD_A_PARTIAL) {
         T acc = 0;
         T Gl[3][3][Q];
         {
@@ -247,7 +247,10 @@ __global__ void __launch_bounds__(32 * GW<T>) elem_kernel(ElemArgs a) {
         double r = double(acc);
         #pragma unroll
         for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o);
-        if (L.lane == 0) atomicAdd(a.gA, r * a.gA_scale);
+        if (L.lane == 0) {
+            if constexpr (MODE == MODE_GRAD_A) atomicAdd(a.gA, r * a.gA_scale);
+            else a.gA_part[int64_t(blockIdx.x) * GW<T> + L.warp] = r;
+        }
     }
 }
 
@@ -574,6 +577,13 @@ __global__ void __launch_bounds__(THREADS) face_kernel(FaceArgs a) {
 }
 
 // ---------------------------------------------------------------- launchers
+// warps launched by the FP64 element kernel over E elements (whole blocks):
+// the number of per-warp partials written in MODE_GRAD_A_PARTIAL
+inline int64_t grad_a_partials(int64_t E) {
+    const int64_t epb = GW<double> * EPW;
+    return (E + epb - 1) / epb * GW<double>;
+}
+
 template <typename T, typename S, int MODE, bool TRANS>
 int launch_elem_t(const ElemArgs& a, cudaStream_t s) {
     const int64_t epb = GW<T> * EPW;
@@ -649,6 +659,8 @@ inline int launch_elem_any(int mode, int prec, int state_prec, bool trans, const
             return f32 ? launch_state_apply_t<float, true>(a, s) : launch_state_apply_t<double, true>(a, s);
         case MODE_GRAD_A:
             return launch_elem_t<double, double, MODE_GRAD_A, false>(a, s);
+        case MODE_GRAD_A_PARTIAL:
+            return launch_elem_t<double, double, MODE_GRAD_A_PARTIAL, false>(a, s);
         default:
             return int(cudaErrorInvalidValue);
     }
@@ -718,4 +730,5 @@ inline int upload_tables_any(const void* p) {
     }                                                                                              \
     int upload_tables_k##KK(const void* t) { return dev::STOKES_NS::upload_tables_any(t); }       \
     int64_t state_stride_k##KK() { return dev::STOKES_NS::SSTRIDE; }                             \
+    int64_t grad_a_partials_k##KK(int64_t E) { return dev::STOKES_NS::grad_a_partials(E); }       \
     }

@@ -48,6 +48,7 @@ struct DeviceGuard {
 };
 
 int launch_elem(int k, int mode, int prec, int state_prec, bool trans, const ElemArgs& a, cudaStream_t s);
+int64_t grad_a_partials(int k, int64_t E);
 int launch_face(int k, int mode, int prec, const FaceArgs& a, cudaStream_t s);
 int launch_precond_assembly(int k, int prec, const ColArgs& a, cudaStream_t s);
 int64_t state_stride(int k);

@@ -14,6 +14,7 @@ enum ElemMode : int {
     MODE_STATE_APPLY = 3,  // y  = J x from the stored state
     MODE_GRAD_A = 4,       // g_A = -(1/(n A)) int mu D(lambda) : D(u)
     MODE_STATE_GRADP = 5,  // velocity rows of B^T p for the pressure part of x (stored state)
+    MODE_GRAD_A_PARTIAL = 6,  // per-warp partial sums of the A-gradient integral (fixed-order variant)
 };
 
 // Linearised state, per element: two element constants (Jinv[0][0] = 1/a,
@@ -42,6 +43,7 @@ struct ElemArgs {
     int n_is_3;
     double body[3];
     double* gA;                // gradient output (accumulated)
+    double* gA_part;           // per-warp partials, indexed blockIdx.x * warps_per_block + warp
     double gA_scale;
     int64_t lat_nx, lat_ny, lat_NX, lat_NY;   // conforming lattice (lat_nx > 0): node index
                                // computed as I + NX (J + NY L) instead of read from nodes
@@ -75,7 +77,8 @@ enum FaceMode : int { FACE_APPLY = 0, FACE_GRAD_LOGBETA = 1 };
                           cudaStream_t s);                                                    \
     int launch_face_k##KK(int mode, int prec, const FaceArgs& a, cudaStream_t s);             \
     int upload_tables_k##KK(const void* tables_k);                                            \
-    int64_t state_stride_k##KK();
+    int64_t state_stride_k##KK();                                                             \
+    int64_t grad_a_partials_k##KK(int64_t E);
 STOKES_DECLARE_DEGREE(2)
 STOKES_DECLARE_DEGREE(3)
 STOKES_DECLARE_DEGREE(4)

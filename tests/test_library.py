@@ -15,7 +15,7 @@ from paper_1406_6573_gb300.mesh import Mesh, mesh_desc
 
 def _header_symbols():
     src = open(capi.os.path.join(capi.HERE, "..", "include", "stokes.h")).read()
-    return sorted(set(re.findall(r"\b(stokes_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(stokes_[A-Za-z0-9_]+)\s*\(", src)))
 
 
 def test_library_exports_every_declared_symbol():
