@@ -25,6 +25,10 @@ import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+# the CPU oracle timings (cpu_baseline, --impl reference) run on one core:
+# no threaded BLAS under numpy (set before numpy is first imported)
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
 
 METRIC = "Jacobian-apply MDoF/s & %HBM roofline; time-to-1e-10 residual FP32-inner vs FP64"
 UNIT = "MDoF/s"
@@ -35,6 +39,20 @@ STATE_FIELDS = 11
 # ncu capture summarised in profiles/state_apply_f32_slab_128x128x8_q2p1.md;
 # only valid for the kernel source that capture was taken from.
 STATE_APPLY_TRAFFIC = {"slab_128x128x8_q2p1": 194371328 + 10344192}
+
+
+def workload_label(wl):
+    """The workload named by what it is (mesh, discretisation, size)."""
+    sp = f"P{wl.k - 1}" if wl.pspace == "P" else f"Q{wl.k - 2}"
+    text = (f"{wl.name}: {wl.nx}x{wl.ny}x{wl.nz} hexahedra, Q{wl.k} x {sp}^disc, "
+            f"{wl.Lx / 1e3:g} km x {wl.Ly / 1e3:g} km slab")
+    if wl.refine_frac == 0.0 and wl.periodic:
+        npr = wl.k * (wl.k + 1) * (wl.k + 2) // 6 if wl.pspace == "P" else (wl.k - 1) ** 3
+        nv = (wl.nx * wl.k) * (wl.ny * wl.k) * (wl.nz * wl.k + 1)
+        text += f", {3 * nv + wl.n_coarse * npr} dofs"
+    else:
+        text += f", {round(100 * wl.refine_frac)} % of cells refined once"
+    return text
 
 
 def parse():
@@ -165,7 +183,9 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded thin periodic ice slab)",
-        "config": {"workload": wl.name, "sample": sample},
+        "config": {"workload": workload_label(wl),
+                   "apply": "Newton Jacobian action, FP64 oracle (dense basis tables, assembled over elements)",
+                   "sample": sample, "parallelism": "host, 1 core"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
@@ -180,6 +200,7 @@ def run_ours(args):
     import stokes_synth as synth
     from paper_1406_6573_gb300 import capi
     from paper_1406_6573_gb300.mesh import Mesh, State, params
+    from paper_1406_6573_gb300.replicas import job_rate, max_over_ranks
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -240,13 +261,9 @@ def run_ours(args):
     prof = capi.stokes_profile_end(mesh.handle)
     clocks = clocks_stop(ck)
     barrier()
-    ms = ev0.elapsed_time(ev1)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ev0.elapsed_time(ev1), "cuda")
     applies = args.steps * B
-    value = world * ndof * applies / (ms / 1e3) / 1e6
+    value = job_rate(ndof * applies, ms / 1e3, "cuda") / 1e6
 
     # roofline of the dominant kernel (volume element kernel of the FP32 state apply)
     peaks = {}
@@ -283,12 +300,8 @@ def run_ours(args):
         for _ in range(ke):
             e2e_step()
         torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([dt], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
-        e2e = {"value": world * ndof * B * ke / dt / 1e6, "unit": UNIT,
+        dt = max_over_ranks(time.perf_counter() - t0, "cuda")
+        e2e = {"value": job_rate(ndof * B * ke, dt, "cuda") / 1e6, "unit": UNIT,
                "h2d_bytes_per_step": B * ndof * 4, "d2h_bytes_per_step": B * ndof * 4,
                "steps": ke}
 
@@ -346,11 +359,7 @@ def run_ours(args):
             t0 = time.perf_counter()
             rc, rep = capi.stokes_newton_solve(sv, p, u0, stream)
             torch.cuda.synchronize()
-            wall = time.perf_counter() - t0
-            if world > 1:
-                t = torch.tensor([wall], device="cuda")
-                dist.all_reduce(t, op=dist.ReduceOp.MAX)
-                wall = float(t.item())
+            wall = max_over_ranks(time.perf_counter() - t0, "cuda")
             capi.stokes_solver_destroy(sv)
             solve[tag] = {"seconds": round(wall, 4), "converged": rep["converged"],
                           "newton_its": rep["newton_its"], "krylov_its": rep["krylov_its"],
@@ -375,9 +384,7 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded thin periodic ice slab, random-Fourier bed and surface)",
             "config": {
-                "workload": f"{wl.name}: {wl.nx}x{wl.ny}x{wl.nz} hexahedra, Q{wl.k} x "
-                            f"{'P' if wl.pspace == 'P' else 'Q'}{wl.k - 1 if wl.pspace == 'P' else wl.k - 2}"
-                            f"^disc, {ndof} dofs, 100 km x 100 km x 1 km",
+                "workload": workload_label(wl),
                 "apply": "Newton Jacobian from the stored FP32 linearised state (Krylov-inner apply)",
                 "applies_per_step": B,
                 "l2": "inputs larger than L2 (FP32 state %d MB + %d distinct x/y pairs of %d MB)"

@@ -257,11 +257,15 @@ int stokes_solver_destroy(stokes_solver* solver);
  * The solver replaces params->constraint_scale by the mean diagonal of the
  * velocity block at the first linearisation (reported in the report); the
  * residual norms it reports use that scale.
- * Returns STOKES_E_NOCONV (report filled) if rtol is not reached. */
+ * Returns STOKES_E_NOCONV (report filled) if rtol is not reached, and
+ * STOKES_E_NONFINITE if the residual at the initial guess or after an update
+ * is not finite (up then holds the last finite iterate). */
 int stokes_newton_solve(stokes_solver* solver, const stokes_params* params, double* up,
                         stokes_solve_report* report, void* stream);
 /* Solve J_c(up_lin) x = b (transpose = 0) or J_c(up_lin)^T x = b (transpose = 1)
- * to ||b - J x|| <= rtol ||b||; up_lin, b, x: device FP64 [3Nv+Np]. */
+ * to ||b - J x|| <= rtol ||b||; up_lin, b, x: device FP64 [3Nv+Np].
+ * Returns STOKES_E_NOCONV if rtol is not reached and STOKES_E_NONFINITE if b
+ * or the final linear residual is not finite. */
 int stokes_linear_solve(stokes_solver* solver, const stokes_params* params, const double* up_lin,
                         const double* b, double* x, int transpose, double rtol,
                         stokes_solve_report* report, void* stream);

@@ -255,6 +255,13 @@ __global__ void __launch_bounds__(32 * GW<T>) elem_kernel(ElemArgs a) {
 }
 
 // ================================================== state apply (hot path)
+// Line exchanges of the sum factorisation in the stored-state kernel: warp
+// shuffles for degrees >= STOKES_STATE_SHFL_MIN_K, shared memory below
+// (measured per degree).
+#ifndef STOKES_STATE_SHFL_MIN_K
+#define STOKES_STATE_SHFL_MIN_K 3
+#endif
+constexpr bool STATE_SHFL = K >= STOKES_STATE_SHFL_MIN_K;
 // y = J x from the stored linearised state.  Persistent: each warp walks its
 // element groups (EPW consecutive elements); the state block of the next
 // group (contiguous, 16-byte multiple) is staged into shared memory by a bulk
@@ -333,7 +340,8 @@ __global__ void __launch_bounds__(32 * StateApplyCfg<T>::W) state_apply_kernel(E
             T v[3][N1];
             gather_velocity<T, T>(a, x, cn, e, active, ij, v);
             if (any_h) hanging_forward<T, 3>(v, h, active, i, j, sb);
-            ref_gradient<T, 3>(R, v, G, i, j, sb);
+            if constexpr (STATE_SHFL) ref_gradient<T, 3>(R, v, G, i, j, sb);
+            else ref_gradient_smem<T, 3>(R, v, G, i, j, sb);
         } else {
             #pragma unroll
             for (int c = 0; c < 3; ++c)
@@ -392,7 +400,8 @@ __global__ void __launch_bounds__(32 * StateApplyCfg<T>::W) state_apply_kernel(E
         __syncwarp();
         T out[3][N1];
         T dummy[3][Q];
-        ref_gradient_T<T, 3, false>(R, G, dummy, out, i, j, sb);
+        if constexpr (STATE_SHFL) ref_gradient_T<T, 3, false>(R, G, dummy, out, i, j, sb);
+        else ref_gradient_T_smem<T, 3, false>(R, G, dummy, out, i, j, sb);
         if constexpr (!PONLY) pressure_rows<T>(gq, a.npr, ps, i, j, ij, active, sb, y + 3 * a.Nv + e * a.npr);
         if (any_h) hanging_transpose<T, 3>(out, h, active, i, j, sb);
         scatter_velocity<T>(a, y, cn, e, active, ij, out);

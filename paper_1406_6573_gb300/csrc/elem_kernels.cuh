@@ -294,6 +294,99 @@ __device__ __forceinline__ void load_line(const T* p, T (&o)[N1]) {
     }
 }
 
+// value v held by the thread of slot (i2, j2) of this thread's element (the
+// element's N1^2 threads are consecutive lanes; idle lanes read any lane)
+template <typename T>
+__device__ __forceinline__ T lane_val(T v, int i2, int j2) {
+    const int base = ((threadIdx.x & 31) / N2) * N2;
+    return __shfl_sync(0xffffffffu, v, base + i2 + N1 * j2);
+}
+
+// Reference gradients at the Gauss points (iq = i, jq = j, lq) of the NC
+// fields whose nodal columns the thread holds in vin:
+//   zeta: interpolate (registers);  eta: interpolate and differentiate the
+//   eta-line through the thread's node column (values from the lanes of that
+//   line);  xi: interpolate and differentiate the interpolated xi-line and
+//   interpolate the eta-derivative line;  zeta derivative by collocation.
+// The lines are exchanged with warp shuffles; buf is not used.
+template <typename T, int NC>
+__device__ __forceinline__ void ref_gradient(const Rows<T>& R, const T (&vin)[NC][N1], T (&G)[NC][3][Q],
+                                             int i, int j, T* /*buf*/) {
+    #pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        T a[Q];
+        #pragma unroll
+        for (int lq = 0; lq < Q; ++lq) {
+            T s = 0;
+            #pragma unroll
+            for (int l = 0; l < N1; ++l) s += Tab<T>::B(lq, l) * vin[c][l];
+            T si = 0, sd = 0;                         // thread (node i, jq = j)
+            #pragma unroll
+            for (int m = 0; m < N1; ++m) {
+                const T x = lane_val(s, i, m);
+                si += R.Bj[m] * x;
+                sd += R.Tj[m] * x;
+            }
+            T sv = 0, sx = 0, sy = 0;                 // thread (iq = i, jq = j)
+            #pragma unroll
+            for (int m = 0; m < N1; ++m) {
+                const T x1 = lane_val(si, m, j);
+                const T x2 = lane_val(sd, m, j);
+                sv += R.Bi[m] * x1;
+                sx += R.Ti[m] * x1;
+                sy += R.Bi[m] * x2;
+            }
+            a[lq] = sv; G[c][0][lq] = sx; G[c][1][lq] = sy;
+        }
+        #pragma unroll
+        for (int lq = 0; lq < Q; ++lq) {          // zeta derivative, collocated
+            T s = 0;
+            #pragma unroll
+            for (int m = 0; m < Q; ++m) s += Tab<T>::Dg(lq, m) * a[m];
+            G[c][2][lq] = s;
+        }
+    }
+}
+
+// Transposed gradients: nodal columns out[c][l] of
+//   sum_qp (d phi/d xi) S[c][0] + (d phi/d eta) S[c][1] + (d phi/d zeta) S[c][2] + phi Sv[c]
+// (collocated derivative transposes at the Gauss points, then the three
+// transposed interpolations); lines exchanged with warp shuffles.
+template <typename T, int NC, bool HAS_VAL>
+__device__ __forceinline__ void ref_gradient_T(const Rows<T>& R, const T (&S)[NC][3][Q], const T (&Sv)[NC][Q],
+                                               T (&out)[NC][N1], int i, int j, T* /*buf*/) {
+    #pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        T t[Q];
+        #pragma unroll
+        for (int lq = 0; lq < Q; ++lq) {
+            T z = HAS_VAL ? Sv[c][lq] : T(0);
+            #pragma unroll
+            for (int m = 0; m < Q; ++m) z += Tab<T>::Dg(m, lq) * S[c][2][m];
+            T s = z;                                  // thread (iq = i, jq = j)
+            #pragma unroll
+            for (int m = 0; m < Q; ++m)
+                s += R.DTi[m] * lane_val(S[c][0][lq], m, j) + R.DTj[m] * lane_val(S[c][1][lq], i, m);
+            T u = 0;                                  // xi^T: thread (node i, jq = j)
+            #pragma unroll
+            for (int m = 0; m < Q; ++m) u += R.BTi[m] * lane_val(s, m, j);
+            T v = 0;                                  // eta^T: thread (node i, node j)
+            #pragma unroll
+            for (int m = 0; m < Q; ++m) v += R.BTj[m] * lane_val(u, i, m);
+            t[lq] = v;
+        }
+        #pragma unroll
+        for (int l = 0; l < N1; ++l) {            // zeta^T
+            T s = 0;
+            #pragma unroll
+            for (int lq = 0; lq < Q; ++lq) s += Tab<T>::B(lq, l) * t[lq];
+            out[c][l] = s;
+        }
+    }
+}
+// Shared-memory exchange variants of ref_gradient / ref_gradient_T (used by
+// the stored-state kernel, where they measured faster than the shuffles;
+// the generic element kernel uses the shuffle variants).
 // Reference gradients at the Gauss points (iq = i, jq = j, lq) of the NC
 // fields whose nodal columns the thread holds in vin, all fields advancing
 // through each stage together (independent chains between warp syncs):
@@ -302,7 +395,7 @@ __device__ __forceinline__ void load_line(const T* p, T (&o)[N1]) {
 //   interpolate the eta-derivative line;  zeta derivative by collocation.
 // buf: 3 NC exchange buffers of BUFLEN values.
 template <typename T, int NC>
-__device__ __forceinline__ void ref_gradient(const Rows<T>& R, const T (&vin)[NC][N1], T (&G)[NC][3][Q],
+__device__ __forceinline__ void ref_gradient_smem(const Rows<T>& R, const T (&vin)[NC][N1], T (&G)[NC][3][Q],
                                              int i, int j, T* buf) {
     #pragma unroll
     for (int c = 0; c < NC; ++c) {
@@ -364,7 +457,7 @@ __device__ __forceinline__ void ref_gradient(const Rows<T>& R, const T (&vin)[NC
 // (collocated derivative transposes at the Gauss points, then the three
 // transposed interpolations), NC fields advancing together.
 template <typename T, int NC, bool HAS_VAL>
-__device__ __forceinline__ void ref_gradient_T(const Rows<T>& R, const T (&S)[NC][3][Q], const T (&Sv)[NC][Q],
+__device__ __forceinline__ void ref_gradient_T_smem(const Rows<T>& R, const T (&S)[NC][3][Q], const T (&Sv)[NC][Q],
                                                T (&out)[NC][N1], int i, int j, T* buf) {
     T t[NC][Q];
     #pragma unroll
@@ -436,6 +529,7 @@ __device__ __forceinline__ void ref_gradient_T(const Rows<T>& R, const T (&S)[NC
     }
     wsync();
 }
+
 
 // ------------------------------------------------------------ gather
 template <typename T>

@@ -35,6 +35,7 @@ struct stokes_solver {
     stokes_state* st_in = nullptr;
     stokes_state* st64 = nullptr;
     int64_t n = 0, nu = 0;
+    int64_t ld = 0;                    // column stride of the Krylov bases V, Z (n rounded up to 64)
     size_t isz = 4;
     double *r = nullptr, *dl = nullptr, *rl = nullptr, *trial = nullptr, *rt = nullptr, *tmp64 = nullptr;
     void *V = nullptr, *Z = nullptr, *tin = nullptr, *tz = nullptr;
@@ -142,8 +143,8 @@ int fgmres_cycle(stokes_solver* S, bool trans, double tol_rel, int max_its, int&
     const int m = std::min(S->o.restart, max_its);
     const int ip = S->inner;
     const size_t isz = S->isz;
-    auto Vj = [&](int j) { return static_cast<char*>(S->V) + size_t(j) * n * isz; };
-    auto Zj = [&](int j) { return static_cast<char*>(S->Z) + size_t(j) * n * isz; };
+    auto Vj = [&](int j) { return static_cast<char*>(S->V) + size_t(j) * S->ld * isz; };
+    auto Zj = [&](int j) { return static_cast<char*>(S->Z) + size_t(j) * S->ld * isz; };
     std::vector<double> H(size_t(m + 1) * m, 0.0), cs(m, 0.0), sn(m, 0.0), g(m + 1, 0.0), h(m + 2, 0.0);
     // V_0 = b / ||b||
     CU(vec_axpby(n, 1.0, nullptr, ip, S->tin, 0.0, ip, Vj(0), st), "copy");
@@ -163,10 +164,10 @@ int fgmres_cycle(stokes_solver* S, bool trans, double tol_rel, int max_its, int&
         // h = V^T w and ||w||^2 together; when the projection removes less
         // than about half of w the new norm follows from Pythagoras,
         // ||w - V h||^2 = ||w||^2 - ||h||^2, and pass 2 subtracts and
-        // normalises at once.  Otherwise (cancellation) a second sweep
-        // subtracts V h and returns V^T w' and ||w'||^2 from the same read of
-        // V, and pass 3 subtracts the correction and normalises.
-        CU(vec_multidot(n, ip, S->V, n, k + 1, ip, Vj(k + 1), S->dsc, 1, st), "orthogonalisation dots");
+        // normalises at once.  Otherwise (cancellation) w' = w - V h is
+        // formed, V^T w' and ||w'||^2 are taken in one pass, and a last pass
+        // subtracts the correction and normalises.
+        CU(vec_multidot(n, ip, S->V, S->ld, k + 1, ip, Vj(k + 1), S->dsc, 1, st), "orthogonalisation dots");
         CU(cudaMemcpyAsync(h.data(), S->dsc, sizeof(double) * (k + 2), cudaMemcpyDeviceToHost, st), "readback");
         CU(cudaStreamSynchronize(st), "sync");
         const double w2 = h[k + 1];
@@ -175,7 +176,7 @@ int fgmres_cycle(stokes_solver* S, bool trans, double tol_rel, int max_its, int&
         double hn2 = w2 - hh;
         const double* hdev = S->dsc;
         if (hn2 < 0.49 * w2) {
-            CU(vec_multiaxpy(n, ip, Vj(k + 1), S->V, n, k + 1, S->dsc, 1.0, S->dsc + (m + 1), st),
+            CU(vec_multiaxpy(n, ip, Vj(k + 1), S->V, S->ld, k + 1, S->dsc, 1.0, S->dsc + (m + 1), st),
                "orthogonalisation");
             CU(cudaMemcpyAsync(h.data(), S->dsc + (m + 1), sizeof(double) * (k + 2), cudaMemcpyDeviceToHost, st),
                "readback");
@@ -186,7 +187,7 @@ int fgmres_cycle(stokes_solver* S, bool trans, double tol_rel, int max_its, int&
             hdev = S->dsc + (m + 1);
         }
         const double hk1 = std::sqrt(std::max(hn2, 0.0));
-        CU(vec_multiaxpy(n, ip, Vj(k + 1), S->V, n, k + 1, hdev, hk1 > 0 ? 1.0 / hk1 : 1.0, nullptr, st),
+        CU(vec_multiaxpy(n, ip, Vj(k + 1), S->V, S->ld, k + 1, hdev, hk1 > 0 ? 1.0 / hk1 : 1.0, nullptr, st),
            "orthogonalisation");
         // Givens rotations on column k
         for (int i = 0; i < k; ++i) {
@@ -212,7 +213,7 @@ int fgmres_cycle(stokes_solver* S, bool trans, double tol_rel, int max_its, int&
         y[i] = s / H[size_t(i) * m + i];
     }
     CU(cudaMemcpyAsync(S->dsc, y.data(), sizeof(double) * k, cudaMemcpyHostToDevice, st), "coefficients");
-    CU(vec_combine(n, ip, S->Z, n, k, S->dsc, STOKES_F64, S->dl, st), "update");
+    CU(vec_combine(n, ip, S->Z, S->ld, k, S->dsc, STOKES_F64, S->dl, st), "update");
     CU(cudaStreamSynchronize(st), "sync");
     return STOKES_OK;
 }
@@ -269,6 +270,7 @@ int stokes_solver_create(const stokes_mesh* mesh, const stokes_solver_opts* opts
     S->inner = o.inner_prec;
     S->isz = S->inner == STOKES_F32 ? 4 : 8;
     S->n = 3 * mesh->h.Nv + mesh->h.Np;
+    S->ld = (S->n + 63) / 64 * 64;
     S->nu = 3 * mesh->h.Nv;
     S->bw = 3 * mesh->h.bnode + 2;
     DeviceGuard g(mesh->device);
@@ -290,8 +292,8 @@ int stokes_solver_create(const stokes_mesh* mesh, const stokes_solver_opts* opts
     alloc(reinterpret_cast<void**>(&S->trial), n * 8);
     alloc(reinterpret_cast<void**>(&S->rt), n * 8);
     alloc(reinterpret_cast<void**>(&S->tmp64), n * 8);
-    alloc(&S->V, n * S->isz * size_t(o.restart + 1));
-    alloc(&S->Z, n * S->isz * size_t(o.restart));
+    alloc(&S->V, size_t(S->ld) * S->isz * size_t(o.restart + 1));
+    alloc(&S->Z, size_t(S->ld) * S->isz * size_t(o.restart));
     alloc(&S->tin, n * S->isz);
     alloc(&S->tz, n * S->isz);
     alloc(&S->A, S->band_elems * S->isz);
@@ -337,6 +339,10 @@ int stokes_newton_solve(stokes_solver* S, const stokes_params* params, double* u
     CK(norm64(S, S->r, n, nr, st));
     const double nr0 = nr;
     R.res0 = nr0;
+    if (!std::isfinite(nr0)) {
+        if (rep) *rep = R;
+        return fail(STOKES_E_NONFINITE, "the residual at the initial guess is not finite");
+    }
     R.history[0] = nr0;
     double eta = S->o.eta_max, nr_prev = nr;
     int k = 0;
@@ -369,6 +375,12 @@ int stokes_newton_solve(stokes_solver* S, const stokes_params* params, double* u
             if (nrt <= (1.0 - 1e-4 * alpha) * nr || cut >= 12) break;
             alpha *= 0.5;
             R.line_search_cuts++;
+        }
+        if (!std::isfinite(nrt)) {
+            R.newton_its = k + 1;
+            R.res_final = nrt;
+            if (rep) *rep = R;
+            return fail(STOKES_E_NONFINITE, "non-finite residual after the Newton update (up left at the last iterate)");
         }
         CU(cudaMemcpyAsync(up, S->trial, sizeof(double) * n, cudaMemcpyDeviceToDevice, st), "update");
         CU(cudaMemcpyAsync(S->r, S->rt, sizeof(double) * n, cudaMemcpyDeviceToDevice, st), "update");
@@ -403,6 +415,7 @@ int stokes_linear_solve(stokes_solver* S, const stokes_params* params, const dou
     CK(precond_setup(S, params, st));
     double nb = 0;
     CK(norm64(S, b, n, nb, st));
+    if (!std::isfinite(nb)) return fail(STOKES_E_NONFINITE, "the right-hand side is not finite");
     int its = 0;
     CK(linear_solve(S, b, nb, rtol, transpose != 0, its, st));
     CU(cudaMemcpyAsync(x, S->dl, sizeof(double) * n, cudaMemcpyDeviceToDevice, st), "solution");
@@ -412,6 +425,10 @@ int stokes_linear_solve(stokes_solver* S, const stokes_params* params, const dou
     R.res0 = nb;
     R.res_final = nrl;
     R.converged = nrl <= rtol * nb;
+    if (!std::isfinite(nrl)) {
+        if (rep) *rep = R;
+        return fail(STOKES_E_NONFINITE, "non-finite linear residual");
+    }
     R.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     if (rep) *rep = R;
     return R.converged ? STOKES_OK : fail(STOKES_E_NOCONV, "Krylov solve did not reach rtol");

@@ -8,6 +8,8 @@
 // error-free two-sums: GB300 runs FP32 at many times its FP64 rate, so this
 // keeps the reductions memory-bound.  Per-thread partial sums are combined
 // in FP64.  FP64 vectors use FP64 arithmetic.
+#include <algorithm>
+#include <cstdint>
 #include <mutex>
 #include <type_traits>
 #include <utility>
@@ -56,119 +58,126 @@ __device__ __forceinline__ void block_add(double v, double* out, double* red) {
     }
 }
 
-// out[j] += sum_i V[j*ld + i] * w[i], j < m, and with SELF also out[m] +=
-// ||w||^2: one pass reading w once and every V_j once.
-template <bool SELF>
-__global__ void __launch_bounds__(VT) multidot_f32(int64_t n, const float* __restrict__ V, int64_t ld, int m,
-                                                   const float* __restrict__ w, double* __restrict__ out) {
-    __shared__ double red[VT / 32];
-    DF acc[MAXV], an;
-    for (int64_t i = int64_t(blockIdx.x) * VT + threadIdx.x; i < n; i += int64_t(gridDim.x) * VT) {
-        const float wi = w[i];
-        #pragma unroll
-        for (int j = 0; j < MAXV; ++j)
-            if (j < m) acc[j].add_prod(__ldcs(V + ld * j + i), wi);
-        if (SELF) an.add_prod(wi, wi);
+// FP64 accumulator with the interface of DF
+struct D1 {
+    double s = 0.0;
+    __device__ __forceinline__ void add_prod(double a, double b) { s = fma(a, b, s); }
+    __device__ __forceinline__ double value() const { return s; }
+};
+template <typename T> using Acc = typename std::conditional<sizeof(T) == 4, DF, D1>::type;
+
+// VEC consecutive values starting at p (16-byte aligned when VEC > 1), streamed
+template <typename T, int VEC>
+__device__ __forceinline__ void load_vec(const T* p, T (&o)[VEC]) {
+    if constexpr (VEC == 4) {
+        const float4 v = __ldcs(reinterpret_cast<const float4*>(p));
+        o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+    } else if constexpr (VEC == 2) {
+        const double2 v = __ldcs(reinterpret_cast<const double2*>(p));
+        o[0] = v.x; o[1] = v.y;
+    } else {
+        o[0] = __ldcs(p);
     }
-    #pragma unroll
-    for (int j = 0; j < MAXV; ++j)
-        if (j < m) block_add(acc[j].value(), out + j, red);
-    if (SELF) block_add(an.value(), out + m, red);
+}
+template <typename T, int VEC>
+__device__ __forceinline__ void store_vec(T* p, const T (&o)[VEC]) {
+    if constexpr (VEC == 4) {
+        *reinterpret_cast<float4*>(p) = make_float4(o[0], o[1], o[2], o[3]);
+    } else if constexpr (VEC == 2) {
+        *reinterpret_cast<double2*>(p) = make_double2(o[0], o[1]);
+    } else {
+        p[0] = o[0];
+    }
 }
 
-template <bool SELF>
-__global__ void __launch_bounds__(VT) multidot_f64(int64_t n, const double* __restrict__ V, int64_t ld, int m,
-                                                   const double* __restrict__ w, double* __restrict__ out) {
-    __shared__ double red[VT / 32];
-    double acc[MAXV], an = 0.0;
-    #pragma unroll
-    for (int j = 0; j < MAXV; ++j) acc[j] = 0.0;
-    for (int64_t i = int64_t(blockIdx.x) * VT + threadIdx.x; i < n; i += int64_t(gridDim.x) * VT) {
-        const double wi = w[i];
-        #pragma unroll
-        for (int j = 0; j < MAXV; ++j)
-            if (j < m) acc[j] = fma(__ldcs(V + ld * j + i), wi, acc[j]);
-        if (SELF) an = fma(wi, wi, an);
-    }
-    #pragma unroll
-    for (int j = 0; j < MAXV; ++j)
-        if (j < m) block_add(acc[j], out + j, red);
-    if (SELF) block_add(an, out + m, red);
-}
+constexpr int MD_ROW = 16;   // vectors per grid row of the multi-dot
 
-// w[i] = scale (w[i] - sum_j h[j] V[j*ld + i]); with DOTS also
-// out[j] += V_j . w_new (j < m) and out[m] += ||w_new||^2 in the same pass
-// (the second classical Gram-Schmidt sweep reads every V_j once for both).
-template <bool DOTS>
-__global__ void __launch_bounds__(VT) multiaxpy_f32(int64_t n, float* __restrict__ w, const float* __restrict__ V,
-                                                    int64_t ld, int m, const double* __restrict__ h, double scale,
-                                                    double* __restrict__ out) {
+// out[j] += sum_i V[j*ld + i] w[i] for the MD_ROW vectors j of grid row
+// blockIdx.y (j < m); with SELF, grid row 0 also adds ||w||^2 to out[m].
+// Values are read in VEC-wide chunks (16-byte loads); the n % VEC tail is
+// read by the first threads of block (0, y).
+template <typename T, bool SELF, int VEC>
+__global__ void __launch_bounds__(VT, 2) multidot_kernel(int64_t n, const T* __restrict__ V, int64_t ld, int m,
+                                                         const T* __restrict__ w, double* __restrict__ out) {
     __shared__ double red[VT / 32];
-    __shared__ float hs[MAXV];
-    if (threadIdx.x < MAXV) hs[threadIdx.x] = threadIdx.x < m ? float(h[threadIdx.x]) : 0.f;
-    __syncthreads();
-    const float sc = float(scale);
-    DF acc[DOTS ? MAXV : 1], an;
-    for (int64_t i = int64_t(blockIdx.x) * VT + threadIdx.x; i < n; i += int64_t(gridDim.x) * VT) {
-        float v[MAXV];
-        float r = w[i];
+    const int j0 = int(blockIdx.y) * MD_ROW;
+    const int mc = min(MD_ROW, m - j0);
+    const bool self = SELF && blockIdx.y == 0;
+    const T* Vr = V + ld * j0;
+    Acc<T> acc[MD_ROW], an;
+    const int64_t nv = n / VEC;
+    for (int64_t c = int64_t(blockIdx.x) * VT + threadIdx.x; c < nv; c += int64_t(gridDim.x) * VT) {
+        T wv[VEC], vv[MD_ROW][VEC];
+        load_vec<T, VEC>(w + c * VEC, wv);
+        // all loads first (predicated, independent), then the arithmetic
         #pragma unroll
-        for (int j = 0; j < MAXV; ++j)
-            if (j < m) {
-                v[j] = __ldcs(V + ld * j + i);
-                r = fmaf(-hs[j], v[j], r);
+        for (int jj = 0; jj < MD_ROW; ++jj)
+            if (jj < mc) load_vec<T, VEC>(Vr + ld * jj + c * VEC, vv[jj]);
+        #pragma unroll
+        for (int jj = 0; jj < MD_ROW; ++jj)
+            if (jj < mc) {
+                #pragma unroll
+                for (int q = 0; q < VEC; ++q) acc[jj].add_prod(vv[jj][q], wv[q]);
             }
-        r *= sc;
-        w[i] = r;
-        if (DOTS) {
+        if (self) {
             #pragma unroll
-            for (int j = 0; j < MAXV; ++j)
-                if (j < m) acc[DOTS ? j : 0].add_prod(v[j], r);
-            an.add_prod(r, r);
+            for (int q = 0; q < VEC; ++q) an.add_prod(wv[q], wv[q]);
         }
     }
-    if (DOTS) {
-        #pragma unroll
-        for (int j = 0; j < MAXV; ++j)
-            if (j < m) block_add(acc[DOTS ? j : 0].value(), out + j, red);
-        block_add(an.value(), out + m, red);
-    }
-}
-
-template <bool DOTS>
-__global__ void __launch_bounds__(VT) multiaxpy_f64(int64_t n, double* __restrict__ w, const double* __restrict__ V,
-                                                    int64_t ld, int m, const double* __restrict__ h, double scale,
-                                                    double* __restrict__ out) {
-    __shared__ double red[VT / 32];
-    __shared__ double hs[MAXV];
-    if (threadIdx.x < MAXV) hs[threadIdx.x] = threadIdx.x < m ? h[threadIdx.x] : 0.0;
-    __syncthreads();
-    double acc[DOTS ? MAXV : 1], an = 0.0;
-    #pragma unroll
-    for (int j = 0; j < (DOTS ? MAXV : 1); ++j) acc[j] = 0.0;
-    for (int64_t i = int64_t(blockIdx.x) * VT + threadIdx.x; i < n; i += int64_t(gridDim.x) * VT) {
-        double v[MAXV];
-        double r = w[i];
-        #pragma unroll
-        for (int j = 0; j < MAXV; ++j)
-            if (j < m) {
-                v[j] = __ldcs(V + ld * j + i);
-                r = fma(-hs[j], v[j], r);
-            }
-        r *= scale;
-        w[i] = r;
-        if (DOTS) {
+    if (VEC > 1 && blockIdx.x == 0) {
+        const int64_t i = nv * VEC + threadIdx.x;
+        if (i < n) {
+            const T wi = w[i];
             #pragma unroll
-            for (int j = 0; j < MAXV; ++j)
-                if (j < m) acc[DOTS ? j : 0] = fma(v[j], r, acc[DOTS ? j : 0]);
-            an = fma(r, r, an);
+            for (int jj = 0; jj < MD_ROW; ++jj)
+                if (jj < mc) acc[jj].add_prod(Vr[ld * jj + i], wi);
+            if (self) an.add_prod(wi, wi);
         }
     }
-    if (DOTS) {
+    #pragma unroll
+    for (int jj = 0; jj < MD_ROW; ++jj)
+        if (jj < mc) block_add(acc[jj].value(), out + j0 + jj, red);
+    if (self) block_add(an.value(), out + m, red);
+}
+
+// w[i] = scale (w[i] - sum_j h[j] V[j*ld + i]), VEC-wide chunks; the vectors
+// are read in groups of 8 (bounded registers, 8 loads in flight per thread).
+template <typename T, int VEC>
+__global__ void __launch_bounds__(VT, 2) multiaxpy_kernel(int64_t n, T* __restrict__ w, const T* __restrict__ V,
+                                                          int64_t ld, int m, const double* __restrict__ h,
+                                                          double scale) {
+    __shared__ T hs[MAXV];
+    if (threadIdx.x < MAXV) hs[threadIdx.x] = threadIdx.x < m ? T(h[threadIdx.x]) : T(0);
+    __syncthreads();
+    const T sc = T(scale);
+    const int64_t nv = n / VEC;
+    auto body = [&](int64_t off, auto tag) {
+        constexpr int W = decltype(tag)::value;
+        T r[W];
+        load_vec<T, W>(w + off, r);
+        #pragma unroll 1
+        for (int g = 0; g < m; g += 8) {
+            T vv[8][W];
+            #pragma unroll
+            for (int jj = 0; jj < 8; ++jj)
+                if (g + jj < m) load_vec<T, W>(V + ld * (g + jj) + off, vv[jj]);
+            #pragma unroll
+            for (int jj = 0; jj < 8; ++jj)
+                if (g + jj < m) {
+                    const T hj = hs[g + jj];
+                    #pragma unroll
+                    for (int q = 0; q < W; ++q) r[q] = fma(-hj, vv[jj][q], r[q]);
+                }
+        }
         #pragma unroll
-        for (int j = 0; j < MAXV; ++j)
-            if (j < m) block_add(acc[DOTS ? j : 0], out + j, red);
-        block_add(an, out + m, red);
+        for (int q = 0; q < W; ++q) r[q] *= sc;
+        store_vec<T, W>(w + off, r);
+    };
+    for (int64_t c = int64_t(blockIdx.x) * VT + threadIdx.x; c < nv; c += int64_t(gridDim.x) * VT)
+        body(c * VEC, std::integral_constant<int, VEC>());
+    if (VEC > 1 && blockIdx.x == 0) {
+        const int64_t i = nv * VEC + threadIdx.x;
+        if (i < n) body(i, std::integral_constant<int, 1>());
     }
 }
 
@@ -246,6 +255,38 @@ int grid_resident(F kernel, int64_t n) {
     else if ((prec_b) == 1) { using TA = double; using TB = float; CALL; }                    \
     else { using TA = double; using TB = double; CALL; }
 
+template <typename T>
+bool aligned16(const T* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+template <typename T>
+int multidot_t(int64_t n, const T* V, int64_t ld, int m, const T* w, double* out, bool self, cudaStream_t s) {
+    constexpr int VEC = sizeof(T) == 4 ? 4 : 2;
+    const bool vec = aligned16(V) && aligned16(w) && (m <= 1 || ld % VEC == 0);
+    const int rows = std::max(1, (m + MD_ROW - 1) / MD_ROW);
+    auto go = [&](auto kernel, int width) {
+        const int gx = grid_resident(kernel, (n + width - 1) / width);
+        const int gxr = std::max(1, gx / rows);
+        kernel<<<dim3(unsigned(gxr), unsigned(rows)), VT, 0, s>>>(n, V, ld, m, w, out);
+    };
+    if (vec) {
+        if (self) go(multidot_kernel<T, true, VEC>, VEC); else go(multidot_kernel<T, false, VEC>, VEC);
+    } else {
+        if (self) go(multidot_kernel<T, true, 1>, 1); else go(multidot_kernel<T, false, 1>, 1);
+    }
+    return int(cudaGetLastError());
+}
+
+template <typename T>
+int multiaxpy_t(int64_t n, T* w, const T* V, int64_t ld, int m, const double* h, double scale, cudaStream_t s) {
+    constexpr int VEC = sizeof(T) == 4 ? 4 : 2;
+    if (aligned16(V) && aligned16(w) && (m <= 1 || ld % VEC == 0))
+        multiaxpy_kernel<T, VEC><<<grid_resident(multiaxpy_kernel<T, VEC>, (n + VEC - 1) / VEC), VT, 0, s>>>(
+            n, w, V, ld, m, h, scale);
+    else
+        multiaxpy_kernel<T, 1><<<grid_resident(multiaxpy_kernel<T, 1>, n), VT, 0, s>>>(n, w, V, ld, m, h, scale);
+    return int(cudaGetLastError());
+}
+
 int vec_multidot(int64_t n, int vprec, const void* V, int64_t ld, int m, int wprec, const void* w,
                  double* out, int self_norm, cudaStream_t s) {
     const int mo = m + (self_norm ? 1 : 0);
@@ -253,39 +294,21 @@ int vec_multidot(int64_t n, int vprec, const void* V, int64_t ld, int m, int wpr
     if (m < 0 || m > MAXV || vprec != wprec) return int(cudaErrorInvalidValue);
     cudaError_t e = cudaMemsetAsync(out, 0, sizeof(double) * mo, s);
     if (e != cudaSuccess) return int(e);
-    const float* vf = static_cast<const float*>(V);
-    const double* vd = static_cast<const double*>(V);
-    const float* wf = static_cast<const float*>(w);
-    const double* wd = static_cast<const double*>(w);
-    if (vprec == 1) {
-        if (self_norm) multidot_f32<true><<<grid_resident(multidot_f32<true>, n), VT, 0, s>>>(n, vf, ld, m, wf, out);
-        else multidot_f32<false><<<grid_resident(multidot_f32<false>, n), VT, 0, s>>>(n, vf, ld, m, wf, out);
-    } else {
-        if (self_norm) multidot_f64<true><<<grid_resident(multidot_f64<true>, n), VT, 0, s>>>(n, vd, ld, m, wd, out);
-        else multidot_f64<false><<<grid_resident(multidot_f64<false>, n), VT, 0, s>>>(n, vd, ld, m, wd, out);
-    }
-    return int(cudaGetLastError());
+    if (vprec == 1)
+        return multidot_t(n, static_cast<const float*>(V), ld, m, static_cast<const float*>(w), out, self_norm != 0, s);
+    return multidot_t(n, static_cast<const double*>(V), ld, m, static_cast<const double*>(w), out, self_norm != 0, s);
 }
 
 int vec_multiaxpy(int64_t n, int prec, void* w, const void* V, int64_t ld, int m, const double* h, double scale,
                   double* dots, cudaStream_t s) {
     if (m < 0 || m > MAXV) return int(cudaErrorInvalidValue);
-    if (dots) {
-        cudaError_t e = cudaMemsetAsync(dots, 0, sizeof(double) * (m + 1), s);
-        if (e != cudaSuccess) return int(e);
-    }
-    const float* vf = static_cast<const float*>(V);
-    const double* vd = static_cast<const double*>(V);
-    if (prec == 1) {
-        float* wf = static_cast<float*>(w);
-        if (dots) multiaxpy_f32<true><<<grid_resident(multiaxpy_f32<true>, n), VT, 0, s>>>(n, wf, vf, ld, m, h, scale, dots);
-        else multiaxpy_f32<false><<<grid_resident(multiaxpy_f32<false>, n), VT, 0, s>>>(n, wf, vf, ld, m, h, scale, nullptr);
-    } else {
-        double* wd = static_cast<double*>(w);
-        if (dots) multiaxpy_f64<true><<<grid_resident(multiaxpy_f64<true>, n), VT, 0, s>>>(n, wd, vd, ld, m, h, scale, dots);
-        else multiaxpy_f64<false><<<grid_resident(multiaxpy_f64<false>, n), VT, 0, s>>>(n, wd, vd, ld, m, h, scale, nullptr);
-    }
-    return int(cudaGetLastError());
+    // the dots of the updated w are a second pass (a multi-dot with its norm):
+    // two bandwidth-bound sweeps measured faster than one sweep that holds
+    // all m values of V per thread for the dots
+    int e = prec == 1 ? multiaxpy_t(n, static_cast<float*>(w), static_cast<const float*>(V), ld, m, h, scale, s)
+                      : multiaxpy_t(n, static_cast<double*>(w), static_cast<const double*>(V), ld, m, h, scale, s);
+    if (e || !dots) return e;
+    return vec_multidot(n, prec, V, ld, m, prec, w, dots, 1, s);
 }
 
 int vec_axpby(int64_t n, double a, const double* da, int xprec, const void* x, double b, int yprec, void* y,

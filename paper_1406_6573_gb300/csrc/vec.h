@@ -14,7 +14,7 @@ int vec_multidot(int64_t n, int vprec, const void* V, int64_t ld, int m, int wpr
                  double* out, int self_norm, cudaStream_t s);
 // w = scale (w - sum_j h[j] V[j ld + .]) (h on the device, m <= 32); if dots
 // (device, may be NULL): dots[j] = V_j . w (j < m) and dots[m] = ||w||^2 of
-// the updated w, from the same pass
+// the updated w (a second pass)
 int vec_multiaxpy(int64_t n, int prec, void* w, const void* V, int64_t ld, int m, const double* h, double scale,
                   double* dots, cudaStream_t s);
 // y = a (* da[0] if da) x + b y

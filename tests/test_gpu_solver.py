@@ -90,3 +90,23 @@ def test_linear_solve(transpose, inner, rtol):
         assert np.linalg.norm(res) <= 1.01 * rtol * np.linalg.norm(b), (np.linalg.norm(res) / np.linalg.norm(b), rep)
     finally:
         capi.stokes_solver_destroy(s)
+
+
+def test_nonfinite_inputs_are_reported():
+    """A NaN in the initial guess or in a right-hand side gives
+    STOKES_E_NONFINITE (-5) without running the iteration."""
+    wl, o, m, lb = _setup("box_4x4x2_q2p1")
+    p = params(wl.phys, torch.as_tensor(lb, dtype=torch.float64, device="cuda"))
+    s = capi.stokes_solver_create(m.handle, _opts(capi.STOKES_F32))
+    try:
+        up = torch.zeros(o.ndof, dtype=torch.float64, device="cuda")
+        up[7] = float("nan")
+        rc, rep = capi.stokes_newton_solve(s, p, up, check=False)
+        assert rc == -5 and not rep["converged"] and rep["newton_its"] == 0
+        b = torch.zeros(o.ndof, dtype=torch.float64, device="cuda")
+        b[3] = float("inf")
+        x = torch.zeros_like(b)
+        rc, _ = capi.stokes_linear_solve(s, p, torch.zeros_like(b), b, x, check=False)
+        assert rc == -5
+    finally:
+        capi.stokes_solver_destroy(s)
