@@ -38,7 +38,7 @@ STATE_FIELDS = 11
 # DRAM bytes (read + write) of one state_apply_kernel<float> launch, from the
 # ncu capture summarised in profiles/state_apply_f32_slab_128x128x8_q2p1.md;
 # only valid for the kernel source that capture was taken from.
-STATE_APPLY_TRAFFIC = {"slab_128x128x8_q2p1": 194371328 + 10344192}
+STATE_APPLY_TRAFFIC = {"slab_128x128x8_q2p1": 214580224 + 12704000}
 
 
 def workload_label(wl):
@@ -276,7 +276,15 @@ def run_ours(args):
     el_launches, el_ms = prof["element"]
     el_avg_s = el_ms / max(el_launches, 1) / 1e3
     sstride = ((2 + STATE_FIELDS * q3) + 3) // 4 * 4
-    bytes_alg = (mesh.E * sstride * 4 + 2 * ndof * 4 + mesh.E * n3 * 4 + mesh.E * 8)
+    # element kernel of one apply (it also does the basal Robin term and the
+    # constraint rows): state, x read and y written once, element map, hanging
+    # code and basal index per element, basal face geometry and map, log(beta),
+    # basal node list and projector
+    mask = wl.refine_mask().reshape(wl.nz, wl.ny, wl.nx)[0]
+    n_faces = int(wl.nx * wl.ny + 3 * mask.sum())
+    q2 = (wl.k + 1) ** 2
+    bytes_basal = (n_faces * (4 * q2 * 8 + q2 * 4) + mesh.Nb * (8 + 4 + 48)) if wl.phys.robin else mesh.Nb * 52
+    bytes_alg = (mesh.E * sstride * 4 + 2 * ndof * 4 + mesh.E * n3 * 4 + mesh.E * 8 + bytes_basal)
     achieved = bytes_alg / el_avg_s / 1e9
     shares = {k: v[1] for k, v in prof.items()}
     tot = sum(shares.values())

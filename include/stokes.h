@@ -219,6 +219,12 @@ int stokes_linearize(stokes_state* state, const stokes_params* params,
 int stokes_state_apply(const stokes_state* state, const void* x, void* y, void* stream);
 int stokes_state_apply_transpose(const stokes_state* state, const void* x, void* y,
                                  void* stream);
+/* y = J_c (0, x_p): the velocity rows are P B^T x_p, the pressure-to-velocity
+ * block of the Newton system (the off-diagonal block of the block
+ * preconditioner, Eq. 4.1), the pressure rows are zero; the velocity part of
+ * x is ignored.  Reads only the geometric part of the stored state. */
+int stokes_state_apply_pressure_block(const stokes_state* state, const void* x, void* y,
+                                      void* stream);
 
 /* ---- Newton-Krylov solver (Section 4) -------------------------------------
  * Inexact Newton with backtracking on ||r||_2 and Eisenstat-Walker forcing;

@@ -99,6 +99,7 @@ _SIGS = {
                                     C.c_void_p, C.c_void_p, C.c_void_p]),
     "stokes_param_grad_A_fixed_order": (C.c_int, [C.c_void_p, C.POINTER(stokes_params), C.c_void_p,
                                                   C.c_void_p, C.c_void_p, C.c_void_p]),
+    "stokes_state_apply_pressure_block": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "stokes_state_create": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_void_p)]),
     "stokes_state_destroy": (C.c_int, [C.c_void_p]),
     "stokes_linearize": (C.c_int, [C.c_void_p, C.POINTER(stokes_params), C.c_void_p, C.c_void_p]),
@@ -236,6 +237,10 @@ def stokes_state_apply(s, x, y, stream=None):
 
 def stokes_state_apply_transpose(s, x, y, stream=None):
     _check(lib().stokes_state_apply_transpose(s, _ptr(x), _ptr(y), _stream(stream)))
+
+
+def stokes_state_apply_pressure_block(s, x, y, stream=None):
+    _check(lib().stokes_state_apply_pressure_block(s, _ptr(x), _ptr(y), _stream(stream)))
 
 
 def stokes_profile_begin(h):

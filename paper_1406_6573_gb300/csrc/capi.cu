@@ -187,10 +187,22 @@ int operator_sequence(const stokes_mesh* m, const stokes_params* p, int mode, in
     if (e) return cuda_fail(cudaError_t(e), "clearing the output");
     ElemArgs a = elem_args(m, p);
     a.x = x; a.y = y; a.u = u; a.cstate = cstate;
+    const bool robin = p->robin && m->h.nF > 0;
+    if (mode == MODE_STATE_APPLY) {
+        // the stored-state kernel also does the basal Robin term and the
+        // constraint rows (one launch per apply)
+        a.face = face_args(m, p);
+        a.face.x = x; a.face.y = y;
+        a.fuse_robin = robin;
+        a.fuse_constraint = 1;
+        a.Nb = m->h.Nb; a.basal_nodes = m->d_basal_nodes; a.basal_P = m->d_basal_P;
+        a.cscale = p->constraint_scale;
+    }
     e = timed(m, 1, s, [&] { return launch_elem(m->h.k, mode, prec, state_prec, trans, a, s); });
     if (e) return cuda_fail(cudaError_t(e), "element kernel launch");
     if (mode == MODE_STATE_GRADP) return STOKES_OK;   // zero velocity input: no Robin or (I - P) term
-    if (p->robin && m->h.nF > 0) {
+    if (mode == MODE_STATE_APPLY) return STOKES_OK;
+    if (robin) {
         FaceArgs f = face_args(m, p);
         f.x = x; f.y = y;
         e = timed(m, 2, s, [&] { return launch_face(m->h.k, FACE_APPLY, prec, f, s); });
@@ -458,7 +470,8 @@ int stokes_linearize(stokes_state* state, const stokes_params* params, const dou
     return STOKES_OK;
 }
 
-static int state_apply_common(const stokes_state* state, const void* x, void* y, void* stream, bool trans) {
+static int state_apply_common(const stokes_state* state, const void* x, void* y, void* stream, bool trans,
+                              int mode = MODE_STATE_APPLY) {
     if (!state) return fail(STOKES_E_INVAL, "state is NULL");
     if (!state->linearized) return fail(STOKES_E_INVAL, "state has not been linearized");
     const stokes_mesh* mesh = state->mesh;
@@ -468,7 +481,7 @@ static int state_apply_common(const stokes_state* state, const void* x, void* y,
     if (x == y) return fail(STOKES_E_INVAL, "x and y must not alias");
     DeviceGuard g(mesh->device);
     if (g.err != cudaSuccess) return cuda_fail(g.err, "selecting the device");
-    return operator_sequence(mesh, &state->params, MODE_STATE_APPLY, state->prec, state->prec, trans, x,
+    return operator_sequence(mesh, &state->params, mode, state->prec, state->prec, trans, x,
                              nullptr, state->d_state, y, static_cast<cudaStream_t>(stream));
 }
 
@@ -478,6 +491,10 @@ int stokes_state_apply(const stokes_state* state, const void* x, void* y, void* 
 
 int stokes_state_apply_transpose(const stokes_state* state, const void* x, void* y, void* stream) {
     return state_apply_common(state, x, y, stream, true);
+}
+
+int stokes_state_apply_pressure_block(const stokes_state* state, const void* x, void* y, void* stream) {
+    return state_apply_common(state, x, y, stream, false, MODE_STATE_GRADP);
 }
 
 }  // extern "C"

@@ -57,6 +57,11 @@ __device__ __forceinline__ void sym6(const T (&g)[3][3], T& E00, T& E11, T& E22,
 // exchange scratch of one element slot: 9 buffers (3 per velocity component),
 // padded so that consecutive slots start 12 banks apart (fewer shared-memory
 // bank conflicts between the elements of a warp); a multiple of 16 bytes
+// packed-line slot of the stored-state kernel: 9 buffers of N1^3 values,
+// padded so that consecutive slots start N2 banks apart (FP32), which puts
+// the N1^2 lanes of the EPW elements of a warp on distinct banks
+template <typename T> constexpr int SLOT_PACKED =
+    sizeof(T) == 4 ? (9 * N2 * N1 + 31 - N2) / 32 * 32 + N2 : 9 * N2 * N1 + 2;
 template <typename T> constexpr int SLOT =
     sizeof(T) == 4 ? (9 * BUFLEN<T> + 31 - 12) / 32 * 32 + 12 : 9 * BUFLEN<T> + 2;
 
@@ -254,161 +259,6 @@ __global__ void __launch_bounds__(32 * GW<T>) elem_kernel(ElemArgs a) {
     }
 }
 
-// ================================================== state apply (hot path)
-// Line exchanges of the sum factorisation in the stored-state kernel: warp
-// shuffles for degrees >= STOKES_STATE_SHFL_MIN_K, shared memory below
-// (measured per degree).
-#ifndef STOKES_STATE_SHFL_MIN_K
-#define STOKES_STATE_SHFL_MIN_K 3
-#endif
-constexpr bool STATE_SHFL = K >= STOKES_STATE_SHFL_MIN_K;
-// y = J x from the stored linearised state.  Persistent: each warp walks its
-// element groups (EPW consecutive elements); the state block of the next
-// group (contiguous, 16-byte multiple) is staged into shared memory by a bulk
-// asynchronous copy (TMA, cp.async.bulk) completing on a per-warp mbarrier,
-// double-buffered, so the state stream overlaps the gather and the forward
-// contractions of the current group.
-template <typename T>
-struct StateApplyCfg {
-    static constexpr int W = sizeof(T) == 8 ? 4 : 8;        // warps per block
-    static constexpr int BUF = EPW * SSTRIDE;                // values per stage buffer
-    static constexpr int SCR = (EPW + 1) * SLOT<T>;          // scratch per warp
-    static constexpr int PER_WARP = ((2 * BUF + SCR) * int(sizeof(T)) + 127) / 128 * 128;
-    static constexpr int SMEM = W * PER_WARP + W * 2 * 8;
-};
-
-// PONLY: the velocity part of x is taken as zero (B^T p only, used by the
-// block preconditioner): no gather, no forward contractions, no pressure rows.
-template <typename T, bool PONLY>
-__global__ void __launch_bounds__(32 * StateApplyCfg<T>::W) state_apply_kernel(ElemArgs a) {
-    using C = StateApplyCfg<T>;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    const LaneMap L;
-    const int i = L.i, j = L.j, ij = L.ij, es = L.es, lane = L.lane;
-    unsigned char* wbase = smem_raw + L.warp * C::PER_WARP;
-    T* stage[2] = {reinterpret_cast<T*>(wbase), reinterpret_cast<T*>(wbase) + C::BUF};
-    T* scratch = reinterpret_cast<T*>(wbase) + 2 * C::BUF;
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + C::W * C::PER_WARP) + 2 * L.warp;
-    T* sb = scratch + es * SLOT<T>;
-    const int ps = a.pspace;
-    const T* S = static_cast<const T*>(a.cstate);
-    const T* x = static_cast<const T*>(a.x);
-    T* y = static_cast<T*>(a.y);
-    Rows<T> R;
-    R.load(i, j);
-
-    const int64_t ngroups = (a.E + EPW - 1) / EPW;
-    const int64_t gstride = int64_t(gridDim.x) * C::W;
-    int64_t g = int64_t(blockIdx.x) * C::W + L.warp;
-
-    auto group_bytes = [&](int64_t gg) -> uint32_t {
-        const int64_t ne = (a.E - gg * EPW) < EPW ? (a.E - gg * EPW) : EPW;
-        return uint32_t(ne * SSTRIDE * int64_t(sizeof(T)));
-    };
-    if (lane == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
-        fence_mbar_init();
-    }
-    __syncwarp();
-    if (g < ngroups && lane == 0) {
-        const uint32_t nb = group_bytes(g);
-        mbar_arrive_expect_tx(&bar[0], nb);
-        bulk_g2s(stage[0], S + g * EPW * SSTRIDE, nb, &bar[0]);
-    }
-    for (int it = 0; g < ngroups; g += gstride, ++it) {
-        const int buf = it & 1;
-        // prefetch the next group into the other buffer (its readers finished
-        // at the end of the previous iteration)
-        if (lane == 0 && g + gstride < ngroups) {
-            const uint32_t nb = group_bytes(g + gstride);
-            fence_proxy_async();
-            mbar_arrive_expect_tx(&bar[buf ^ 1], nb);
-            bulk_g2s(stage[buf ^ 1], S + (g + gstride) * EPW * SSTRIDE, nb, &bar[buf ^ 1]);
-        }
-        const int64_t e = g * EPW + es;
-        const bool active = (es < EPW) && (e < a.E);
-        ColNodes cn;
-        col_nodes(a, e, ij, active, cn);
-        const uint32_t h = active ? a.hang[e] : 0u;
-        const bool any_h = a.any_hang ? (__any_sync(0xffffffffu, (h & ((1u << HANG_CHILD0) - 1)) != 0) != 0) : false;
-
-        T pc[N1];
-        pressure_fold<T, T>(a, x, e, active, i, j, pc);
-        T G[3][3][Q];
-        if constexpr (!PONLY) {
-            T v[3][N1];
-            gather_velocity<T, T>(a, x, cn, e, active, ij, v);
-            if (any_h) hanging_forward<T, 3>(v, h, active, i, j, sb);
-            if constexpr (STATE_SHFL) ref_gradient<T, 3>(R, v, G, i, j, sb);
-            else ref_gradient_smem<T, 3>(R, v, G, i, j, sb);
-        } else {
-            #pragma unroll
-            for (int c = 0; c < 3; ++c)
-                #pragma unroll
-                for (int m = 0; m < 3; ++m)
-                    #pragma unroll
-                    for (int lq = 0; lq < Q; ++lq) G[c][m][lq] = T(0);
-        }
-
-        if (!mbar_wait_bounded(&bar[buf], uint32_t((it >> 1) & 1))) {
-            // the staged state never arrived: report, let the copy drain, stop
-            if (lane == 0) atomicOr(a.err, 1);
-            mbar_wait_bounded(&bar[buf], uint32_t((it >> 1) & 1));
-            return;
-        }
-        const T* st = stage[buf] + (es < EPW ? es : 0) * SSTRIDE;
-        const T ia = st[0], ib = st[1];
-        T gq[Q];
-        #pragma unroll
-        for (int lq = 0; lq < Q; ++lq) {
-            const T* f = st + 2 + sidx(i, j, lq);
-            const T g0 = f[0], g1 = f[Q3], g2 = f[2 * Q3];
-            const T wdj = f[3 * Q3], muw = f[4 * Q3];
-            const T D00 = f[5 * Q3], D11 = f[6 * Q3], D22 = f[7 * Q3];
-            const T D01 = f[8 * Q3], D02 = f[9 * Q3], D12 = f[10 * Q3];
-            // physical gradient: Jinv = [[ia,0,0],[0,ib,0],[g0,g1,g2]]
-            T gr[3][3];
-            #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const T gz = G[c][2][lq];
-                gr[c][0] = G[c][0][lq] * ia + gz * g0;
-                gr[c][1] = G[c][1][lq] * ib + gz * g1;
-                gr[c][2] = gz * g2;
-            }
-            T E00, E11, E22, E01, E02, E12;
-            sym6(gr, E00, E11, E22, E01, E02, E12);
-            // Eq. 2.7 as a symmetric map: w detJ mu' E = muw E - (Dhat:E) Dhat
-            const T s = D00 * E00 + D11 * E11 + D22 * E22 + T(2) * (D01 * E01 + D02 * E02 + D12 * E12);
-            const T pw = active ? pressure_at<T>(pc, ps, lq) * wdj : T(0);
-            T tau[3][3];
-            tau[0][0] = muw * E00 - s * D00 - pw;
-            tau[1][1] = muw * E11 - s * D11 - pw;
-            tau[2][2] = muw * E22 - s * D22 - pw;
-            tau[0][1] = tau[1][0] = muw * E01 - s * D01;
-            tau[0][2] = tau[2][0] = muw * E02 - s * D02;
-            tau[1][2] = tau[2][1] = muw * E12 - s * D12;
-            gq[lq] = -wdj * (gr[0][0] + gr[1][1] + gr[2][2]);
-            // reference stress S[c][m] = sum_d Jinv[m][d] tau[c][d]
-            #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                G[c][0][lq] = ia * tau[c][0];
-                G[c][1][lq] = ib * tau[c][1];
-                G[c][2][lq] = g0 * tau[c][0] + g1 * tau[c][1] + g2 * tau[c][2];
-            }
-        }
-        __syncwarp();
-        T out[3][N1];
-        T dummy[3][Q];
-        if constexpr (STATE_SHFL) ref_gradient_T<T, 3, false>(R, G, dummy, out, i, j, sb);
-        else ref_gradient_T_smem<T, 3, false>(R, G, dummy, out, i, j, sb);
-        if constexpr (!PONLY) pressure_rows<T>(gq, a.npr, ps, i, j, ij, active, sb, y + 3 * a.Nv + e * a.npr);
-        if (any_h) hanging_transpose<T, 3>(out, h, active, i, j, sb);
-        scatter_velocity<T>(a, y, cn, e, active, ij, out);
-        __syncwarp();
-    }
-}
-
 // ============================================================ basal faces
 // Robin term int_{Gamma_b} beta T v . T w ds (Eq. 2.4a in weak form, Eq. 2.5)
 // and its log(beta) adjoint product.  One lane per bottom-plane node (i, j) of
@@ -513,20 +363,19 @@ __device__ __forceinline__ void face_interp_T(const Rows<T>& R, const T (&v)[NC]
     wsync();
 }
 
+// One group of EPW basal faces (faces fg * EPW + fs) on one warp; sb: the
+// lane's element scratch (4 N2 values).  Called by face_kernel and by the
+// stored-state kernel after its element groups.
 template <typename T, int MODE>
-__global__ void __launch_bounds__(THREADS) face_kernel(FaceArgs a) {
+__device__ __forceinline__ void face_group(const FaceArgs& a, const LaneMap& L, const Rows<T>& R, int64_t fg,
+                                           T* sb) {
     constexpr int Q2 = Q * Q;
-    __shared__ T sbuf[WARPS][EPW + 1][4 * N2];
-    const LaneMap L;
     const int i = L.i, j = L.j, ij = L.ij, fs = L.es;
-    const int64_t f = int64_t(blockIdx.x) * EPB + L.warp * EPW + fs;
+    const int64_t f = fg * EPW + fs;
     const bool active = (fs < EPW) && (f < a.nF);
-    T* sb = sbuf[L.warp][fs];
     const int64_t e = active ? a.face_elem[f] : 0;
     const uint32_t h = active ? a.hang[e] : 0u;
     const bool any_h = __any_sync(0xffffffffu, (h & ((1u << HANG_CHILD0) - 1)) != 0) != 0;
-    Rows<T> R;
-    R.load(i, j);
 
     // log(beta) at the face nodes (hanging-interpolated), then at Gauss points
     T lb[1];
@@ -584,6 +433,231 @@ __global__ void __launch_bounds__(THREADS) face_kernel(FaceArgs a) {
         if (active) atomic_add(a.g + a.fmap[f * N2 + ij], double(o[0]));
     }
 }
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(THREADS) face_kernel(FaceArgs a) {
+    __shared__ T sbuf[WARPS][EPW + 1][4 * N2];
+    const LaneMap L;
+    Rows<T> R;
+    R.load(L.i, L.j);
+    face_group<T, MODE>(a, L, R, int64_t(blockIdx.x) * WARPS + L.warp, sbuf[L.warp][L.es]);
+}
+
+// constraint rows y += s (I - P) x at basal nodes b = b0 + t * bstride (atomic:
+// run alongside other contributions to y)
+template <typename T>
+__device__ __forceinline__ void constraint_rows(const ElemArgs& a, int64_t b0, int64_t bstride) {
+    const T* x = static_cast<const T*>(a.face.x);
+    T* y = static_cast<T*>(a.face.y);
+    const T sc = T(a.cscale);
+    for (int64_t b = b0; b < a.Nb; b += bstride) {
+        const int64_t g = a.basal_nodes[b];
+        const double* p = a.basal_P + 6 * b;
+        const T x0 = x[3 * g], x1 = x[3 * g + 1], x2 = x[3 * g + 2];
+        const T p00 = T(p[0]), p11 = T(p[1]), p22 = T(p[2]), p01 = T(p[3]), p02 = T(p[4]), p12 = T(p[5]);
+        atomic_add(y + 3 * g, sc * (x0 - (p00 * x0 + p01 * x1 + p02 * x2)));
+        atomic_add(y + 3 * g + 1, sc * (x1 - (p01 * x0 + p11 * x1 + p12 * x2)));
+        atomic_add(y + 3 * g + 2, sc * (x2 - (p02 * x0 + p12 * x1 + p22 * x2)));
+    }
+}
+
+// ================================================== state apply (hot path)
+// Line exchanges of the sum factorisation in the stored-state kernel: warp
+// shuffles for degrees >= STOKES_STATE_SHFL_MIN_K, shared memory below
+// (measured per degree).
+#ifndef STOKES_STATE_SHFL_MIN_K
+#define STOKES_STATE_SHFL_MIN_K 3
+#endif
+constexpr bool STATE_SHFL = K >= STOKES_STATE_SHFL_MIN_K;
+// shared-memory exchange of the stored-state kernel with packed lines
+// (pitch N1) instead of 16-byte padded lines
+#ifndef STOKES_STATE_PACKED
+#define STOKES_STATE_PACKED 1
+#endif
+template <typename T> constexpr int STATE_PITCH = STOKES_STATE_PACKED ? N1 : LP<T>;
+template <typename T> constexpr int STATE_SLOT = STOKES_STATE_PACKED ? SLOT_PACKED<T> : SLOT<T>;
+// y = J x from the stored linearised state.  Persistent: each warp walks its
+// element groups (EPW consecutive elements); the state block of the next
+// group (contiguous, 16-byte multiple) is staged into shared memory by a bulk
+// asynchronous copy (TMA, cp.async.bulk) completing on a per-warp mbarrier,
+// double-buffered, so the state stream overlaps the gather and the forward
+// contractions of the current group.
+template <typename T>
+struct StateApplyCfg {
+    static constexpr int W = sizeof(T) == 8 ? 4 : 8;        // warps per block
+    // resident blocks per SM asked of the compiler: two for FP32 Q2 (128
+    // registers); shared memory allows only one for k >= 3 and for FP64
+    static constexpr int MINB = (sizeof(T) == 4 && K == 2) ? 2 : 1;
+    static constexpr int BUF = EPW * SSTRIDE;                // values per stage buffer
+    static constexpr int SCR = (EPW + 1) * STATE_SLOT<T>;    // scratch per warp
+    static constexpr int PER_WARP = ((2 * BUF + SCR) * int(sizeof(T)) + 127) / 128 * 128;
+    static constexpr int SMEM = W * PER_WARP + W * 2 * 8;
+};
+
+// bytes of the state prefix PONLY reads per element (2 + 4 q^3 values, 16-byte multiple)
+template <typename T> constexpr uint32_t STATE_PREFIX_BYTES = ((2 + 4 * Q3) * sizeof(T) + 15) / 16 * 16;
+
+// PONLY: the velocity part of x is taken as zero (B^T p only, used by the
+// block preconditioner): no gather, no forward contractions, no pressure rows.
+template <typename T, bool PONLY>
+__global__ void __launch_bounds__(32 * StateApplyCfg<T>::W, StateApplyCfg<T>::MINB) state_apply_kernel(ElemArgs a) {
+    using C = StateApplyCfg<T>;
+    constexpr uint32_t PREFIX_BYTES = STATE_PREFIX_BYTES<T>;
+    static_assert(STATE_PREFIX_BYTES<T> <= SSTRIDE * sizeof(T), "prefix inside the element block");
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const LaneMap L;
+    const int i = L.i, j = L.j, ij = L.ij, es = L.es, lane = L.lane;
+    unsigned char* wbase = smem_raw + L.warp * C::PER_WARP;
+    T* stage[2] = {reinterpret_cast<T*>(wbase), reinterpret_cast<T*>(wbase) + C::BUF};
+    T* scratch = reinterpret_cast<T*>(wbase) + 2 * C::BUF;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + C::W * C::PER_WARP) + 2 * L.warp;
+    T* sb = scratch + es * STATE_SLOT<T>;
+    const int ps = a.pspace;
+    const T* S = static_cast<const T*>(a.cstate);
+    const T* x = static_cast<const T*>(a.x);
+    T* y = static_cast<T*>(a.y);
+    Rows<T> R;
+    R.load(i, j);
+
+    const int64_t ngroups = (a.E + EPW - 1) / EPW;
+    const int64_t gstride = int64_t(gridDim.x) * C::W;
+    int64_t g = int64_t(blockIdx.x) * C::W + L.warp;
+
+    auto group_elems = [&](int64_t gg) -> int {
+        return int((a.E - gg * EPW) < EPW ? (a.E - gg * EPW) : EPW);
+    };
+    // stage the state of group gg into buffer b (lane 0).  PONLY needs only the
+    // leading fields of each element block (1/a, 1/b, Jinv row 3, w detJ):
+    // one copy per element of that prefix instead of the whole group block.
+    auto stage_group = [&](int64_t gg, int b) {
+        const int ne = group_elems(gg);
+        if constexpr (PONLY) {
+            mbar_arrive_expect_tx(&bar[b], uint32_t(ne) * PREFIX_BYTES);
+            for (int ee = 0; ee < ne; ++ee)
+                bulk_g2s(stage[b] + ee * SSTRIDE, S + (gg * EPW + ee) * SSTRIDE, PREFIX_BYTES, &bar[b]);
+        } else {
+            const uint32_t nb = uint32_t(ne * SSTRIDE * int64_t(sizeof(T)));
+            mbar_arrive_expect_tx(&bar[b], nb);
+            bulk_g2s(stage[b], S + gg * EPW * SSTRIDE, nb, &bar[b]);
+        }
+    };
+    if (lane == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+    if (g < ngroups && lane == 0) stage_group(g, 0);
+    for (int it = 0; g < ngroups; g += gstride, ++it) {
+        const int buf = it & 1;
+        // prefetch the next group into the other buffer (its readers finished
+        // at the end of the previous iteration)
+        if (lane == 0 && g + gstride < ngroups) {
+            fence_proxy_async();
+            stage_group(g + gstride, buf ^ 1);
+        }
+        const int64_t e = g * EPW + es;
+        const bool active = (es < EPW) && (e < a.E);
+        ColNodes cn;
+        col_nodes(a, e, ij, active, cn);
+        const uint32_t h = active ? a.hang[e] : 0u;
+        const bool any_h = a.any_hang ? (__any_sync(0xffffffffu, (h & ((1u << HANG_CHILD0) - 1)) != 0) != 0) : false;
+
+        T pc[N1];
+        pressure_fold<T, T>(a, x, e, active, i, j, pc);
+        T G[3][3][Q];
+        if constexpr (!PONLY) {
+            T v[3][N1];
+            gather_velocity<T, T>(a, x, cn, e, active, ij, v);
+            if (any_h) hanging_forward<T, 3>(v, h, active, i, j, sb);
+            if constexpr (STATE_SHFL) ref_gradient<T, 3>(R, v, G, i, j, sb);
+            else ref_gradient_smem<T, 3, STATE_PITCH<T>>(R, v, G, i, j, sb);
+        } else {
+            #pragma unroll
+            for (int c = 0; c < 3; ++c)
+                #pragma unroll
+                for (int m = 0; m < 3; ++m)
+                    #pragma unroll
+                    for (int lq = 0; lq < Q; ++lq) G[c][m][lq] = T(0);
+        }
+
+        if (!mbar_wait_bounded(&bar[buf], uint32_t((it >> 1) & 1))) {
+            // the staged state never arrived: report, let the copy drain, stop
+            if (lane == 0) atomicOr(a.err, 1);
+            mbar_wait_bounded(&bar[buf], uint32_t((it >> 1) & 1));
+            return;
+        }
+        const T* st = stage[buf] + (es < EPW ? es : 0) * SSTRIDE;
+        const T ia = st[0], ib = st[1];
+        T gq[Q];
+        #pragma unroll
+        for (int lq = 0; lq < Q; ++lq) {
+            const T* f = st + 2 + sidx(i, j, lq);
+            const T g0 = f[0], g1 = f[Q3], g2 = f[2 * Q3];
+            const T wdj = f[3 * Q3];
+            if constexpr (PONLY) {
+                // tau = -p w detJ I; reference stress S[c][m] = Jinv[m][c] tau_cc
+                const T pw = active ? pressure_at<T>(pc, ps, lq) * wdj : T(0);
+                G[0][0][lq] = -ia * pw; G[0][1][lq] = T(0); G[0][2][lq] = -g0 * pw;
+                G[1][0][lq] = T(0); G[1][1][lq] = -ib * pw; G[1][2][lq] = -g1 * pw;
+                G[2][0][lq] = T(0); G[2][1][lq] = T(0); G[2][2][lq] = -g2 * pw;
+                gq[lq] = T(0);
+                continue;
+            }
+            const T muw = f[4 * Q3];
+            const T D00 = f[5 * Q3], D11 = f[6 * Q3], D22 = f[7 * Q3];
+            const T D01 = f[8 * Q3], D02 = f[9 * Q3], D12 = f[10 * Q3];
+            // physical gradient: Jinv = [[ia,0,0],[0,ib,0],[g0,g1,g2]]
+            T gr[3][3];
+            #pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const T gz = G[c][2][lq];
+                gr[c][0] = G[c][0][lq] * ia + gz * g0;
+                gr[c][1] = G[c][1][lq] * ib + gz * g1;
+                gr[c][2] = gz * g2;
+            }
+            T E00, E11, E22, E01, E02, E12;
+            sym6(gr, E00, E11, E22, E01, E02, E12);
+            // Eq. 2.7 as a symmetric map: w detJ mu' E = muw E - (Dhat:E) Dhat
+            const T s = D00 * E00 + D11 * E11 + D22 * E22 + T(2) * (D01 * E01 + D02 * E02 + D12 * E12);
+            const T pw = active ? pressure_at<T>(pc, ps, lq) * wdj : T(0);
+            T tau[3][3];
+            tau[0][0] = muw * E00 - s * D00 - pw;
+            tau[1][1] = muw * E11 - s * D11 - pw;
+            tau[2][2] = muw * E22 - s * D22 - pw;
+            tau[0][1] = tau[1][0] = muw * E01 - s * D01;
+            tau[0][2] = tau[2][0] = muw * E02 - s * D02;
+            tau[1][2] = tau[2][1] = muw * E12 - s * D12;
+            gq[lq] = -wdj * (gr[0][0] + gr[1][1] + gr[2][2]);
+            // reference stress S[c][m] = sum_d Jinv[m][d] tau[c][d]
+            #pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                G[c][0][lq] = ia * tau[c][0];
+                G[c][1][lq] = ib * tau[c][1];
+                G[c][2][lq] = g0 * tau[c][0] + g1 * tau[c][1] + g2 * tau[c][2];
+            }
+        }
+        __syncwarp();
+        T out[3][N1];
+        T dummy[3][Q];
+        if constexpr (STATE_SHFL) ref_gradient_T<T, 3, false>(R, G, dummy, out, i, j, sb);
+        else ref_gradient_T_smem<T, 3, false, STATE_PITCH<T>>(R, G, dummy, out, i, j, sb);
+        if constexpr (!PONLY) pressure_rows<T>(gq, a.npr, ps, i, j, ij, active, sb, y + 3 * a.Nv + e * a.npr);
+        if (any_h) hanging_transpose<T, 3>(out, h, active, i, j, sb);
+        scatter_velocity<T>(a, y, cn, e, active, ij, out);
+        __syncwarp();
+    }
+    if constexpr (!PONLY) {
+        // basal terms of the same apply, after this warp's element groups
+        const int64_t w0 = int64_t(blockIdx.x) * C::W + L.warp;
+        if (a.fuse_robin) {
+            const int64_t nfg = (a.face.nF + EPW - 1) / EPW;
+            for (int64_t fg = w0; fg < nfg; fg += gstride) face_group<T, FACE_APPLY>(a.face, L, R, fg, sb);
+        }
+        if (a.fuse_constraint) constraint_rows<T>(a, w0 * 32 + lane, gstride * 32);
+    }
+}
+
 
 // ---------------------------------------------------------------- launchers
 // warps launched by the FP64 element kernel over E elements (whole blocks):

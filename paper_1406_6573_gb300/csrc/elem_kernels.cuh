@@ -302,6 +302,22 @@ __device__ __forceinline__ T lane_val(T v, int i2, int j2) {
     return __shfl_sync(0xffffffffu, v, base + i2 + N1 * j2);
 }
 
+// Line layouts and loads for a line pitch P (values between consecutive
+// lines): the padded pitch LP<T> allows one 16-byte load per line; the packed
+// pitch N1 puts the N1^2 lanes of an element on consecutive banks (no store
+// conflicts between the elements of a warp) at one scalar load per value.
+template <int P> __device__ __forceinline__ int xlp(int i, int j, int l) { return i + P * (j + N1 * l); }
+template <int P> __device__ __forceinline__ int ylp(int i, int j, int l) { return j + P * (i + N1 * l); }
+template <typename T, int P>
+__device__ __forceinline__ void load_line_p(const T* p, T (&o)[N1]) {
+    if constexpr (P == LP<T>) {
+        load_line<T>(p, o);
+    } else {
+        #pragma unroll
+        for (int k = 0; k < N1; ++k) o[k] = p[k];
+    }
+}
+
 // Reference gradients at the Gauss points (iq = i, jq = j, lq) of the NC
 // fields whose nodal columns the thread holds in vin:
 //   zeta: interpolate (registers);  eta: interpolate and differentiate the
@@ -394,48 +410,48 @@ __device__ __forceinline__ void ref_gradient_T(const Rows<T>& R, const T (&S)[NC
 //   same line;  xi: interpolate and differentiate the interpolated line, and
 //   interpolate the eta-derivative line;  zeta derivative by collocation.
 // buf: 3 NC exchange buffers of BUFLEN values.
-template <typename T, int NC>
+template <typename T, int NC, int P = LP<T>>
 __device__ __forceinline__ void ref_gradient_smem(const Rows<T>& R, const T (&vin)[NC][N1], T (&G)[NC][3][Q],
                                              int i, int j, T* buf) {
     #pragma unroll
     for (int c = 0; c < NC; ++c) {
-        T* b0 = buf + (3 * c) * BUFLEN<T>;
+        T* b0 = buf + (3 * c) * P * N2;
         #pragma unroll
         for (int lq = 0; lq < Q; ++lq) {
             T s = 0;
             #pragma unroll
             for (int l = 0; l < N1; ++l) s += Tab<T>::B(lq, l) * vin[c][l];
-            b0[yl<T>(i, j, lq)] = s;
+            b0[ylp<P>(i, j, lq)] = s;
         }
     }
     wsync();
     #pragma unroll
     for (int c = 0; c < NC; ++c) {              // eta: thread (node i, jq = j)
-        const T* b0 = buf + (3 * c) * BUFLEN<T>;
-        T* b1 = buf + (3 * c + 1) * BUFLEN<T>;
-        T* b2 = buf + (3 * c + 2) * BUFLEN<T>;
+        const T* b0 = buf + (3 * c) * P * N2;
+        T* b1 = buf + (3 * c + 1) * P * N2;
+        T* b2 = buf + (3 * c + 2) * P * N2;
         #pragma unroll
         for (int lq = 0; lq < Q; ++lq) {
             T ln[N1];
-            load_line<T>(b0 + yl<T>(i, 0, lq), ln);
+            load_line_p<T, P>(b0 + ylp<P>(i, 0, lq), ln);
             T si = 0, sd = 0;
             #pragma unroll
             for (int m = 0; m < N1; ++m) { si += R.Bj[m] * ln[m]; sd += R.Tj[m] * ln[m]; }
-            b1[xl<T>(i, j, lq)] = si;
-            b2[xl<T>(i, j, lq)] = sd;
+            b1[xlp<P>(i, j, lq)] = si;
+            b2[xlp<P>(i, j, lq)] = sd;
         }
     }
     wsync();
     #pragma unroll
     for (int c = 0; c < NC; ++c) {              // xi: thread (iq = i, jq = j)
-        const T* b1 = buf + (3 * c + 1) * BUFLEN<T>;
-        const T* b2 = buf + (3 * c + 2) * BUFLEN<T>;
+        const T* b1 = buf + (3 * c + 1) * P * N2;
+        const T* b2 = buf + (3 * c + 2) * P * N2;
         T a[Q];
         #pragma unroll
         for (int lq = 0; lq < Q; ++lq) {
             T l1[N1], l2[N1];
-            load_line<T>(b1 + xl<T>(0, j, lq), l1);
-            load_line<T>(b2 + xl<T>(0, j, lq), l2);
+            load_line_p<T, P>(b1 + xlp<P>(0, j, lq), l1);
+            load_line_p<T, P>(b2 + xlp<P>(0, j, lq), l2);
             T sv = 0, sx = 0, sy = 0;
             #pragma unroll
             for (int m = 0; m < N1; ++m) { sv += R.Bi[m] * l1[m]; sx += R.Ti[m] * l1[m]; sy += R.Bi[m] * l2[m]; }
@@ -456,18 +472,18 @@ __device__ __forceinline__ void ref_gradient_smem(const Rows<T>& R, const T (&vi
 //   sum_qp (d phi/d xi) S[c][0] + (d phi/d eta) S[c][1] + (d phi/d zeta) S[c][2] + phi Sv[c]
 // (collocated derivative transposes at the Gauss points, then the three
 // transposed interpolations), NC fields advancing together.
-template <typename T, int NC, bool HAS_VAL>
+template <typename T, int NC, bool HAS_VAL, int P = LP<T>>
 __device__ __forceinline__ void ref_gradient_T_smem(const Rows<T>& R, const T (&S)[NC][3][Q], const T (&Sv)[NC][Q],
                                                T (&out)[NC][N1], int i, int j, T* buf) {
     T t[NC][Q];
     #pragma unroll
     for (int c = 0; c < NC; ++c) {
-        T* b0 = buf + (3 * c) * BUFLEN<T>;
-        T* b1 = buf + (3 * c + 1) * BUFLEN<T>;
+        T* b0 = buf + (3 * c) * P * N2;
+        T* b1 = buf + (3 * c + 1) * P * N2;
         #pragma unroll
         for (int lq = 0; lq < Q; ++lq) {
-            b0[xl<T>(i, j, lq)] = S[c][0][lq];
-            b1[yl<T>(i, j, lq)] = S[c][1][lq];
+            b0[xlp<P>(i, j, lq)] = S[c][0][lq];
+            b1[ylp<P>(i, j, lq)] = S[c][1][lq];
             T s = HAS_VAL ? Sv[c][lq] : T(0);
             #pragma unroll
             for (int m = 0; m < Q; ++m) s += Tab<T>::Dg(m, lq) * S[c][2][m];
@@ -477,43 +493,43 @@ __device__ __forceinline__ void ref_gradient_T_smem(const Rows<T>& R, const T (&
     wsync();
     #pragma unroll
     for (int c = 0; c < NC; ++c) {
-        const T* b0 = buf + (3 * c) * BUFLEN<T>;
-        const T* b1 = buf + (3 * c + 1) * BUFLEN<T>;
-        T* b2 = buf + (3 * c + 2) * BUFLEN<T>;
+        const T* b0 = buf + (3 * c) * P * N2;
+        const T* b1 = buf + (3 * c + 1) * P * N2;
+        T* b2 = buf + (3 * c + 2) * P * N2;
         #pragma unroll
         for (int lq = 0; lq < Q; ++lq) {
             T lx[N1], ly[N1];
-            load_line<T>(b0 + xl<T>(0, j, lq), lx);
-            load_line<T>(b1 + yl<T>(i, 0, lq), ly);
+            load_line_p<T, P>(b0 + xlp<P>(0, j, lq), lx);
+            load_line_p<T, P>(b1 + ylp<P>(i, 0, lq), ly);
             T s = t[c][lq];
             #pragma unroll
             for (int m = 0; m < Q; ++m) s += R.DTi[m] * lx[m] + R.DTj[m] * ly[m];
-            b2[xl<T>(i, j, lq)] = s;
+            b2[xlp<P>(i, j, lq)] = s;
         }
     }
     wsync();
     #pragma unroll
     for (int c = 0; c < NC; ++c) {              // xi^T: thread (node i, jq = j)
-        const T* b2 = buf + (3 * c + 2) * BUFLEN<T>;
-        T* b0 = buf + (3 * c) * BUFLEN<T>;
+        const T* b2 = buf + (3 * c + 2) * P * N2;
+        T* b0 = buf + (3 * c) * P * N2;
         #pragma unroll
         for (int lq = 0; lq < Q; ++lq) {
             T ln[N1];
-            load_line<T>(b2 + xl<T>(0, j, lq), ln);
+            load_line_p<T, P>(b2 + xlp<P>(0, j, lq), ln);
             T s = 0;
             #pragma unroll
             for (int m = 0; m < Q; ++m) s += R.BTi[m] * ln[m];
-            b0[yl<T>(i, j, lq)] = s;
+            b0[ylp<P>(i, j, lq)] = s;
         }
     }
     wsync();
     #pragma unroll
     for (int c = 0; c < NC; ++c) {              // eta^T then zeta^T
-        const T* b0 = buf + (3 * c) * BUFLEN<T>;
+        const T* b0 = buf + (3 * c) * P * N2;
         #pragma unroll
         for (int lq = 0; lq < Q; ++lq) {
             T ln[N1];
-            load_line<T>(b0 + yl<T>(i, 0, lq), ln);
+            load_line_p<T, P>(b0 + ylp<P>(i, 0, lq), ln);
             T s = 0;
             #pragma unroll
             for (int m = 0; m < Q; ++m) s += R.BTj[m] * ln[m];

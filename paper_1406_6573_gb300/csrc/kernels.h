@@ -24,6 +24,23 @@ enum ElemMode : int {
 // Dhat (6: 00 11 22 01 02 12).
 constexpr int STATE_FIELDS = 11;
 
+struct FaceArgs {
+    int64_t nF, Nv;
+    const int32_t* face_elem;  // [nF]
+    const int32_t* nodes;
+    const uint32_t* hang;
+    const int32_t* pidx;
+    const double* pel;
+    const double* fgeo;        // [nF][4][q^2]
+    const int32_t* fmap;       // [nF][n1^2]
+    const double* logbeta;     // [Nb]
+    const void* x;             // vector whose basal trace enters beta T x
+    void* y;                   // output (accumulated)
+    const double* u;           // gradient: state
+    const double* lam;         // gradient: adjoint
+    double* g;                 // gradient output [Nb] (accumulated)
+};
+
 struct ElemArgs {
     int64_t E, Nv;
     int npr, pspace, any_hang;
@@ -49,24 +66,17 @@ struct ElemArgs {
                                // computed as I + NX (J + NY L) instead of read from nodes
     int* err;                  // device status word (bounded waits that expired)
     int persistent_blocks;     // grid size of the persistent state-apply kernel
+    // basal terms done by the stored-state kernel after its element groups
+    // (one launch per apply): the Robin term (face, fuse_robin) and the
+    // constraint rows s (I - P) x at the Nb basal nodes (fuse_constraint)
+    int fuse_robin, fuse_constraint;
+    FaceArgs face;
+    int64_t Nb;
+    const int32_t* basal_nodes;
+    const double* basal_P;     // [Nb][6]
+    double cscale;
 };
 
-struct FaceArgs {
-    int64_t nF, Nv;
-    const int32_t* face_elem;  // [nF]
-    const int32_t* nodes;
-    const uint32_t* hang;
-    const int32_t* pidx;
-    const double* pel;
-    const double* fgeo;        // [nF][4][q^2]
-    const int32_t* fmap;       // [nF][n1^2]
-    const double* logbeta;     // [Nb]
-    const void* x;             // vector whose basal trace enters beta T x
-    void* y;                   // output (accumulated)
-    const double* u;           // gradient: state
-    const double* lam;         // gradient: adjoint
-    double* g;                 // gradient output [Nb] (accumulated)
-};
 
 enum FaceMode : int { FACE_APPLY = 0, FACE_GRAD_LOGBETA = 1 };
 

@@ -103,6 +103,9 @@ class State:
     def apply_transpose(self, x, y, stream=None):
         capi.stokes_state_apply_transpose(self.handle, x, y, stream)
 
+    def apply_pressure_block(self, x, y, stream=None):
+        capi.stokes_state_apply_pressure_block(self.handle, x, y, stream)
+
     def close(self):
         if getattr(self, "handle", None) is not None:
             capi.stokes_state_destroy(self.handle)

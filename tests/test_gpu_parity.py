@@ -118,6 +118,26 @@ def test_state_apply(name, prec):
 
 
 @pytest.mark.parametrize("name", CASES)
+@pytest.mark.parametrize("prec", [capi.STOKES_F64, capi.STOKES_F32])
+def test_state_pressure_block(name, prec):
+    """y = J_c (0, x_p): against the oracle Jacobian applied to x with its
+    velocity part zeroed (velocity rows P B^T x_p, pressure rows zero)."""
+    wl, o, m, lb = setup(name)
+    up, x = inputs(o, 17)
+    xp = x.copy()
+    xp[: 3 * o.Nv] = 0.0
+    ref = ostokes.jacobian_apply(o, wl.phys, up, xp, lb)
+    assert np.linalg.norm(ref[3 * o.Nv:]) == 0.0
+    dt = torch.float64 if prec == capi.STOKES_F64 else torch.float32
+    st = State(m, prec)
+    st.linearize(params(wl.phys, dev(lb)), dev(up))
+    y = torch.full((o.ndof,), float("nan"), dtype=dt, device="cuda")
+    st.apply_pressure_block(dev(x, dt), y)
+    tol = TOL64 if prec == capi.STOKES_F64 else TOL32
+    assert_close(o, y.double().cpu().numpy(), ref, tol, f"pressure block prec={prec}")
+
+
+@pytest.mark.parametrize("name", CASES)
 def test_fused_f32(name):
     wl, o, m, lb = setup(name)
     up, x = inputs(o, 14)
