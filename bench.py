@@ -69,6 +69,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-solve", action="store_true",
                     help="skip the time-to-1e-10 Newton solves (FP32-inner vs FP64)")
+    ap.add_argument("--adjoint-check", type=int, default=0, metavar="N",
+                    help="adjoint gradient of a surface misfit and N central-difference directional checks")
     ap.add_argument("--solve-precs", default="fp32_inner,fp64",
                     help="which time-to-1e-10 solves to run (comma list of fp32_inner, fp64)")
     return ap.parse_args()
@@ -154,6 +156,62 @@ def cpu_oracle_rate(wl, seconds=12.0, n_side=8, reps=None):
     text = (f"{sw.nx}x{sw.ny}x{sw.nz} column block of {wl.name} ({om.E} elements, {om.ndof} dofs), "
             f"{n} FP64 oracle Jacobian applies in {dt:.1f} s, numpy single thread")
     return rate, text, n, dt
+
+
+def adjoint_check(args, wl, mesh, rank):
+    """Gradient of J = 1/2 sum_top |u - u_obs|^2 with respect to log(beta) and A
+    by one adjoint solve (FP32-inner solver), checked against central
+    differences of forward Newton solves along seeded smooth directions.
+    u_obs comes from a forward solve at a perturbed log(beta)."""
+    import numpy as np
+    import torch
+    import stokes_synth as synth
+    from paper_1406_6573_gb300 import capi
+    from paper_1406_6573_gb300.adjoint import StokesForward, StokesProblem, misfit, top_nodes
+
+    xyz = mesh.node_coords()
+    bxy = xyz[mesh.basal_nodes(), :2]
+    lb_ref = torch.as_tensor(wl.phys.logbeta(bxy[:, 0], bxy[:, 1]), dtype=torch.float64, device="cuda")
+    prob = StokesProblem(mesh, wl.phys, inner_prec=capi.STOKES_F32, rtol=1e-11, adjoint_rtol=1e-11,
+                         max_krylov=20000, max_newton=80)
+    top = top_nodes(mesh)
+    A = torch.tensor(wl.phys.A, dtype=torch.float64, device="cuda")
+
+    def smooth(seed):   # a few random Fourier modes of the periodic basal plane
+        rng = np.random.default_rng([seed, 77])
+        f = np.zeros(len(bxy))
+        for _ in range(4):
+            kx, ky = rng.integers(1, 4, size=2)
+            ph = rng.uniform(0, 2 * np.pi)
+            f += rng.uniform(-1, 1) * np.cos(2 * np.pi * (kx * bxy[:, 0] / wl.Lx + ky * bxy[:, 1] / wl.Ly) + ph)
+        return torch.as_tensor(f, device="cuda")
+
+    with torch.no_grad():
+        u_obs = StokesForward.apply(lb_ref + 0.3 * smooth(1), A, prob)[: 3 * mesh.Nv].view(-1, 3)[top].clone()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lb = lb_ref.clone().requires_grad_(True)
+    J = misfit(StokesForward.apply(lb, A, prob), u_obs, mesh, top)
+    t_fwd = time.perf_counter() - t0
+    J.backward()
+    torch.cuda.synchronize()
+    t_adj = time.perf_counter() - t0 - t_fwd
+    g = lb.grad.detach()
+    h = 1e-4
+    checks = []
+    for d_i in range(args.adjoint_check):
+        d = smooth(100 + d_i)
+        with torch.no_grad():
+            jp = misfit(StokesForward.apply(lb_ref + h * d, A, prob), u_obs, mesh, top).item()
+            jm = misfit(StokesForward.apply(lb_ref - h * d, A, prob), u_obs, mesh, top).item()
+        fd = (jp - jm) / (2 * h)
+        ad = float((g * d).sum())
+        checks.append(abs(fd - ad) / abs(ad))
+    prob.close()
+    return {"misfit": float(J), "forward_solve_s": round(t_fwd, 3), "adjoint_s": round(t_adj, 3),
+            "grad_norm": float(g.norm()), "directions": args.adjoint_check, "h": h,
+            "fd_rel_diff_max": max(checks), "fd_rel_diff": [float("%.3g" % c) for c in checks],
+            "forward_rtol": 1e-11, "adjoint_rtol": 1e-11}
 
 
 def run_reference(args):
@@ -296,11 +354,26 @@ def run_ours(args):
         Yh = [torch.empty(ndof, dtype=torch.float32).pin_memory() for _ in range(B)]
         Xd = [torch.empty_like(x) for x in X]
         ke = max(1, min(args.steps, 50))
+        # host -> device copies on one copy stream, device -> host on another,
+        # the applies on the compute stream: input b + 1 and output b - 1 move
+        # while apply b runs (the link is full duplex)
+        s_h2d, s_d2h = torch.cuda.Stream(), torch.cuda.Stream()
+        ev_in = [torch.cuda.Event() for _ in range(B)]
+        ev_out = [torch.cuda.Event() for _ in range(B)]
         def e2e_step():
+            s_h2d.wait_stream(stream)          # inputs of the previous step are consumed
             for b in range(B):
-                Xd[b].copy_(Xh[b], non_blocking=True)
+                with torch.cuda.stream(s_h2d):
+                    Xd[b].copy_(Xh[b], non_blocking=True)
+                    ev_in[b].record(s_h2d)
+            for b in range(B):
+                stream.wait_event(ev_in[b])
                 st.apply(Xd[b], Y[b], stream)
-                Yh[b].copy_(Y[b], non_blocking=True)
+                ev_out[b].record(stream)
+                s_d2h.wait_event(ev_out[b])
+                with torch.cuda.stream(s_d2h):
+                    Yh[b].copy_(Y[b], non_blocking=True)
+            stream.wait_stream(s_d2h)          # outputs are on the host before the next step
         e2e_step()
         torch.cuda.synchronize()
         barrier()
@@ -380,6 +453,8 @@ def run_ours(args):
         if "fp32_inner" in solve and "fp64" in solve:
             solve["speedup_fp32_inner"] = round(solve["fp64"]["seconds"] / solve["fp32_inner"]["seconds"], 3)
 
+    adjoint = adjoint_check(args, wl, mesh, rank) if args.adjoint_check > 0 else None
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, text, n, dt = cpu_oracle_rate(wl, args.cpu_seconds)
@@ -413,6 +488,7 @@ def run_ours(args):
             "time_to_1e-10": solve,
             "variants": variants,
             "cpu_baseline": cpu,
+            "adjoint_check": adjoint,
         }
         print(json.dumps(out))
     if world > 1:

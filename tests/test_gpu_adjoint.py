@@ -31,9 +31,12 @@ def _problem(name):
     return wl, o, lb_ref, u_obs, top_o
 
 
+@pytest.mark.parametrize("name", ["cbox_3x3x2_q2p1", "slab_5x3x3_q2p1"])
 @pytest.mark.parametrize("inner", [capi.STOKES_F64, capi.STOKES_F32])
-def test_adjoint_gradient_matches_oracle(inner):
-    wl, o, lb_ref, u_obs, top_o = _problem("cbox_3x3x2_q2p1")
+def test_adjoint_gradient_matches_oracle(name, inner):
+    """cbox: curved box, unit-scale parameters; slab: periodic ice slab in SI
+    units (A = 1e-16, slip + Robin), the physics of the large slab workloads."""
+    wl, o, lb_ref, u_obs, top_o = _problem(name)
     J_o, g_o, gA_o, _ = oadjoint.gradient(o, wl.phys, lb_ref, u_obs, top_o)
     m = Mesh(wl, device=0)
     prob = StokesProblem(m, wl.phys, inner_prec=inner, rtol=1e-11, adjoint_rtol=1e-11)
