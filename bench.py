@@ -38,7 +38,19 @@ STATE_FIELDS = 11
 # DRAM bytes (read + write) of one state_apply_kernel<float> launch, from the
 # ncu capture summarised in profiles/state_apply_f32_slab_128x128x8_q2p1.md;
 # only valid for the kernel source that capture was taken from.
-STATE_APPLY_TRAFFIC = {"slab_128x128x8_q2p1": 214580224 + 12704000}
+STATE_APPLY_TRAFFIC = {}
+
+
+def state_stride(k):
+    """Values per element of the linearised state (the library's layout: 2
+    constants, a one-value shift slot, 11 fields per quadrature point, padded
+    to 16 bytes; for two elements per warp (k = 3) the stride is 16 mod 32)."""
+    n1 = k + 1
+    s = (2 + STATE_FIELDS * n1 ** 3 + 1 + 3) // 4 * 4
+    if 32 // (n1 * n1) == 2:
+        while s % 32 != 16:
+            s += 4
+    return s
 
 
 def workload_label(wl):
@@ -333,7 +345,7 @@ def run_ours(args):
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
     el_launches, el_ms = prof["element"]
     el_avg_s = el_ms / max(el_launches, 1) / 1e3
-    sstride = ((2 + STATE_FIELDS * q3) + 3) // 4 * 4
+    sstride = state_stride(wl.k)
     # element kernel of one apply (it also does the basal Robin term and the
     # constraint rows): state, x read and y written once, element map, hanging
     # code and basal index per element, basal face geometry and map, log(beta),

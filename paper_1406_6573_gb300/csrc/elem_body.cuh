@@ -494,8 +494,8 @@ struct StateApplyCfg {
     static constexpr int SMEM = W * PER_WARP + W * 2 * 8;
 };
 
-// bytes of the state prefix PONLY reads per element (2 + 4 q^3 values, 16-byte multiple)
-template <typename T> constexpr uint32_t STATE_PREFIX_BYTES = ((2 + 4 * Q3) * sizeof(T) + 15) / 16 * 16;
+// bytes of the state prefix PONLY reads per element (2 + shift + 4 q^3 values, 16-byte multiple)
+template <typename T> constexpr uint32_t STATE_PREFIX_BYTES = ((3 + 4 * Q3) * sizeof(T) + 15) / 16 * 16;
 
 // PONLY: the velocity part of x is taken as zero (B^T p only, used by the
 // block preconditioner): no gather, no forward contractions, no pressure rows.
@@ -592,7 +592,7 @@ __global__ void __launch_bounds__(32 * StateApplyCfg<T>::W, StateApplyCfg<T>::MI
         T gq[Q];
         #pragma unroll
         for (int lq = 0; lq < Q; ++lq) {
-            const T* f = st + 2 + sidx(i, j, lq);
+            const T* f = st + 2 + state_shift(es) + sidx(i, j, lq);
             const T g0 = f[0], g1 = f[Q3], g2 = f[2 * Q3];
             const T wdj = f[3 * Q3];
             if constexpr (PONLY) {

@@ -61,9 +61,22 @@ template <typename T> constexpr int LP = LineLen<T>::v;
 template <typename T> constexpr int BUFLEN = LP<T> * N2;
 constexpr int NPRK = (K - 1) * (K - 1) * (K - 1) > K * (K + 1) * (K + 2) / 6
                          ? (K - 1) * (K - 1) * (K - 1) : K * (K + 1) * (K + 2) / 6;
-// per-element stride of the linearised state: 2 element constants then
-// STATE_FIELDS values per quadrature point, padded to a 16-byte multiple
-constexpr int SSTRIDE = ((2 + STATE_FIELDS * Q3) + 3) / 4 * 4;
+// Per-element block of the linearised state: 2 element constants, a shift
+// of STATE_SHIFT(e) values, STATE_FIELDS values per quadrature point, padding
+// to a 16-byte multiple.  The stride and the shift place the q^2 values that
+// the lanes of a warp's EPW elements read together on distinct shared-memory
+// banks once a group of blocks is staged: for EPW = 3 (k = 2) the shift is 1
+// for the first two elements of each group (windows at banks 3, 15 and 26
+// mod 32); for EPW = 2 (k = 3) the stride is 16 mod 32.
+constexpr int STATE_USED = 2 + STATE_FIELDS * Q3;
+constexpr int sstride_calc() {
+    int s = (STATE_USED + 1 + 3) / 4 * 4;
+    if (EPW == 2)
+        while (s % 32 != 16) s += 4;
+    return s;
+}
+constexpr int SSTRIDE = sstride_calc();
+__host__ __device__ constexpr int state_shift(int64_t e) { return (EPW == 3 && e % 3 != 2) ? 1 : 0; }
 
 // ---------------------------------------------------------------- tables
 __constant__ double cB[Q][N1];        // GLL Lagrange at Gauss points
@@ -119,8 +132,11 @@ template <typename T> struct Rows {
     }
 };
 
-// Linearised-state slot s of element e (element-major, [E][SSTRIDE]).
-__device__ __forceinline__ int64_t state_index(int64_t e, int s) { return e * SSTRIDE + s; }
+// Linearised-state slot s of element e (element-major, [E][SSTRIDE]): slots
+// 0, 1 are the element constants, slot 2 + f q^3 + qp field f at qp.
+__device__ __forceinline__ int64_t state_index(int64_t e, int s) {
+    return e * SSTRIDE + (s < 2 ? s : s + state_shift(e));
+}
 
 // --------------------------------------------------------------- helpers
 template <typename T> __device__ __forceinline__ T ld(const T* p) { return __ldg(p); }
@@ -402,7 +418,9 @@ __device__ __forceinline__ void ref_gradient_T(const Rows<T>& R, const T (&S)[NC
 }
 // Shared-memory exchange variants of ref_gradient / ref_gradient_T (used by
 // the stored-state kernel, where they measured faster than the shuffles;
-// the generic element kernel uses the shuffle variants).
+// the generic element kernel uses the shuffle variants).  The idle lanes of a
+// warp (32 mod N1^2) do not store: their slot would share banks with the
+// first element's; what they load is never used.
 // Reference gradients at the Gauss points (iq = i, jq = j, lq) of the NC
 // fields whose nodal columns the thread holds in vin, all fields advancing
 // through each stage together (independent chains between warp syncs):
@@ -413,6 +431,7 @@ __device__ __forceinline__ void ref_gradient_T(const Rows<T>& R, const T (&S)[NC
 template <typename T, int NC, int P = LP<T>>
 __device__ __forceinline__ void ref_gradient_smem(const Rows<T>& R, const T (&vin)[NC][N1], T (&G)[NC][3][Q],
                                              int i, int j, T* buf) {
+    const bool live = (threadIdx.x & 31) < EPW * N2;   // lanes of the warp's elements
     #pragma unroll
     for (int c = 0; c < NC; ++c) {
         T* b0 = buf + (3 * c) * P * N2;
@@ -421,7 +440,7 @@ __device__ __forceinline__ void ref_gradient_smem(const Rows<T>& R, const T (&vi
             T s = 0;
             #pragma unroll
             for (int l = 0; l < N1; ++l) s += Tab<T>::B(lq, l) * vin[c][l];
-            b0[ylp<P>(i, j, lq)] = s;
+            if (live) b0[ylp<P>(i, j, lq)] = s;
         }
     }
     wsync();
@@ -437,8 +456,8 @@ __device__ __forceinline__ void ref_gradient_smem(const Rows<T>& R, const T (&vi
             T si = 0, sd = 0;
             #pragma unroll
             for (int m = 0; m < N1; ++m) { si += R.Bj[m] * ln[m]; sd += R.Tj[m] * ln[m]; }
-            b1[xlp<P>(i, j, lq)] = si;
-            b2[xlp<P>(i, j, lq)] = sd;
+            if (live) b1[xlp<P>(i, j, lq)] = si;
+            if (live) b2[xlp<P>(i, j, lq)] = sd;
         }
     }
     wsync();
@@ -475,6 +494,7 @@ __device__ __forceinline__ void ref_gradient_smem(const Rows<T>& R, const T (&vi
 template <typename T, int NC, bool HAS_VAL, int P = LP<T>>
 __device__ __forceinline__ void ref_gradient_T_smem(const Rows<T>& R, const T (&S)[NC][3][Q], const T (&Sv)[NC][Q],
                                                T (&out)[NC][N1], int i, int j, T* buf) {
+    const bool live = (threadIdx.x & 31) < EPW * N2;   // lanes of the warp's elements
     T t[NC][Q];
     #pragma unroll
     for (int c = 0; c < NC; ++c) {
@@ -482,8 +502,8 @@ __device__ __forceinline__ void ref_gradient_T_smem(const Rows<T>& R, const T (&
         T* b1 = buf + (3 * c + 1) * P * N2;
         #pragma unroll
         for (int lq = 0; lq < Q; ++lq) {
-            b0[xlp<P>(i, j, lq)] = S[c][0][lq];
-            b1[ylp<P>(i, j, lq)] = S[c][1][lq];
+            if (live) b0[xlp<P>(i, j, lq)] = S[c][0][lq];
+            if (live) b1[ylp<P>(i, j, lq)] = S[c][1][lq];
             T s = HAS_VAL ? Sv[c][lq] : T(0);
             #pragma unroll
             for (int m = 0; m < Q; ++m) s += Tab<T>::Dg(m, lq) * S[c][2][m];
@@ -504,7 +524,7 @@ __device__ __forceinline__ void ref_gradient_T_smem(const Rows<T>& R, const T (&
             T s = t[c][lq];
             #pragma unroll
             for (int m = 0; m < Q; ++m) s += R.DTi[m] * lx[m] + R.DTj[m] * ly[m];
-            b2[xlp<P>(i, j, lq)] = s;
+            if (live) b2[xlp<P>(i, j, lq)] = s;
         }
     }
     wsync();
@@ -519,7 +539,7 @@ __device__ __forceinline__ void ref_gradient_T_smem(const Rows<T>& R, const T (&
             T s = 0;
             #pragma unroll
             for (int m = 0; m < Q; ++m) s += R.BTi[m] * ln[m];
-            b0[ylp<P>(i, j, lq)] = s;
+            if (live) b0[ylp<P>(i, j, lq)] = s;
         }
     }
     wsync();
@@ -684,7 +704,7 @@ __device__ void pressure_rows(const T (&gq)[Q], int npr, int ps, int i, int j, i
                 for (int c = 0; c < N1; ++c) if (c == cz) hz = h[c];
                 s = Tab<T>::P1(ps, i, cPm[ps][b][0]) * Tab<T>::P1(ps, j, cPm[ps][b][1]) * hz;
             }
-            sb[cb * N2 + ij] = s;
+            if ((threadIdx.x & 31) < EPW * N2) sb[cb * N2 + ij] = s;   // idle lanes do not store
         }
         wsync();
         if (active && ij < CH && b0 + ij < npr) {
