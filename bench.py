@@ -38,7 +38,7 @@ STATE_FIELDS = 11
 # DRAM bytes (read + write) of one state_apply_kernel<float> launch, from the
 # ncu capture summarised in profiles/state_apply_f32_slab_128x128x8_q2p1.md;
 # only valid for the kernel source that capture was taken from.
-STATE_APPLY_TRAFFIC = {}
+STATE_APPLY_TRAFFIC = {"slab_128x128x8_q2p1": 214632448 + 12453632}
 
 
 def state_stride(k):
@@ -83,6 +83,8 @@ def parse():
                     help="skip the time-to-1e-10 Newton solves (FP32-inner vs FP64)")
     ap.add_argument("--adjoint-check", type=int, default=0, metavar="N",
                     help="adjoint gradient of a surface misfit and N central-difference directional checks")
+    ap.add_argument("--eta-max", type=float, default=0.1,
+                    help="cap of the Eisenstat-Walker forcing term of the time-to-solution runs")
     ap.add_argument("--solve-precs", default="fp32_inner,fp64",
                     help="which time-to-1e-10 solves to run (comma list of fp32_inner, fp64)")
     return ap.parse_args()
@@ -444,7 +446,7 @@ def run_ours(args):
             op.max_krylov = 4000
             op.max_newton = 60
             op.rtol = 1e-10
-            op.eta_max = 0.1
+            op.eta_max = args.eta_max
             sv = capi.stokes_solver_create(mesh.handle, op)
             u0 = torch.zeros(ndof, dtype=torch.float64, device="cuda")
             barrier()
@@ -462,6 +464,7 @@ def run_ours(args):
             elif "fp32_inner" in solve:
                 du = (u0 - u_fp32).norm() / u0.norm()
                 solve["rel_diff_fp32_vs_fp64_solution"] = float(du)
+        solve["eta_max"] = args.eta_max
         if "fp32_inner" in solve and "fp64" in solve:
             solve["speedup_fp32_inner"] = round(solve["fp64"]["seconds"] / solve["fp32_inner"]["seconds"], 3)
 

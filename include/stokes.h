@@ -212,7 +212,9 @@ int stokes_param_grad_A_fixed_order(const stokes_mesh* mesh, const stokes_params
  * stream them instead of recomputing the viscosity. */
 int stokes_state_create(const stokes_mesh* mesh, int prec, stokes_state** out);
 int stokes_state_destroy(stokes_state* state);
-/* up_lin: device FP64 [3Nv+Np]. params is copied into the state. */
+/* up_lin: device FP64 [3Nv+Np]. params is copied into the state; the device
+ * array params->logbeta points to must stay valid while the state is applied
+ * (the copy keeps the pointer, not the values). */
 int stokes_linearize(stokes_state* state, const stokes_params* params,
                      const double* up_lin, void* stream);
 /* y = J_c x from the stored state; x, y of the state's precision. */

@@ -171,6 +171,7 @@ int fgmres_cycle(stokes_solver* S, bool trans, double tol_rel, int max_its, int&
         CU(cudaMemcpyAsync(h.data(), S->dsc, sizeof(double) * (k + 2), cudaMemcpyDeviceToHost, st), "readback");
         CU(cudaStreamSynchronize(st), "sync");
         const double w2 = h[k + 1];
+        if (!std::isfinite(w2)) return fail(STOKES_E_NONFINITE, "non-finite Krylov vector");
         double hh = 0;
         for (int i = 0; i <= k; ++i) { H[size_t(i) * m + k] = h[i]; hh += h[i] * h[i]; }
         double hn2 = w2 - hh;
@@ -186,9 +187,13 @@ int fgmres_cycle(stokes_solver* S, bool trans, double tol_rel, int max_its, int&
             hn2 = std::max(h[k + 1] - hh, 0.0);
             hdev = S->dsc + (m + 1);
         }
-        const double hk1 = std::sqrt(std::max(hn2, 0.0));
-        CU(vec_multiaxpy(n, ip, Vj(k + 1), S->V, S->ld, k + 1, hdev, hk1 > 0 ? 1.0 / hk1 : 1.0, nullptr, st),
-           "orthogonalisation");
+        // breakdown (the new direction lies in the Krylov space up to
+        // rounding): no new basis vector; the cycle ends after this column
+        double hk1 = std::sqrt(std::max(hn2, 0.0));
+        if (!(hk1 > 1e-14 * std::sqrt(w2))) hk1 = 0.0;
+        if (hk1 > 0)
+            CU(vec_multiaxpy(n, ip, Vj(k + 1), S->V, S->ld, k + 1, hdev, 1.0 / hk1, nullptr, st),
+               "orthogonalisation");
         // Givens rotations on column k
         for (int i = 0; i < k; ++i) {
             const double a = H[size_t(i) * m + k], b = H[size_t(i + 1) * m + k];
@@ -197,6 +202,7 @@ int fgmres_cycle(stokes_solver* S, bool trans, double tol_rel, int max_its, int&
         }
         const double a = H[size_t(k) * m + k];
         const double rr = std::hypot(a, hk1);
+        if (!(rr > 0)) break;          // A z_k = 0 here: column k adds nothing (and would not be invertible)
         cs[k] = rr > 0 ? a / rr : 1.0;
         sn[k] = rr > 0 ? hk1 / rr : 0.0;
         H[size_t(k) * m + k] = rr;

@@ -2,6 +2,7 @@
 import ctypes as C
 
 import numpy as np
+import torch
 
 from . import capi
 
@@ -81,7 +82,14 @@ def params(phys, logbeta=None, constraint_scale=None):
     for c in range(3):
         p.body[c] = phys.body[c]
     p.robin = 1 if phys.robin else 0
-    p.logbeta = C.c_void_p(logbeta.data_ptr()) if logbeta is not None else None
+    if logbeta is not None:
+        if not (logbeta.is_cuda and logbeta.dtype == torch.float64 and logbeta.is_contiguous()):
+            raise ValueError("logbeta must be a contiguous CUDA float64 tensor")
+        p.logbeta = C.c_void_p(logbeta.data_ptr())
+    else:
+        p.logbeta = None
+    # the struct holds a raw device pointer: keep the tensor alive with it
+    p._logbeta_tensor = logbeta
     p.constraint_scale = phys.constraint_scale if constraint_scale is None else constraint_scale
     return p
 
@@ -96,6 +104,7 @@ class State:
 
     def linearize(self, p, up_lin, stream=None):
         capi.stokes_linearize(self.handle, p, up_lin, stream)
+        self._params = p     # the state keeps params' device pointers (log beta)
 
     def apply(self, x, y, stream=None):
         capi.stokes_state_apply(self.handle, x, y, stream)
