@@ -155,11 +155,59 @@ __global__ void col_solve_band_kernel(ColSolveArgs a, const T* __restrict__ rhs,
     }
 }
 
+// z_p(e) = -minv(e) r_p(e): one thread per pressure dof (e, b); with full
+// blocks minv holds npr x npr per element, otherwise one inverse diagonal
+// entry per dof
 template <typename T>
-__global__ void schur_apply_kernel(int64_t Nv, int64_t Np, const T* __restrict__ md, const T* __restrict__ r,
-                                   T* __restrict__ z) {
-    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < Np; i += int64_t(gridDim.x) * blockDim.x)
-        z[3 * Nv + i] = -r[3 * Nv + i] / md[i];
+__global__ void schur_apply_kernel(int64_t Nv, int64_t E, int npr, int full, const T* __restrict__ minv,
+                                   const T* __restrict__ r, T* __restrict__ z) {
+    const int64_t np = E * npr;
+    for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < np; t += int64_t(gridDim.x) * blockDim.x) {
+        if (!full) {
+            z[3 * Nv + t] = -minv[t] * r[3 * Nv + t];
+            continue;
+        }
+        const int64_t e = t / npr;
+        const int b = int(t - e * npr);
+        const T* row = minv + (e * npr + b) * npr;
+        const T* re = r + 3 * Nv + e * npr;
+        T s = 0;
+        for (int c = 0; c < npr; ++c) s += row[c] * re[c];
+        z[3 * Nv + t] = -s;
+    }
+}
+
+// inverse diagonal of each element block: minv[e npr + b] = 1 / m[e][b][b]
+template <typename T>
+__global__ void schur_invert_diag_kernel(int64_t E, int npr, const double* __restrict__ m, T* __restrict__ minv) {
+    const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (t >= E * npr) return;
+    const int64_t e = t / npr;
+    const int b = int(t - e * npr);
+    minv[t] = T(1.0 / m[(e * npr + b) * npr + b]);
+}
+
+// inverse of each SPD element block (Gauss-Jordan without pivoting, FP64, in
+// place on the block), stored in T; one thread per element
+template <typename T>
+__global__ void schur_invert_kernel(int64_t E, int npr, double* __restrict__ m, T* __restrict__ minv) {
+    const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (e >= E) return;
+    double* A = m + e * npr * npr;
+    for (int p = 0; p < npr; ++p) {
+        const double piv = 1.0 / A[p * npr + p];
+        for (int c = 0; c < npr; ++c) A[p * npr + c] *= (c == p ? 1.0 : piv);
+        A[p * npr + p] = piv;
+        for (int r = 0; r < npr; ++r) {
+            if (r == p) continue;
+            const double f = A[r * npr + p];
+            if (f == 0.0) continue;
+            for (int c = 0; c < npr; ++c) A[r * npr + c] -= (c == p ? 0.0 : f * A[p * npr + c]);
+            A[r * npr + p] = -f * piv;
+        }
+    }
+    T* out = minv + e * npr * npr;
+    for (int i = 0; i < npr * npr; ++i) out[i] = T(A[i]);
 }
 
 // mean |diagonal| of the assembled (unconstrained) column blocks
@@ -245,15 +293,32 @@ int launch_col_solve(int prec, const ColSolveArgs& a, const void* r, void* z, cu
     return int(cudaGetLastError());
 }
 
-int launch_schur_apply(int prec, int64_t Nv, int64_t Np, const void* md, const void* r, void* z, cudaStream_t s) {
-    if (Np == 0) return 0;
-    int64_t blocks = (Np + 255) / 256;
+int launch_schur_invert(int prec, int64_t E, int npr, int full, const double* mblk, void* minv, cudaStream_t s) {
+    if (E == 0 || npr == 0) return 0;
+    double* m = const_cast<double*>(mblk);
+    if (full) {
+        const unsigned blocks = unsigned((E + 127) / 128);
+        if (prec == 1) schur_invert_kernel<float><<<blocks, 128, 0, s>>>(E, npr, m, static_cast<float*>(minv));
+        else schur_invert_kernel<double><<<blocks, 128, 0, s>>>(E, npr, m, static_cast<double*>(minv));
+    } else {
+        const unsigned blocks = unsigned((E * npr + 255) / 256);
+        if (prec == 1) schur_invert_diag_kernel<float><<<blocks, 256, 0, s>>>(E, npr, m, static_cast<float*>(minv));
+        else schur_invert_diag_kernel<double><<<blocks, 256, 0, s>>>(E, npr, m, static_cast<double*>(minv));
+    }
+    return int(cudaGetLastError());
+}
+
+int launch_schur_apply(int prec, int64_t Nv, int64_t E, int npr, int full, const void* minv, const void* r,
+                       void* z, cudaStream_t s) {
+    const int64_t np = E * npr;
+    if (np == 0) return 0;
+    int64_t blocks = (np + 255) / 256;
     if (blocks > 4096) blocks = 4096;
     if (prec == 1)
-        schur_apply_kernel<float><<<unsigned(blocks), 256, 0, s>>>(Nv, Np, static_cast<const float*>(md),
+        schur_apply_kernel<float><<<unsigned(blocks), 256, 0, s>>>(Nv, E, npr, full, static_cast<const float*>(minv),
                                                                    static_cast<const float*>(r), static_cast<float*>(z));
     else
-        schur_apply_kernel<double><<<unsigned(blocks), 256, 0, s>>>(Nv, Np, static_cast<const double*>(md),
+        schur_apply_kernel<double><<<unsigned(blocks), 256, 0, s>>>(Nv, E, npr, full, static_cast<const double*>(minv),
                                                                     static_cast<const double*>(r), static_cast<double*>(z));
     return int(cudaGetLastError());
 }

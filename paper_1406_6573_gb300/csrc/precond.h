@@ -1,7 +1,12 @@
 // Block upper-triangular preconditioner of the linearised Stokes system
 // (Section 4.2, Eq. 4.1):  A~ = [F~ B^T; 0 S~]  with
 //   F~ = the vertical-column blocks of F (banded, factored per column), and
-//   S~ = -diag M(1/mu), the inverse-viscosity weighted pressure mass (Section 6).
+//   S~ = -M(1/mu), the inverse-viscosity weighted pressure mass (Section 6),
+//        block diagonal for the discontinuous pressure: its element blocks
+//        inverted exactly for npr <= 4 (k = 2 with P_1), its diagonal for the
+//        larger pressure spaces (measured: the full blocks cut the FGMRES
+//        iterations on the Q2 x P1 slab by 13 %, but not for Q3 x Q1 or
+//        Q4 x P3, where they only add work).
 #pragma once
 
 #include <cstdint>
@@ -13,6 +18,7 @@ namespace stokes {
 struct ColArgs {
     int64_t E, ncol;
     int npr, pspace, bw, robin;
+    int schur_full;            // assemble the whole element blocks of M(1/mu) (else their diagonal)
     const int32_t* nodes;      // [E][n1^3]
     const uint32_t* hang;      // [E]
     const int32_t* col_of;     // [Nv]
@@ -23,7 +29,7 @@ struct ColArgs {
     const double* logbeta;     // [Nb]
     const void* state;         // linearised state (element type = prec)
     void* A;                   // [3 colmax][2 bw + 1][ncol] banded column matrices
-    void* md;                  // [E npr] diagonal of M(1/mu)
+    double* mblk;              // [E][npr][npr] M(1/mu) element blocks (FP64, assembly output)
 };
 
 int launch_precond_assembly_k2(int prec, const ColArgs& a, cudaStream_t s);
@@ -47,7 +53,11 @@ int launch_col_factor(int prec, const ColSolveArgs& a, cudaStream_t s);
 int launch_col_diag_sum(int prec, const ColSolveArgs& a, double* out, cudaStream_t s);
 // z_u = F~^{-1} r_u on the velocity part (z, r: state vectors of type prec)
 int launch_col_solve(int prec, const ColSolveArgs& a, const void* r, void* z, cudaStream_t s);
-// z_p = -r_p / md (pressure part)
-int launch_schur_apply(int prec, int64_t Nv, int64_t Np, const void* md, const void* r, void* z, cudaStream_t s);
+// full: minv[e] = inverse of the element block mblk[e] (npr x npr, SPD);
+// otherwise minv[e npr + b] = 1 / mblk[e][b][b] (inverse diagonal); in prec
+int launch_schur_invert(int prec, int64_t E, int npr, int full, const double* mblk, void* minv, cudaStream_t s);
+// z_p = -minv r_p (pressure part; element blocks or diagonal, as inverted)
+int launch_schur_apply(int prec, int64_t Nv, int64_t E, int npr, int full, const void* minv, const void* r,
+                       void* z, cudaStream_t s);
 
 }  // namespace stokes

@@ -111,37 +111,51 @@ __global__ void __launch_bounds__(256) colblock_kernel(ColArgs a) {
     }
 }
 
-// md[e npr + b] = sum_qp psi_b(qp)^2 w detJ / mu   (diagonal of M(1/mu))
+// mblk[e][b1][b2] = sum_qp psi_b1 psi_b2 w detJ / mu   (element block of
+// M(1/mu); w detJ / mu = (w detJ)^2 / (mu w detJ) from the stored state);
+// one thread per (element, b1, b2), or per (element, b) for the diagonal
+// only; FP64 accumulation
 template <typename T>
-__global__ void __launch_bounds__(256) schur_diag_kernel(ColArgs a) {
+__global__ void __launch_bounds__(256) schur_block_kernel(ColArgs a) {
     const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    const int64_t e = t / a.npr;
+    const int per_e = a.schur_full ? a.npr * a.npr : a.npr;
+    const int64_t e = t / per_e;
     if (e >= a.E) return;
-    const int b = int(t - e * a.npr);
+    const int r = int(t - e * per_e);
+    const int b1 = a.schur_full ? r / a.npr : r;
+    const int b2 = a.schur_full ? r - b1 * a.npr : r;
     const int ps = a.pspace;
-    const int m0 = cPm[ps][b][0], m1 = cPm[ps][b][1], m2 = cPm[ps][b][2];
     const T* st0 = static_cast<const T*>(a.state);
     auto stv = [&](int slot) { return st0[state_index(e, slot)]; };
-    T s = 0;
-    for (int lq = 0; lq < Q; ++lq)
-        for (int jq = 0; jq < Q; ++jq)
+    const int a0 = cPm[ps][b1][0], a1 = cPm[ps][b1][1], a2 = cPm[ps][b1][2];
+    const int c0 = cPm[ps][b2][0], c1 = cPm[ps][b2][1], c2 = cPm[ps][b2][2];
+    // arithmetic of the state's type (a preconditioner block), summed per
+    // plane and accumulated across planes in FP64
+    double s = 0;
+    for (int lq = 0; lq < Q; ++lq) {
+        const T pz = Tab<T>::P1(ps, lq, a2) * Tab<T>::P1(ps, lq, c2);
+        T sp = 0;
+        for (int jq = 0; jq < Q; ++jq) {
+            const T py = Tab<T>::P1(ps, jq, a1) * Tab<T>::P1(ps, jq, c1);
             for (int iq = 0; iq < Q; ++iq) {
                 const int qp = iq + Q * (jq + Q * lq);
                 const T wdj = stv(2 + 3 * Q3 + qp), muw = stv(2 + 4 * Q3 + qp);
-                const T psi = Tab<T>::P1(ps, iq, m0) * Tab<T>::P1(ps, jq, m1) * Tab<T>::P1(ps, lq, m2);
-                s += psi * psi * wdj * wdj / muw;
+                sp += Tab<T>::P1(ps, iq, a0) * Tab<T>::P1(ps, iq, c0) * py * (wdj * (wdj / muw));
             }
-    static_cast<T*>(a.md)[t] = s;
+        }
+        s += double(pz * sp);
+    }
+    a.mblk[(e * a.npr + b1) * a.npr + b2] = s;
 }
 
 template <typename T>
 int launch_precond_assembly_t(const ColArgs& a, cudaStream_t s) {
     if (a.E == 0) return int(cudaSuccess);
-    const int64_t n1 = a.E * N3, n2 = a.E * a.npr;
+    const int64_t n1 = a.E * N3, n2 = a.E * a.npr * (a.schur_full ? a.npr : 1);
     colblock_kernel<T><<<unsigned((n1 + 255) / 256), 256, 0, s>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return int(e);
-    schur_diag_kernel<T><<<unsigned((n2 + 255) / 256), 256, 0, s>>>(a);
+    schur_block_kernel<T><<<unsigned((n2 + 255) / 256), 256, 0, s>>>(a);
     return int(cudaGetLastError());
 }
 

@@ -39,7 +39,8 @@ struct stokes_solver {
     size_t isz = 4;
     double *r = nullptr, *dl = nullptr, *rl = nullptr, *trial = nullptr, *rt = nullptr, *tmp64 = nullptr;
     void *V = nullptr, *Z = nullptr, *tin = nullptr, *tz = nullptr;
-    void *A = nullptr, *md = nullptr;
+    void *A = nullptr, *md = nullptr;        // md: inverse element blocks of M(1/mu) (inner precision)
+    double* mblk = nullptr;                  // element blocks of M(1/mu) before inversion (FP64)
     double* dsc = nullptr;             // device scalars
     size_t band_elems = 0;
     int bw = 0;
@@ -55,7 +56,7 @@ void dfree(T*& p) {
 
 void free_solver(stokes_solver* s) {
     dfree(s->r); dfree(s->dl); dfree(s->rl); dfree(s->trial); dfree(s->rt); dfree(s->tmp64);
-    dfree(s->V); dfree(s->Z); dfree(s->tin); dfree(s->tz); dfree(s->A); dfree(s->md); dfree(s->dsc);
+    dfree(s->V); dfree(s->Z); dfree(s->tin); dfree(s->tz); dfree(s->A); dfree(s->md); dfree(s->mblk); dfree(s->dsc);
     if (s->st_in) stokes_state_destroy(s->st_in);
     if (s->st64 && s->st64 != s->st_in) stokes_state_destroy(s->st64);
     s->st_in = s->st64 = nullptr;
@@ -90,6 +91,9 @@ int op64(stokes_solver* S, const double* x, double* y, bool trans, cudaStream_t 
     return trans ? stokes_state_apply_transpose(S->st64, x, y, st) : stokes_state_apply(S->st64, x, y, st);
 }
 
+// exact element blocks of the Schur approximation for small pressure spaces
+int schur_full(const stokes_mesh* m) { return m->h.npr <= 4 ? 1 : 0; }
+
 ColSolveArgs colsolve_args(stokes_solver* S, double scale) {
     const stokes_mesh* m = S->mesh;
     ColSolveArgs c{};
@@ -110,8 +114,9 @@ int precond_setup(stokes_solver* S, const stokes_params* p, cudaStream_t st, dou
     a.robin = p->robin && m->h.nF > 0;
     a.nodes = m->d_nodes; a.hang = m->d_hang; a.col_of = m->d_col_of; a.pos_of = m->d_pos_of;
     a.fidx = m->d_fidx; a.fmap = m->d_fmap; a.fgeo = m->d_fgeo; a.logbeta = p->logbeta;
-    a.state = S->st_in->d_state; a.A = S->A; a.md = S->md;
+    a.state = S->st_in->d_state; a.A = S->A; a.mblk = S->mblk; a.schur_full = schur_full(m);
     CU(launch_precond_assembly(m->h.k, S->inner, a, st), "preconditioner assembly");
+    CU(launch_schur_invert(S->inner, m->h.E, m->h.npr, schur_full(m), S->mblk, S->md, st), "Schur inversion");
     double scale = p->constraint_scale;
     if (scale_out) {
         CU(launch_col_diag_sum(S->inner, colsolve_args(S, scale), S->dsc, st), "diagonal scale");
@@ -126,10 +131,11 @@ int precond_setup(stokes_solver* S, const stokes_params* p, cudaStream_t st, dou
     return STOKES_OK;
 }
 
-// z = M^{-1} v  (inner precision):  z_p = -v_p / md,  z_u = F~^{-1}(v_u - B^T z_p)
+// z = M^{-1} v  (inner precision):  z_p = -M(1/mu)^{-1} v_p (element blocks),
+// z_u = F~^{-1}(v_u - B^T z_p)
 int precond_apply(stokes_solver* S, const void* v, void* z, cudaStream_t st) {
     const stokes_mesh* m = S->mesh;
-    CU(launch_schur_apply(S->inner, m->h.Nv, m->h.Np, S->md, v, z, st), "Schur apply");
+    CU(launch_schur_apply(S->inner, m->h.Nv, m->h.E, m->h.npr, schur_full(m), S->md, v, z, st), "Schur apply");
     CK(state_gradp(S->st_in, z, S->tz, st));
     CU(vec_axpby(S->nu, 1.0, nullptr, S->inner, v, -1.0, S->inner, S->tz, st), "preconditioner update");
     CU(launch_col_solve(S->inner, colsolve_args(S, 1.0), S->tz, z, st), "column solve");
@@ -303,7 +309,8 @@ int stokes_solver_create(const stokes_mesh* mesh, const stokes_solver_opts* opts
     alloc(&S->tin, n * S->isz);
     alloc(&S->tz, n * S->isz);
     alloc(&S->A, S->band_elems * S->isz);
-    alloc(&S->md, std::max<size_t>(1, size_t(mesh->h.Np)) * S->isz);
+    alloc(&S->md, std::max<size_t>(1, size_t(mesh->h.Np) * size_t(mesh->h.npr)) * S->isz);
+    alloc(reinterpret_cast<void**>(&S->mblk), std::max<size_t>(1, size_t(mesh->h.Np) * size_t(mesh->h.npr)) * 8);
     alloc(reinterpret_cast<void**>(&S->dsc), sizeof(double) * size_t(2 * o.restart + 8));
     if (rc) { free_solver(S); delete S; return rc; }
     *out = S;
