@@ -27,8 +27,11 @@ __device__ __forceinline__ T Bd(int iq, int i) {
 //                     + d_c' phi_a d_c phi_b) - (Dhat grad phi_a)_c (Dhat grad phi_b)_c'
 // (the bilinear form of Eq. 2.6 with the tensor of Eq. 2.7), plus the basal
 // Robin block of slot a with itself; accumulated into the banded column
-// matrices.  Hanging slots are skipped (the preconditioner ignores the
-// hanging-node couplings).
+// matrices.  A hanging slot contributes through the node its element map
+// names, the coarse neighbour's node at the same local GLL position (an
+// injective nearest-node stand-in for the interpolation R_i, so every
+// element term stays positive semi-definite); the exact interpolation
+// weights are used by the operator, not by this preconditioner.
 template <typename T>
 __global__ void __launch_bounds__(256) colblock_kernel(ColArgs a) {
     const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -36,9 +39,6 @@ __global__ void __launch_bounds__(256) colblock_kernel(ColArgs a) {
     if (e >= a.E) return;
     const int sl = int(t - e * N3);
     const int i = sl % N1, j = (sl / N1) % N1, l = sl / N2;
-    const uint32_t h = a.hang[e];
-    const int idx[3] = {i, j, l};
-    if (slot_on_hanging_entity(h, idx, K)) return;
     const int64_t na = a.nodes[e * N3 + sl];
     const int col = a.col_of[na], pa = a.pos_of[na];
     const T* st0 = static_cast<const T*>(a.state);
@@ -47,8 +47,6 @@ __global__ void __launch_bounds__(256) colblock_kernel(ColArgs a) {
     const int bw = a.bw, W = 2 * a.bw + 1;
     T* A = static_cast<T*>(a.A);
     for (int l2 = 0; l2 < N1; ++l2) {
-        const int idx2[3] = {i, j, l2};
-        if (slot_on_hanging_entity(h, idx2, K)) continue;
         const int64_t nb = a.nodes[e * N3 + sidx(i, j, l2)];
         if (a.col_of[nb] != col) continue;
         const int pb = a.pos_of[nb];
