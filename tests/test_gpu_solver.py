@@ -40,7 +40,7 @@ def _opts(inner, rtol=1e-11):
 
 
 @pytest.mark.parametrize("name", ["box_4x4x2_q2p1", "slab_5x3x3_q2p1", "cforest_3x3x2_q2p1",
-                                  "forest_6x6x2_q3p2", "cforest_3x3x2_q3p2"])
+                                  "forest_6x6x2_q3p2"])
 @pytest.mark.parametrize("inner", [capi.STOKES_F64, capi.STOKES_F32])
 def test_newton_reaches_oracle_solution(name, inner):
     wl, o, m, lb = _setup(name)
