@@ -116,7 +116,17 @@ typedef struct {
                                      not depend on s.  1 = plain projector;
                                      the solver picks s ~ the diagonal of J so
                                      that FP32 arithmetic resolves these rows. */
+    int linearization;            /* STOKES_LIN_NEWTON: the Newton Jacobian of
+                                     Eqs. 2.6-2.7 (default, 0); STOKES_LIN_PICARD:
+                                     the fixed-viscosity (Picard) operator
+                                     A(u) w = int mu(u) D(v):D(w) - ..., i.e. no
+                                     derivative of mu.  Affects the Jacobian
+                                     applies, stokes_linearize and the solver
+                                     (a Picard iteration); not the residual. */
 } stokes_params;
+
+#define STOKES_LIN_NEWTON 0
+#define STOKES_LIN_PICARD 1
 
 typedef struct {
     int64_t E;        /* elements                                               */

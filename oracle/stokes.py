@@ -152,7 +152,10 @@ def element_jacobian(mesh, phys, ue, we, qe, logbeta):
         Dw = _sym(gw)
         DD = _frob(Du, Du)
         mu = _viscosity(phys, DD)
+        # Newton (Eq. 2.7); the Picard linearisation freezes mu and drops this term
         coef = 2.0 * phys.gamma * pn * _frob(Du, Dw) / (phys.gamma * DD + phys.delta)
+        if phys.linearization == "picard":
+            coef = 0.0 * coef
         stress = mu[..., None, None] * (Dw + coef[..., None, None] * Du)
         pq = np.einsum("qb,eb->eq", mesh.Psi, qe[sl])
         sig = stress - pq[..., None, None] * np.eye(3)
@@ -184,7 +187,8 @@ def residual(mesh, phys, up, logbeta=None):
 
 
 def jacobian_apply(mesh, phys, up, x, logbeta=None):
-    """Constrained Newton Jacobian action  (P J(P u) P + s (I - P)) x."""
+    """Constrained Newton Jacobian action  (P J(P u) P + s (I - P)) x; with
+    phys.linearization == 'picard' the fixed-viscosity operator instead."""
     logbeta = _logbeta(mesh, phys, logbeta)
     u, _ = split(mesh, up)
     w, qv = split(mesh, x)

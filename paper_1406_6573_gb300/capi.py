@@ -45,7 +45,12 @@ class stokes_mesh_desc(C.Structure):
 class stokes_params(C.Structure):
     _fields_ = [("n", C.c_double), ("A", C.c_double), ("C0", C.c_double),
                 ("gamma", C.c_double), ("delta", C.c_double), ("body", C.c_double * 3),
-                ("robin", C.c_int), ("logbeta", C.c_void_p), ("constraint_scale", C.c_double)]
+                ("robin", C.c_int), ("logbeta", C.c_void_p), ("constraint_scale", C.c_double),
+                ("linearization", C.c_int)]
+
+
+STOKES_LIN_NEWTON = 0
+STOKES_LIN_PICARD = 1
 
 
 class stokes_sizes(C.Structure):

@@ -163,6 +163,7 @@ ElemArgs elem_args(const stokes_mesh* m, const stokes_params* p) {
         a.gamma = p->gamma; a.delta = p->delta;
         a.pexp = (1.0 - p->n) / (2.0 * p->n);
         a.n_is_3 = (p->n == 3.0);
+        a.picard = p->linearization == STOKES_LIN_PICARD;
         for (int c = 0; c < 3; ++c) a.body[c] = p->body[c];
     }
     return a;

@@ -139,7 +139,9 @@ __global__ void __launch_bounds__(32 * GW<T>) elem_kernel(ElemArgs a) {
                 const T DD = E00 * E00 + E11 * E11 + E22 * E22 + T(2) * (E01 * E01 + E02 * E02 + E12 * E12);
                 const T mu = viscosity<T>(a, DD);
                 lin[0][lq] = mu * wdj;
-                lin[1][lq] = T(2) * T(a.gamma) * T(a.pexp) * mu * wdj / (T(a.gamma) * DD + T(a.delta));
+                // Picard: the viscosity is frozen at u, no derivative term
+                lin[1][lq] = a.picard ? T(0)
+                                      : T(2) * T(a.gamma) * T(a.pexp) * mu * wdj / (T(a.gamma) * DD + T(a.delta));
                 lin[2][lq] = E00; lin[3][lq] = E11; lin[4][lq] = E22;
                 lin[5][lq] = E01; lin[6][lq] = E02; lin[7][lq] = E12;
             }
@@ -200,7 +202,7 @@ __global__ void __launch_bounds__(32 * GW<T>) elem_kernel(ElemArgs a) {
             const T mu = viscosity<T>(a, DD);
             // -kappa w detJ >= 0 because p_n = (1-n)/(2n) <= 0
             const T mk = -T(2) * T(a.gamma) * T(a.pexp) * mu * wdj / (T(a.gamma) * DD + T(a.delta));
-            const T sq = sqrt(mk > T(0) ? mk : T(0));
+            const T sq = (a.picard || !(mk > T(0))) ? T(0) : sqrt(mk);   // Picard: no rank-one term
             if (active) {
                 auto put = [&](int slot, T v) { st[state_index(e, slot)] = S(v); };
                 if (qp == 0) { put(0, Ji[0]); put(1, Ji[4]); }

@@ -58,6 +58,7 @@ struct ElemArgs {
     const void* cstate;        // same (state apply input)
     double C, gamma, delta, pexp;
     int n_is_3;
+    int picard;                // linearisation: 0 Newton (Eq. 2.7), 1 Picard (viscosity frozen)
     double body[3];
     double* gA;                // gradient output (accumulated)
     double* gA_part;           // per-warp partials, indexed blockIdx.x * warps_per_block + warp

@@ -91,6 +91,7 @@ def params(phys, logbeta=None, constraint_scale=None):
     # the struct holds a raw device pointer: keep the tensor alive with it
     p._logbeta_tensor = logbeta
     p.constraint_scale = phys.constraint_scale if constraint_scale is None else constraint_scale
+    p.linearization = capi.STOKES_LIN_PICARD if phys.linearization == "picard" else capi.STOKES_LIN_NEWTON
     return p
 
 

@@ -30,6 +30,7 @@ class PhysParams:
     robin: bool = True        # basal Robin term  int beta T v . T u
     logbeta: ModalField = None
     constraint_scale: float = 1.0   # s of the constraint rows s (I - P)
+    linearization: str = "newton"   # Jacobian: 'newton' (Eq. 2.7) or 'picard' (viscosity frozen)
 
     def viscosity_prefactor(self):
         return self.C0 * self.A ** (-1.0 / self.n)

@@ -201,3 +201,47 @@ def test_empty_hanging_free_paths_agree():
     capi.stokes_jacobian_apply(a.handle, p, dev(up), dev(x), ya, capi.STOKES_F64)
     capi.stokes_jacobian_apply(b.handle, p, dev(up), dev(x), yb, capi.STOKES_F64)
     assert torch.allclose(ya, yb, rtol=1e-13, atol=0)
+
+
+@pytest.mark.parametrize("name", ["box_4x4x2_q2p1", "slab_8x8x2_q2p1", "forest_6x6x2_q3p2", "slab_4x4x2_q4p3"])
+@pytest.mark.parametrize("prec", [capi.STOKES_F64, capi.STOKES_F32])
+def test_picard_operators(name, prec):
+    """Picard (fixed-viscosity) linearisation: stored-state and fused applies
+    against the oracle's Picard operator."""
+    import dataclasses
+    wl, o, m, lb = setup(name)
+    phys = dataclasses.replace(wl.phys, linearization="picard")
+    up, x = inputs(o, 23)
+    ref = ostokes.jacobian_apply(o, phys, up, x, lb)
+    dt = torch.float64 if prec == capi.STOKES_F64 else torch.float32
+    tol = TOL64 if prec == capi.STOKES_F64 else TOL32
+    lbd = dev(lb)
+    p = params(phys, lbd)
+    st = State(m, prec)
+    st.linearize(p, dev(up))
+    y = torch.empty(o.ndof, dtype=dt, device="cuda")
+    st.apply(dev(x, dt), y)
+    assert_close(o, y.double().cpu().numpy(), ref, tol, f"picard state apply prec={prec}")
+    yf = torch.empty(o.ndof, dtype=dt, device="cuda")
+    capi.stokes_jacobian_apply(m.handle, p, dev(up, dt), dev(x, dt), yf, prec)
+    assert_close(o, yf.double().cpu().numpy(), ref, tol, f"picard fused apply prec={prec}")
+
+
+def test_picard_identity_on_the_gpu():
+    """J_Picard(u) u - r_c(u) = -r_c(0) with the GPU operators (FP64)."""
+    import dataclasses
+    wl, o, m, lb = setup("cforest_3x3x2_q3p2")
+    phys = dataclasses.replace(wl.phys, linearization="picard")
+    up = synth.uniform_vector(9, o.ndof)
+    up[: 3 * o.Nv] *= 50.0
+    lbd = dev(lb)
+    p = params(phys, lbd)
+    u = dev(up)
+    ju = torch.empty_like(u)
+    capi.stokes_jacobian_apply(m.handle, p, u, u, ju, capi.STOKES_F64)
+    r = torch.empty_like(u)
+    capi.stokes_residual(m.handle, p, u, r, capi.STOKES_F64)
+    r0 = torch.empty_like(u)
+    capi.stokes_residual(m.handle, p, torch.zeros_like(u), r0, capi.STOKES_F64)
+    err = float((ju - r + r0).norm())
+    assert err <= 1e-12 * float(r.norm()), err / float(r.norm())

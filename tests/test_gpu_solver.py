@@ -144,3 +144,27 @@ def test_nonfinite_inputs_are_reported():
         assert rc == -5
     finally:
         capi.stokes_solver_destroy(s)
+
+
+@pytest.mark.parametrize("inner", [capi.STOKES_F64, capi.STOKES_F32])
+def test_picard_iteration_reaches_oracle_solution(inner):
+    """The solver with the Picard linearisation (a fixed-point iteration on
+    the frozen viscosity) reaches the same discrete solution, in more steps
+    than Newton."""
+    wl, o, m, lb = _setup("box_4x4x2_q2p1")
+    phys = dataclasses.replace(wl.phys, linearization="picard")
+    lbd = torch.as_tensor(lb, dtype=torch.float64, device="cuda")
+    p = params(phys, lbd)
+    op = _opts(inner, rtol=1e-9)
+    op.max_newton = 200
+    s = capi.stokes_solver_create(m.handle, op)
+    try:
+        up = torch.zeros(o.ndof, dtype=torch.float64, device="cuda")
+        rc, rep = capi.stokes_newton_solve(s, p, up, check=False)
+        assert rc == 0 and rep["converged"], (rc, rep)
+        assert rep["newton_its"] > 10, rep
+        r0 = np.linalg.norm(ostokes.residual(o, wl.phys, np.zeros(o.ndof), lb))
+        r = np.linalg.norm(ostokes.residual(o, wl.phys, up.cpu().numpy(), lb))
+        assert r <= 1e-9 * r0, r / r0
+    finally:
+        capi.stokes_solver_destroy(s)
