@@ -35,10 +35,10 @@ UNIT = "MDoF/s"
 STATE_FIELDS = 11
 
 
-# DRAM bytes (read + write) of one state_apply_kernel<float> launch, from the
-# ncu capture summarised in profiles/state_apply_f32_slab_128x128x8_q2p1.md;
-# only valid for the kernel source that capture was taken from.
-STATE_APPLY_TRAFFIC = {"slab_128x128x8_q2p1": 214632448 + 12453632}
+# DRAM bytes (read + write) of one launch of the stored-state apply kernel,
+# from the ncu capture summarised under profiles/ for that workload; only
+# valid for the kernel source that capture was taken from.
+STATE_APPLY_TRAFFIC = {}
 
 
 def state_stride(k):
@@ -350,14 +350,18 @@ def run_ours(args):
     el_avg_s = el_ms / max(el_launches, 1) / 1e3
     sstride = state_stride(wl.k)
     # element kernel of one apply (it also does the basal Robin term and the
-    # constraint rows): state, x read and y written once, element map, hanging
-    # code and basal index per element, basal face geometry and map, log(beta),
-    # basal node list and projector
+    # constraint rows): state, x read and y written once, basal index per
+    # element, element map and hanging code where the kernel reads them (not
+    # on conforming lattice meshes, whose nodes follow from the element
+    # index), basal face geometry and map, log(beta), basal node list and
+    # projector
     mask = wl.refine_mask().reshape(wl.nz, wl.ny, wl.nx)[0]
+    refined = bool(wl.refine_mask().any())
     n_faces = int(wl.nx * wl.ny + 3 * mask.sum())
     q2 = (wl.k + 1) ** 2
     bytes_basal = (n_faces * (4 * q2 * 8 + q2 * 4) + mesh.Nb * (8 + 4 + 48)) if wl.phys.robin else mesh.Nb * 52
-    bytes_alg = (mesh.E * sstride * 4 + 2 * ndof * 4 + mesh.E * n3 * 4 + mesh.E * 8 + bytes_basal)
+    bytes_desc = mesh.E * 4 + (mesh.E * (n3 * 4 + 4) if refined else 0)
+    bytes_alg = mesh.E * sstride * 4 + 2 * ndof * 4 + bytes_desc + bytes_basal
     achieved = bytes_alg / el_avg_s / 1e9
     shares = {k: v[1] for k, v in prof.items()}
     tot = sum(shares.values())
@@ -500,7 +504,8 @@ def run_ours(args):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                          "frac": achieved / hbm_peak,
                          "traffic": STATE_APPLY_TRAFFIC.get(wl.name),
-                         "kernel": "state_apply_kernel<float>",
+                         "kernel": ("cpl_state_apply_kernel<%d,false>" % (0 if wl.pspace == "P" else 1)
+                                    if (wl.k == 2 and not refined) else "state_apply_kernel<float,false>"),
                          "bytes_per_launch": bytes_alg, "avg_launch_ms": el_avg_s * 1e3,
                          "peak_source": f"{peak_src} hbm_gbs"},
             "kernel_time_share": {k: round(v / tot, 4) for k, v in shares.items()} if tot > 0 else {},

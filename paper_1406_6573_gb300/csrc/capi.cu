@@ -183,11 +183,13 @@ size_t vec_bytes(const stokes_mesh* m, int prec) {
 }
 
 int operator_sequence(const stokes_mesh* m, const stokes_params* p, int mode, int prec, int state_prec,
-                      bool trans, const void* x, const void* u, const void* cstate, void* y, cudaStream_t s) {
+                      bool trans, const void* x, const void* u, const void* cstate, void* y, cudaStream_t s,
+                      int state_cpl) {
     int e = timed(m, 0, s, [&] { return int(cudaMemsetAsync(y, 0, vec_bytes(m, prec), s)); });
     if (e) return cuda_fail(cudaError_t(e), "clearing the output");
     ElemArgs a = elem_args(m, p);
     a.x = x; a.y = y; a.u = u; a.cstate = cstate;
+    a.state_cpl = state_cpl;
     const bool robin = p->robin && m->h.nF > 0;
     if (mode == MODE_STATE_APPLY) {
         // the stored-state kernel also does the basal Robin term and the
@@ -218,7 +220,7 @@ int operator_sequence(const stokes_mesh* m, const stokes_params* p, int mode, in
 
 int state_gradp(const stokes_state* st, const void* x, void* y, cudaStream_t s) {
     return operator_sequence(st->mesh, &st->params, MODE_STATE_GRADP, st->prec, st->prec, false, x, nullptr,
-                             st->d_state, y, s);
+                             st->d_state, y, s, st->cpl);
 }
 
 }  // namespace stokes
@@ -434,10 +436,21 @@ int stokes_state_create(const stokes_mesh* mesh, int prec, stokes_state** out) {
     st->prec = prec;
     DeviceGuard g(mesh->device);
     if (g.err != cudaSuccess) { delete st; return cuda_fail(g.err, "selecting the device"); }
-    const size_t bytes = size_t(mesh->h.E) * size_t(state_stride(mesh->h.k)) * (prec == STOKES_F32 ? 4 : 8);
+    // FP32 states of conforming k = 2 meshes use the group layout of the
+    // component-per-lane apply kernel
+    st->cpl = (STOKES_CPL && prec == STOKES_F32 && mesh->h.k == 2 && mesh->h.n_hang == 0) ? 1 : 0;
+    const size_t values = st->cpl ? size_t((mesh->h.E + CPL_GROUP_ELEMS - 1) / CPL_GROUP_ELEMS) * CPL_GROUP_VALUES
+                                  : size_t(mesh->h.E) * size_t(state_stride(mesh->h.k));
+    const size_t bytes = values * (prec == STOKES_F32 ? 4 : 8);
     if (cudaMalloc(&st->d_state, bytes) != cudaSuccess) {
         delete st;
         return fail(STOKES_E_NOMEM, "cudaMalloc of the linearised state failed");
+    }
+    // padding slots of the last group are read (never used) by the apply
+    if (cudaMemset(st->d_state, 0, bytes) != cudaSuccess) {
+        cudaFree(st->d_state);
+        delete st;
+        return fail(STOKES_E_CUDA, "clearing the linearised state failed");
     }
     *out = st;
     return STOKES_OK;
@@ -463,6 +476,7 @@ int stokes_linearize(stokes_state* state, const stokes_params* params, const dou
     ElemArgs a = elem_args(mesh, params);
     a.ud = up_lin;
     a.state = state->d_state;
+    a.state_cpl = state->cpl;
     int e = launch_elem(mesh->h.k, MODE_LINEARIZE, STOKES_F64, state->prec, false, a,
                         static_cast<cudaStream_t>(stream));
     if (e) return cuda_fail(cudaError_t(e), "linearize kernel launch");
@@ -483,7 +497,7 @@ static int state_apply_common(const stokes_state* state, const void* x, void* y,
     DeviceGuard g(mesh->device);
     if (g.err != cudaSuccess) return cuda_fail(g.err, "selecting the device");
     return operator_sequence(mesh, &state->params, mode, state->prec, state->prec, trans, x,
-                             nullptr, state->d_state, y, static_cast<cudaStream_t>(stream));
+                             nullptr, state->d_state, y, static_cast<cudaStream_t>(stream), state->cpl);
 }
 
 int stokes_state_apply(const stokes_state* state, const void* x, void* y, void* stream) {

@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(32 * GW<T>) elem_kernel(ElemArgs a) {
             const T mk = -T(2) * T(a.gamma) * T(a.pexp) * mu * wdj / (T(a.gamma) * DD + T(a.delta));
             const T sq = (a.picard || !(mk > T(0))) ? T(0) : sqrt(mk);   // Picard: no rank-one term
             if (active) {
-                auto put = [&](int slot, T v) { st[state_index(e, slot)] = S(v); };
+                auto put = [&](int slot, T v) { st[state_index(e, slot, a.state_cpl)] = S(v); };
                 if (qp == 0) { put(0, Ji[0]); put(1, Ji[4]); }
                 put(2 + 0 * Q3 + qp, Ji[6]);
                 put(2 + 1 * Q3 + qp, Ji[7]);
@@ -478,6 +478,11 @@ constexpr bool STATE_SHFL = K >= STOKES_STATE_SHFL_MIN_K;
 #endif
 template <typename T> constexpr int STATE_PITCH = STOKES_STATE_PACKED ? N1 : LP<T>;
 template <typename T> constexpr int STATE_SLOT = STOKES_STATE_PACKED ? SLOT_PACKED<T> : SLOT<T>;
+// latency of the next group's gather hidden behind the current group:
+// 0 none, 1 L1 prefetch of the node lines (conforming lattice meshes)
+#ifndef STOKES_STATE_PREFETCH
+#define STOKES_STATE_PREFETCH 1
+#endif
 // y = J x from the stored linearised state.  Persistent: each warp walks its
 // element groups (EPW consecutive elements); the state block of the next
 // group (contiguous, 16-byte multiple) is staged into shared memory by a bulk
@@ -510,7 +515,10 @@ __global__ void __launch_bounds__(32 * StateApplyCfg<T>::W, StateApplyCfg<T>::MI
     const LaneMap L;
     const int i = L.i, j = L.j, ij = L.ij, es = L.es, lane = L.lane;
     unsigned char* wbase = smem_raw + L.warp * C::PER_WARP;
-    T* stage[2] = {reinterpret_cast<T*>(wbase), reinterpret_cast<T*>(wbase) + C::BUF};
+    // stage buffer b of this warp (computed, not an indexed pointer array,
+    // which would live in local memory)
+    T* const stage0 = reinterpret_cast<T*>(wbase);
+    auto stage = [&](int b) { return stage0 + b * C::BUF; };
     T* scratch = reinterpret_cast<T*>(wbase) + 2 * C::BUF;
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + C::W * C::PER_WARP) + 2 * L.warp;
     T* sb = scratch + es * STATE_SLOT<T>;
@@ -536,11 +544,11 @@ __global__ void __launch_bounds__(32 * StateApplyCfg<T>::W, StateApplyCfg<T>::MI
         if constexpr (PONLY) {
             mbar_arrive_expect_tx(&bar[b], uint32_t(ne) * PREFIX_BYTES);
             for (int ee = 0; ee < ne; ++ee)
-                bulk_g2s(stage[b] + ee * SSTRIDE, S + (gg * EPW + ee) * SSTRIDE, PREFIX_BYTES, &bar[b]);
+                bulk_g2s(stage(b) + ee * SSTRIDE, S + (gg * EPW + ee) * SSTRIDE, PREFIX_BYTES, &bar[b]);
         } else {
             const uint32_t nb = uint32_t(ne * SSTRIDE * int64_t(sizeof(T)));
             mbar_arrive_expect_tx(&bar[b], nb);
-            bulk_g2s(stage[b], S + gg * EPW * SSTRIDE, nb, &bar[b]);
+            bulk_g2s(stage(b), S + gg * EPW * SSTRIDE, nb, &bar[b]);
         }
     };
     if (lane == 0) {
@@ -562,8 +570,26 @@ __global__ void __launch_bounds__(32 * StateApplyCfg<T>::W, StateApplyCfg<T>::MI
         const bool active = (es < EPW) && (e < a.E);
         ColNodes cn;
         col_nodes(a, e, ij, active, cn);
-        const uint32_t h = active ? a.hang[e] : 0u;
+        const uint32_t h = (active && a.any_hang) ? a.hang[e] : 0u;
         const bool any_h = a.any_hang ? (__any_sync(0xffffffffu, (h & ((1u << HANG_CHILD0) - 1)) != 0) != 0) : false;
+#if STOKES_STATE_PREFETCH == 1
+        {
+            // the next group's node lines, pressure block and projector index
+            const int64_t en = (g + gstride) * EPW + es;
+            if (es < EPW && en < a.E) {
+                if (!PONLY && a.lat_nx > 0) {
+                    ColNodes cnn;
+                    col_nodes(a, en, ij, true, cnn);
+                    #pragma unroll
+                    for (int l = 0; l < N1; ++l) prefetch_l1(x + 3 * int64_t(cnn.g[l]));
+                }
+                if (ij == 0) {
+                    prefetch_l1(x + 3 * a.Nv + en * a.npr);
+                    prefetch_l1(a.pidx + en);
+                }
+            }
+        }
+#endif
 
         T pc[N1];
         pressure_fold<T, T>(a, x, e, active, i, j, pc);
@@ -589,7 +615,7 @@ __global__ void __launch_bounds__(32 * StateApplyCfg<T>::W, StateApplyCfg<T>::MI
             mbar_wait_bounded(&bar[buf], uint32_t((it >> 1) & 1));
             return;
         }
-        const T* st = stage[buf] + (es < EPW ? es : 0) * SSTRIDE;
+        const T* st = stage(buf) + (es < EPW ? es : 0) * SSTRIDE;
         const T ia = st[0], ib = st[1];
         T gq[Q];
         #pragma unroll
@@ -722,6 +748,16 @@ int launch_face_t(const FaceArgs& a, cudaStream_t s) {
     return int(cudaGetLastError());
 }
 
+}  // namespace STOKES_NS
+}  // namespace dev
+}  // namespace stokes
+
+#include "cpl_apply.cuh"
+
+namespace stokes {
+namespace dev {
+namespace STOKES_NS {
+
 inline int launch_elem_any(int mode, int prec, int state_prec, bool trans, const ElemArgs& a, cudaStream_t s) {
     const bool f32 = prec == 1;
     switch (mode) {
@@ -737,11 +773,20 @@ inline int launch_elem_any(int mode, int prec, int state_prec, bool trans, const
             return state_prec == 1 ? launch_elem_t<double, float, MODE_LINEARIZE, false>(a, s)
                                    : launch_elem_t<double, double, MODE_LINEARIZE, false>(a, s);
         case MODE_STATE_APPLY:
+        case MODE_STATE_GRADP:
             // the pointwise map of Eq. 2.7 is symmetric: the transposed apply
             // runs the same kernel
+            if (a.state_cpl) {
+#if STOKES_K == 2
+                if (!f32) return int(cudaErrorInvalidValue);
+                return launch_cpl(a, mode == MODE_STATE_GRADP, s);
+#else
+                return int(cudaErrorInvalidValue);
+#endif
+            }
+            if (mode == MODE_STATE_GRADP)
+                return f32 ? launch_state_apply_t<float, true>(a, s) : launch_state_apply_t<double, true>(a, s);
             return f32 ? launch_state_apply_t<float, false>(a, s) : launch_state_apply_t<double, false>(a, s);
-        case MODE_STATE_GRADP:
-            return f32 ? launch_state_apply_t<float, true>(a, s) : launch_state_apply_t<double, true>(a, s);
         case MODE_GRAD_A:
             return launch_elem_t<double, double, MODE_GRAD_A, false>(a, s);
         case MODE_GRAD_A_PARTIAL:
@@ -797,6 +842,19 @@ inline int upload_tables_any(const void* p) {
     if (e == cudaSuccess) e = cudaMemcpyToSymbol(fP1, fp, sizeof(fp));
     if (e == cudaSuccess) e = cudaMemcpyToSymbol(cBd, Bdv, sizeof(Bdv));
     if (e == cudaSuccess) e = cudaMemcpyToSymbol(fBd, fbd, sizeof(fbd));
+#if STOKES_K == 2
+    {
+        float psi[2][NPRK][Q3] = {};
+        for (int sp = 0; sp < 2; ++sp)
+            for (int m = 0; m < t[sp].npr && m < NPRK; ++m)
+                for (int l = 0; l < Q; ++l)
+                    for (int jj = 0; jj < Q; ++jj)
+                        for (int ii = 0; ii < Q; ++ii)
+                            psi[sp][m][ii + Q * (jj + Q * l)] =
+                                float(P1[sp][ii][pm[sp][m][0]] * P1[sp][jj][pm[sp][m][1]] * P1[sp][l][pm[sp][m][2]]);
+        if (e == cudaSuccess) e = cudaMemcpyToSymbol(fPsi, psi, sizeof(psi));
+    }
+#endif
     return int(e);
 }
 

@@ -91,6 +91,10 @@ __constant__ float fI[2][N1][N1];
 __constant__ float fP1[2][Q][N1];
 __constant__ double cBd[Q][N1];       // (Dg B)[iq][i]: derivative of GLL Lagrange i at Gauss point iq
 __constant__ float fBd[Q][N1];
+#if STOKES_K == 2
+// pressure basis at the Gauss points, psi_b(qp) [pspace][mode][qp]
+__constant__ float fPsi[2][NPRK][Q3];
+#endif
 
 template <typename T> struct Tab;
 template <> struct Tab<double> {
@@ -132,9 +136,31 @@ template <typename T> struct Rows {
     }
 };
 
-// Linearised-state slot s of element e (element-major, [E][SSTRIDE]): slots
-// 0, 1 are the element constants, slot 2 + f q^3 + qp field f at qp.
-__device__ __forceinline__ int64_t state_index(int64_t e, int s) {
+// Group layout of the FP32 state of conforming k = 2 meshes (read by the
+// component-per-lane apply): groups of CPL_E consecutive elements, each a
+// header (the 2 element constants of the group's elements, padded) and one
+// block per Gauss plane lq holding, field by field, the 9 points of the plane
+// for the CPL_E elements ([f][q9][element], plane padded to a 16-byte
+// multiple).  A group is one contiguous 16-byte-multiple block.
+constexpr int CPL_E = 10;
+constexpr int CPL_HDR = 24;
+constexpr int CPL_FS = N2 * CPL_E;                                 // values per field and plane
+constexpr int CPL_PL = (STATE_FIELDS * CPL_FS + 3) / 4 * 4;       // values per plane
+constexpr int CPL_GROUP = CPL_HDR + N1 * CPL_PL;                   // values per group
+static_assert(K != 2 || (CPL_E == CPL_GROUP_ELEMS && CPL_GROUP == CPL_GROUP_VALUES), "group layout of k = 2");
+
+// Linearised-state slot s of element e: slots 0, 1 are the element
+// constants, slot 2 + f q^3 + qp field f at qp.  Element-major [E][SSTRIDE]
+// layout, or the group layout above (cpl != 0).
+__device__ __forceinline__ int64_t state_index(int64_t e, int s, int cpl) {
+    if (cpl) {
+        const int64_t gg = e / CPL_E;
+        const int el = int(e - gg * CPL_E);
+        if (s < 2) return gg * CPL_GROUP + s * CPL_E + el;
+        const int f = (s - 2) / Q3, qp = (s - 2) - f * Q3;
+        const int lq = qp / N2, q9 = qp - lq * N2;
+        return gg * CPL_GROUP + CPL_HDR + lq * CPL_PL + f * CPL_FS + q9 * CPL_E + el;
+    }
     return e * SSTRIDE + (s < 2 ? s : s + state_shift(e));
 }
 

@@ -84,6 +84,7 @@ struct stokes_state {
     const stokes_mesh* mesh = nullptr;
     int prec = 0;
     void* d_state = nullptr;
+    int cpl = 0;               // group layout, applied by the component-per-lane kernel
     stokes_params params{};
     bool linearized = false;
 };
@@ -97,7 +98,8 @@ FaceArgs face_args(const stokes_mesh* m, const stokes_params* p);
 size_t vec_bytes(const stokes_mesh* m, int prec);
 // y = (element terms of x) + Robin(x) + (I - P) x ; mode selects the element term
 int operator_sequence(const stokes_mesh* m, const stokes_params* p, int mode, int prec, int state_prec,
-                      bool trans, const void* x, const void* u, const void* cstate, void* y, cudaStream_t s);
+                      bool trans, const void* x, const void* u, const void* cstate, void* y, cudaStream_t s,
+                      int state_cpl = 0);
 // velocity part of y = B^T p  for the pressure part of x (from the stored state)
 int state_gradp(const stokes_state* st, const void* x, void* y, cudaStream_t s);
 

@@ -24,6 +24,16 @@ enum ElemMode : int {
 // Dhat (6: 00 11 22 01 02 12).
 constexpr int STATE_FIELDS = 11;
 
+// FP32 states of conforming k = 2 meshes are stored in groups of 10 elements
+// (3000 values per group, 12000 bytes) and applied by the component-per-lane
+// kernel; STOKES_CPL = 0 keeps them in the element-major layout of the
+// warp-per-element-group kernel.
+#ifndef STOKES_CPL
+#define STOKES_CPL 1
+#endif
+constexpr int CPL_GROUP_ELEMS = 10;
+constexpr int CPL_GROUP_VALUES = 3000;
+
 struct FaceArgs {
     int64_t nF, Nv;
     const int32_t* face_elem;  // [nF]
@@ -56,6 +66,7 @@ struct ElemArgs {
     const double* lam;         // FP64 adjoint (gradient)
     void* state;               // [E][state stride] (linearize output)
     const void* cstate;        // same (state apply input)
+    int state_cpl;             // state in the group layout (k = 2, FP32, conforming mesh)
     double C, gamma, delta, pexp;
     int n_is_3;
     int picard;                // linearisation: 0 Newton (Eq. 2.7), 1 Picard (viscosity frozen)

@@ -28,6 +28,7 @@ struct ColArgs {
     const double* fgeo;        // [nF][4][q^2]
     const double* logbeta;     // [Nb]
     const void* state;         // linearised state (element type = prec)
+    int state_cpl;             // the state is in the group layout of k = 2 FP32 states
     void* A;                   // [3 colmax][2 bw + 1][ncol] banded column matrices
     double* mblk;              // [E][npr][npr] M(1/mu) element blocks (FP64, assembly output)
 };

@@ -42,7 +42,7 @@ __global__ void __launch_bounds__(256) colblock_kernel(ColArgs a) {
     const int64_t na = a.nodes[e * N3 + sl];
     const int col = a.col_of[na], pa = a.pos_of[na];
     const T* st0 = static_cast<const T*>(a.state);
-    auto stv = [&](int slot) { return st0[state_index(e, slot)]; };
+    auto stv = [&](int slot) { return st0[state_index(e, slot, a.state_cpl)]; };
     const T ia = stv(0), ib = stv(1);
     const int bw = a.bw, W = 2 * a.bw + 1;
     T* A = static_cast<T*>(a.A);
@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(256) schur_block_kernel(ColArgs a) {
     const int b2 = a.schur_full ? r - b1 * a.npr : r;
     const int ps = a.pspace;
     const T* st0 = static_cast<const T*>(a.state);
-    auto stv = [&](int slot) { return st0[state_index(e, slot)]; };
+    auto stv = [&](int slot) { return st0[state_index(e, slot, a.state_cpl)]; };
     const int a0 = cPm[ps][b1][0], a1 = cPm[ps][b1][1], a2 = cPm[ps][b1][2];
     const int c0 = cPm[ps][b2][0], c1 = cPm[ps][b2][1], c2 = cPm[ps][b2][2];
     // arithmetic of the state's type (a preconditioner block), summed per

@@ -114,7 +114,7 @@ int precond_setup(stokes_solver* S, const stokes_params* p, cudaStream_t st, dou
     a.robin = p->robin && m->h.nF > 0;
     a.nodes = m->d_nodes; a.hang = m->d_hang; a.col_of = m->d_col_of; a.pos_of = m->d_pos_of;
     a.fidx = m->d_fidx; a.fmap = m->d_fmap; a.fgeo = m->d_fgeo; a.logbeta = p->logbeta;
-    a.state = S->st_in->d_state; a.A = S->A; a.mblk = S->mblk; a.schur_full = schur_full(m);
+    a.state = S->st_in->d_state; a.state_cpl = S->st_in->cpl; a.A = S->A; a.mblk = S->mblk; a.schur_full = schur_full(m);
     CU(launch_precond_assembly(m->h.k, S->inner, a, st), "preconditioner assembly");
     CU(launch_schur_invert(S->inner, m->h.E, m->h.npr, schur_full(m), S->mblk, S->md, st), "Schur inversion");
     double scale = p->constraint_scale;
