@@ -67,7 +67,7 @@ int timed(const stokes_mesh* m, int c, cudaStream_t s, F&& launch) {
 void free_mesh_device(stokes_mesh* m) {
     for (cudaEvent_t ev : m->prof.pool) cudaEventDestroy(ev);
     m->prof.pool.clear();
-    void* ptrs[] = {m->d_nodes, m->d_hang, m->d_geo, m->d_pidx, m->d_pel, m->d_face_elem, m->d_fidx,
+    void* ptrs[] = {m->d_nodes, m->d_hang, m->d_geo, m->d_pidx, m->d_pel, m->d_pel_f, m->d_face_elem, m->d_fidx,
                     m->d_fgeo, m->d_fmap, m->d_basal_nodes, m->d_basal_P, m->d_err, m->d_col_of,
                     m->d_pos_of, m->d_col_nodes, m->d_col_len, m->d_col_basal};
     for (void* p : ptrs) if (p) cudaFree(p);
@@ -154,6 +154,7 @@ ElemArgs elem_args(const stokes_mesh* m, const stokes_params* p) {
     a.E = m->h.E; a.Nv = m->h.Nv; a.npr = m->h.npr; a.pspace = m->h.pspace;
     a.any_hang = m->h.n_hang > 0;
     a.nodes = m->d_nodes; a.hang = m->d_hang; a.geo = m->d_geo; a.pidx = m->d_pidx; a.pel = m->d_pel;
+    a.pel_f = m->d_pel_f;
     a.err = m->d_err;
     if (m->h.lattice) {
         a.lat_nx = m->h.nx; a.lat_ny = m->h.ny; a.lat_NX = m->h.latNX; a.lat_NY = m->h.latNY;
@@ -256,6 +257,7 @@ int stokes_mesh_create(const stokes_mesh_desc* desc, stokes_mesh** out) {
         if (rc == STOKES_OK) rc = upload(&m->d_geo, m->h.geo);
         if (rc == STOKES_OK) rc = upload(&m->d_pidx, m->h.elem_pidx);
         if (rc == STOKES_OK) rc = upload(&m->d_pel, m->h.pel);
+        if (rc == STOKES_OK) rc = upload(&m->d_pel_f, std::vector<float>(m->h.pel.begin(), m->h.pel.end()));
         if (rc == STOKES_OK) rc = upload(&m->d_face_elem, m->h.face_elem);
         if (rc == STOKES_OK) rc = upload(&m->d_fgeo, m->h.fgeo);
         if (rc == STOKES_OK) rc = upload(&m->d_fmap, m->h.fmap);

@@ -36,6 +36,11 @@ namespace STOKES_NS {
 #ifndef CPL_MINB
 #define CPL_MINB 3
 #endif
+// the next group's velocity, pressure and projector index loaded into
+// registers before the current group's transposed sweeps and scatter
+#ifndef CPL_PREFETCH
+#define CPL_PREFETCH 1
+#endif
 struct CplCfg {
     static constexpr int W = CPL_WARPS;                  // warps per block
     static constexpr int TAIL = (EPW + 1) * 4 * N2;      // basal face scratch per warp (values)
@@ -151,13 +156,12 @@ __device__ __forceinline__ void cpl_transpose(const float (&Sx)[27], const float
 __device__ __forceinline__ void cpl_project(const ElemArgs& a, float (&v)[27], int pi, int c, int l1, int l2) {
     const int po1 = c == 0 ? 3 : (c == 1 ? 5 : 4);   // P[c][c+1]: 01, 12, 20
     const int po2 = c == 0 ? 4 : (c == 1 ? 3 : 5);   // P[c][c+2]: 02, 10, 21
-    const double* P = a.pel + int64_t(pi < 0 ? 0 : pi) * 6 * N2;
+    const float* P = a.pel_f + int64_t(pi < 0 ? 0 : pi) * 6 * N2;
     #pragma unroll
     for (int ab = 0; ab < 9; ++ab) {
         const float v1 = __shfl_sync(0xffffffffu, v[ab], l1);
         const float v2 = __shfl_sync(0xffffffffu, v[ab], l2);
-        if (pi >= 0)
-            v[ab] = float(P[c * N2 + ab]) * v[ab] + float(P[po1 * N2 + ab]) * v1 + float(P[po2 * N2 + ab]) * v2;
+        if (pi >= 0) v[ab] = P[c * N2 + ab] * v[ab] + P[po1 * N2 + ab] * v1 + P[po2 * N2 + ab] * v2;
     }
 }
 
@@ -238,22 +242,43 @@ __global__ void __launch_bounds__(32 * CplCfg::W, CPL_MINB) cpl_state_apply_kern
     __syncwarp();
     if (g < ngroups && lane == 0) stage(g);
 
+    // inputs of a group: velocity component c at the 27 nodes, pressure
+    // coefficients, basal projector index
+    float wn[27], pvn[NPR];
+    int pin = -1;
+    auto load_inputs = [&](int64_t gg) {
+        const int64_t en = gg * CPL_E + el;
+        const bool an = (el < CPL_E) && (gg < ngroups) && (en < a.E);
+        pin = an ? a.pidx[en] : -1;
+        #pragma unroll
+        for (int b = 0; b < NPR; ++b) pvn[b] = an ? ld(x + 3 * a.Nv + en * NPR + b) : 0.f;
+        if constexpr (!PONLY)
+            cpl_nodes(a, en, an, [&](int n, int64_t gn) { wn[n] = an ? ld(x + 3 * gn + c) : 0.f; });
+    };
+#if CPL_PREFETCH
+    load_inputs(g);
+#endif
+
     for (int it = 0; g < ngroups; g += gstride, ++it) {
         const int64_t e = g * CPL_E + el;
         const bool active = (el < CPL_E) && (e < a.E);
-        const int pi = active ? a.pidx[e] : -1;
+#if !CPL_PREFETCH
+        load_inputs(g);
+#endif
+        const int pi = pin;
         const bool any_basal = __any_sync(0xffffffffu, pi >= 0) != 0;
+        float pv[NPR];
+        #pragma unroll
+        for (int b = 0; b < NPR; ++b) pv[b] = pvn[b];
 
         float Gx[27], Gy[27], Gz[27];
         if constexpr (!PONLY) {
             float w[27];
-            cpl_nodes(a, e, active, [&](int n, int64_t gn) { w[n] = active ? ld(x + 3 * gn + c) : 0.f; });
+            #pragma unroll
+            for (int n = 0; n < 27; ++n) w[n] = wn[n];
             if (any_basal) cpl_project(a, w, pi, c, l1, l2);
             cpl_forward(w, Gx, Gy, Gz);
         }
-        float pv[NPR];
-        #pragma unroll
-        for (int b = 0; b < NPR; ++b) pv[b] = active ? ld(x + 3 * a.Nv + e * NPR + b) : 0.f;
 
         if (!mbar_wait_bounded(bar, uint32_t(it & 1))) {
             // the staged state never arrived: report, let the copy drain, stop
@@ -273,7 +298,7 @@ __global__ void __launch_bounds__(32 * CplCfg::W, CPL_MINB) cpl_state_apply_kern
             #pragma unroll
             for (int q9 = 0; q9 < 9; ++q9) {
                 const int qp = q9 + 9 * lq;
-                const float* F = buf + CPL_HDR + lq * CPL_PL + q9 * CPL_E + els;
+                const float* F = buf + CPL_HDR + lq * CPL_PL + els * N2 + q9;
                 const float wdj = F[3 * CPL_FS];
                 const float z0 = F[c * CPL_FS], z1 = F[fz1 * CPL_FS], z2 = F[fz2 * CPL_FS];
                 float p = 0.f;
@@ -328,6 +353,9 @@ __global__ void __launch_bounds__(32 * CplCfg::W, CPL_MINB) cpl_state_apply_kern
             }
         }
 
+#if CPL_PREFETCH
+        load_inputs(g + gstride);
+#endif
         float out[27];
         cpl_transpose(Gx, Gy, Gz, out);
         if (any_basal) cpl_project(a, out, pi, c, l1, l2);

@@ -140,8 +140,9 @@ template <typename T> struct Rows {
 // component-per-lane apply): groups of CPL_E consecutive elements, each a
 // header (the 2 element constants of the group's elements, padded) and one
 // block per Gauss plane lq holding, field by field, the 9 points of the plane
-// for the CPL_E elements ([f][q9][element], plane padded to a 16-byte
-// multiple).  A group is one contiguous 16-byte-multiple block.
+// of each of the CPL_E elements ([f][element][q9], plane padded to a 16-byte
+// multiple: the reads of a warp, three fields at a time, fall on distinct
+// shared-memory banks).  A group is one contiguous 16-byte-multiple block.
 constexpr int CPL_E = 10;
 constexpr int CPL_HDR = 24;
 constexpr int CPL_FS = N2 * CPL_E;                                 // values per field and plane
@@ -159,7 +160,7 @@ __device__ __forceinline__ int64_t state_index(int64_t e, int s, int cpl) {
         if (s < 2) return gg * CPL_GROUP + s * CPL_E + el;
         const int f = (s - 2) / Q3, qp = (s - 2) - f * Q3;
         const int lq = qp / N2, q9 = qp - lq * N2;
-        return gg * CPL_GROUP + CPL_HDR + lq * CPL_PL + f * CPL_FS + q9 * CPL_E + el;
+        return gg * CPL_GROUP + CPL_HDR + lq * CPL_PL + f * CPL_FS + el * N2 + q9;
     }
     return e * SSTRIDE + (s < 2 ? s : s + state_shift(e));
 }

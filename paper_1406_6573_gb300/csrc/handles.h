@@ -65,6 +65,7 @@ struct stokes_mesh {
     double* d_geo = nullptr;
     int32_t* d_pidx = nullptr;
     double* d_pel = nullptr;
+    float* d_pel_f = nullptr;      // the same projector entries in FP32 (FP32 kernels)
     int32_t* d_face_elem = nullptr;
     int32_t* d_fidx = nullptr;
     double* d_fgeo = nullptr;

@@ -59,6 +59,7 @@ struct ElemArgs {
     const double* geo;         // [E][10][q^3]
     const int32_t* pidx;       // [E]
     const double* pel;         // [nP][6][n1^2]
+    const float* pel_f;        // the same in FP32
     const void* x;             // input state vector (residual: up; apply: direction)
     void* y;                   // output state vector (accumulated; zeroed by the caller)
     const void* u;             // linearisation point (fused apply), same type as x
