@@ -83,6 +83,7 @@ def parse():
                     help="skip the time-to-1e-10 Newton solves (FP32-inner vs FP64)")
     ap.add_argument("--adjoint-check", type=int, default=0, metavar="N",
                     help="adjoint gradient of a surface misfit and N central-difference directional checks")
+    ap.add_argument("--restart", type=int, default=30, help="FGMRES restart length of the solves")
     ap.add_argument("--eta-max", type=float, default=0.1,
                     help="cap of the Eisenstat-Walker forcing term of the time-to-solution runs")
     ap.add_argument("--solve-precs", default="fp32_inner,fp64",
@@ -451,7 +452,7 @@ def run_ours(args):
             p_solve = p_picard if tag.endswith("picard") else p
             op = capi.stokes_solver_opts()
             op.inner_prec = inner
-            op.restart = 30
+            op.restart = args.restart
             op.max_krylov = 4000
             op.max_newton = 300 if tag.endswith("picard") else 60
             op.rtol = 1e-10
@@ -474,6 +475,7 @@ def run_ours(args):
                 du = (u0 - u_fp32).norm() / u0.norm()
                 solve["rel_diff_fp32_vs_fp64_solution"] = float(du)
         solve["eta_max"] = args.eta_max
+        solve["restart"] = args.restart
         if "fp32_inner" in solve and "fp64" in solve:
             solve["speedup_fp32_inner"] = round(solve["fp64"]["seconds"] / solve["fp32_inner"]["seconds"], 3)
 

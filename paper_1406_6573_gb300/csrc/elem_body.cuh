@@ -189,6 +189,7 @@ __global__ void __launch_bounds__(32 * GW<T>) elem_kernel(ElemArgs a) {
         if (any_h) hanging_forward<T, 3>(v, h, active, i, j, sb);
         ref_gradient<T, 3>(R, v, G, i, j, sb);
         S* st = static_cast<S*>(a.state);
+        const StateRef sr(active ? e : 0, a.state_cpl);
         #pragma unroll
         for (int lq = 0; lq < Q; ++lq) {
             const int qp = sidx(i, j, lq);
@@ -204,19 +205,20 @@ __global__ void __launch_bounds__(32 * GW<T>) elem_kernel(ElemArgs a) {
             const T mk = -T(2) * T(a.gamma) * T(a.pexp) * mu * wdj / (T(a.gamma) * DD + T(a.delta));
             const T sq = (a.picard || !(mk > T(0))) ? T(0) : sqrt(mk);   // Picard: no rank-one term
             if (active) {
-                auto put = [&](int slot, T v) { st[state_index(e, slot, a.state_cpl)] = S(v); };
-                if (qp == 0) { put(0, Ji[0]); put(1, Ji[4]); }
-                put(2 + 0 * Q3 + qp, Ji[6]);
-                put(2 + 1 * Q3 + qp, Ji[7]);
-                put(2 + 2 * Q3 + qp, Ji[8]);
-                put(2 + 3 * Q3 + qp, wdj);
-                put(2 + 4 * Q3 + qp, mu * wdj);
-                put(2 + 5 * Q3 + qp, sq * E00);
-                put(2 + 6 * Q3 + qp, sq * E11);
-                put(2 + 7 * Q3 + qp, sq * E22);
-                put(2 + 8 * Q3 + qp, sq * E01);
-                put(2 + 9 * Q3 + qp, sq * E02);
-                put(2 + 10 * Q3 + qp, sq * E12);
+                S* F = st + sr.f(0, lq, i + N1 * j);
+                const int fs = sr.fstride;
+                if (qp == 0) { st[sr.c(0)] = S(Ji[0]); st[sr.c(1)] = S(Ji[4]); }
+                F[0] = S(Ji[6]);
+                F[fs] = S(Ji[7]);
+                F[2 * fs] = S(Ji[8]);
+                F[3 * fs] = S(wdj);
+                F[4 * fs] = S(mu * wdj);
+                F[5 * fs] = S(sq * E00);
+                F[6 * fs] = S(sq * E11);
+                F[7 * fs] = S(sq * E22);
+                F[8 * fs] = S(sq * E01);
+                F[9 * fs] = S(sq * E02);
+                F[10 * fs] = S(sq * E12);
             }
         }
     } else if constexpr (MODE == MODE_GRAD_A || MODE == MODE_GRAD_A_PARTIAL) {

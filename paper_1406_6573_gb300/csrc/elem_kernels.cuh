@@ -150,20 +150,36 @@ constexpr int CPL_PL = (STATE_FIELDS * CPL_FS + 3) / 4 * 4;       // values per 
 constexpr int CPL_GROUP = CPL_HDR + N1 * CPL_PL;                   // values per group
 static_assert(K != 2 || (CPL_E == CPL_GROUP_ELEMS && CPL_GROUP == CPL_GROUP_VALUES), "group layout of k = 2");
 
-// Linearised-state slot s of element e: slots 0, 1 are the element
-// constants, slot 2 + f q^3 + qp field f at qp.  Element-major [E][SSTRIDE]
-// layout, or the group layout above (cpl != 0).
-__device__ __forceinline__ int64_t state_index(int64_t e, int s, int cpl) {
-    if (cpl) {
-        const int64_t gg = e / CPL_E;
-        const int el = int(e - gg * CPL_E);
-        if (s < 2) return gg * CPL_GROUP + s * CPL_E + el;
-        const int f = (s - 2) / Q3, qp = (s - 2) - f * Q3;
-        const int lq = qp / N2, q9 = qp - lq * N2;
-        return gg * CPL_GROUP + CPL_HDR + lq * CPL_PL + f * CPL_FS + el * N2 + q9;
+// Linearised-state slots of element e, with the layout arithmetic done once:
+// the element constants s = 0, 1 and field f at the Gauss point q9 + N2 lq
+// (q9 = i + N1 j).  Element-major [E][SSTRIDE] layout (constants, shift
+// slot, then field-major q^3 values), or the group layout above (cpl != 0).
+struct StateRef {
+    int64_t c0, f0;       // slot of constant 0, of field 0 at point 0
+    int cstride;          // between the two constants
+    int fstride, lstride; // between fields, between Gauss planes
+    __device__ __forceinline__ StateRef(int64_t e, int cpl) {
+        if (cpl) {
+            const int64_t gg = e / CPL_E;
+            const int el = int(e - gg * CPL_E);
+            c0 = gg * CPL_GROUP + el;
+            cstride = CPL_E;
+            f0 = gg * CPL_GROUP + CPL_HDR + el * N2;
+            fstride = CPL_FS;
+            lstride = CPL_PL;
+        } else {
+            c0 = e * SSTRIDE;
+            cstride = 1;
+            f0 = e * SSTRIDE + 2 + state_shift(e);
+            fstride = Q3;
+            lstride = N2;
+        }
     }
-    return e * SSTRIDE + (s < 2 ? s : s + state_shift(e));
-}
+    __device__ __forceinline__ int64_t c(int s) const { return c0 + s * cstride; }
+    __device__ __forceinline__ int64_t f(int field, int lq, int q9) const {
+        return f0 + field * fstride + lq * lstride + q9;
+    }
+};
 
 // --------------------------------------------------------------- helpers
 template <typename T> __device__ __forceinline__ T ld(const T* p) { return __ldg(p); }

@@ -96,10 +96,16 @@ __global__ void col_solve_kernel(ColSolveArgs a, const T* __restrict__ rhs, T* _
     }
 }
 
-// The same solve with the band width fixed at compile time: each row's BW
-// band entries are loaded together (independent loads, one latency per row)
-// while the previous row is being eliminated, instead of one dependent load
-// per entry.
+// The same solve with the band width fixed at compile time.  The band entries
+// of a row are loaded CS_AHEAD rows before they are used (a ring of
+// CS_AHEAD + 1 rows in registers, the row loop unrolled by the ring length so
+// that every ring index is known at compile time): one thread per column
+// would otherwise keep a single row of loads in flight, too few bytes per SM
+// to cover the DRAM latency of the 227 MB band of the 128x128x8 Q2 slab.
+// The arithmetic is the same, in the same order, as in col_solve_kernel.
+#ifndef CS_AHEAD
+#define CS_AHEAD 3
+#endif
 template <typename T, int BW>
 __global__ void col_solve_band_kernel(ColSolveArgs a, const T* __restrict__ rhs, T* __restrict__ z) {
     extern __shared__ unsigned char smraw[];
@@ -108,6 +114,7 @@ __global__ void col_solve_band_kernel(ColSolveArgs a, const T* __restrict__ rhs,
     const int nt = blockDim.x, t = threadIdx.x;
     if (c >= a.ncol) return;
     constexpr int W = 2 * BW + 1;
+    constexpr int R = CS_AHEAD + 1;
     const int64_t ncol = a.ncol;
     const T* A = static_cast<const T*>(a.A) + c;
     const int len = a.col_len[c], n = 3 * len;
@@ -117,37 +124,51 @@ __global__ void col_solve_band_kernel(ColSolveArgs a, const T* __restrict__ rhs,
     }
     if (n == 0) return;
     auto row = [&](int r) { return A + int64_t(r) * W * ncol; };
-    // L y = r (unit lower): row r holds L[r][r - d] at band slot BW - d
-    T cur[BW], nxt[BW];
+    // L y = r (unit lower): row r holds L[r][r - d] at band slot BW - d;
+    // row r lives in ring slot r mod R
+    T L[R][BW];
+    auto loadL = [&](int r, T (&dst)[BW]) {
+        #pragma unroll
+        for (int d = 1; d <= BW; ++d) dst[d - 1] = (r < n && r - d >= 0) ? row(r)[(BW - d) * ncol] : T(0);
+    };
     #pragma unroll
-    for (int d = 1; d <= BW; ++d) cur[d - 1] = (n > 1 && 1 - d >= 0) ? row(1)[(BW - d) * ncol] : T(0);
-    for (int r = 1; r < n; ++r) {
-        const T* rn = row(r + 1);
+    for (int u = 1; u < R; ++u) loadL(u, L[u]);
+    for (int r0 = 0; r0 < n; r0 += R) {
         #pragma unroll
-        for (int d = 1; d <= BW; ++d) nxt[d - 1] = (r + 1 < n && r + 1 - d >= 0) ? rn[(BW - d) * ncol] : T(0);
-        T s = zc[r * nt + t];
-        #pragma unroll
-        for (int d = 1; d <= BW; ++d)
-            if (r - d >= 0) s -= cur[d - 1] * zc[(r - d) * nt + t];
-        zc[r * nt + t] = s;
-        #pragma unroll
-        for (int d = 0; d < BW; ++d) cur[d] = nxt[d];
+        for (int u = 0; u < R; ++u) {
+            const int r = r0 + u;
+            if (r >= 1 && r < n) {
+                loadL(r + R - 1, L[(u + R - 1) % R]);   // into the slot of row r - 1
+                T s = zc[r * nt + t];
+                #pragma unroll
+                for (int d = 1; d <= BW; ++d)
+                    if (r - d >= 0) s -= L[u][d - 1] * zc[(r - d) * nt + t];
+                zc[r * nt + t] = s;
+            }
+        }
     }
-    // U x = y: row r holds U[r][r] at slot BW and U[r][r + d] at slot BW + d
-    T cu[BW + 1], nu[BW + 1];
+    // U x = y: row r holds U[r][r] at slot BW and U[r][r + d] at slot BW + d;
+    // row n - 1 - i lives in ring slot i mod R
+    T U[R][BW + 1];
+    auto loadU = [&](int r, T (&dst)[BW + 1]) {
+        #pragma unroll
+        for (int d = 0; d <= BW; ++d) dst[d] = (r >= 0 && r + d < n) ? row(r)[(BW + d) * ncol] : T(0);
+    };
     #pragma unroll
-    for (int d = 0; d <= BW; ++d) cu[d] = (n - 1 + d < n) ? row(n - 1)[(BW + d) * ncol] : T(0);
-    for (int r = n - 1; r >= 0; --r) {
-        const T* rp = row(r > 0 ? r - 1 : 0);
+    for (int u = 0; u < R - 1; ++u) loadU(n - 1 - u, U[u]);
+    for (int i0 = 0; i0 < n; i0 += R) {
         #pragma unroll
-        for (int d = 0; d <= BW; ++d) nu[d] = (r > 0 && r - 1 + d < n) ? rp[(BW + d) * ncol] : T(0);
-        T s = zc[r * nt + t];
-        #pragma unroll
-        for (int d = 1; d <= BW; ++d)
-            if (r + d < n) s -= cu[d] * zc[(r + d) * nt + t];
-        zc[r * nt + t] = s / cu[0];
-        #pragma unroll
-        for (int d = 0; d <= BW; ++d) cu[d] = nu[d];
+        for (int u = 0; u < R; ++u) {
+            const int r = n - 1 - (i0 + u);
+            if (r >= 0) {
+                loadU(r - (R - 1), U[(u + R - 1) % R]);   // into the slot of row r + 1
+                T s = zc[r * nt + t];
+                #pragma unroll
+                for (int d = 1; d <= BW; ++d)
+                    if (r + d < n) s -= U[u][d] * zc[(r + d) * nt + t];
+                zc[r * nt + t] = s / U[u][0];
+            }
+        }
     }
     for (int p = 0; p < len; ++p) {
         const int64_t g = a.col_nodes[int64_t(p) * ncol + c];

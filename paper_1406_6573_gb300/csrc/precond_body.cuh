@@ -42,8 +42,8 @@ __global__ void __launch_bounds__(256) colblock_kernel(ColArgs a) {
     const int64_t na = a.nodes[e * N3 + sl];
     const int col = a.col_of[na], pa = a.pos_of[na];
     const T* st0 = static_cast<const T*>(a.state);
-    auto stv = [&](int slot) { return st0[state_index(e, slot, a.state_cpl)]; };
-    const T ia = stv(0), ib = stv(1);
+    const StateRef sr(e, a.state_cpl);
+    const T ia = st0[sr.c(0)], ib = st0[sr.c(1)];
     const int bw = a.bw, W = 2 * a.bw + 1;
     T* A = static_cast<T*>(a.A);
     for (int l2 = 0; l2 < N1; ++l2) {
@@ -54,11 +54,11 @@ __global__ void __launch_bounds__(256) colblock_kernel(ColArgs a) {
         for (int lq = 0; lq < Q; ++lq)
             for (int jq = 0; jq < Q; ++jq)
                 for (int iq = 0; iq < Q; ++iq) {
-                    const int qp = iq + Q * (jq + Q * lq);
-                    const int f = 2 + qp;
-                    const T g0 = stv(f), g1 = stv(f + Q3), g2 = stv(f + 2 * Q3), muw = stv(f + 4 * Q3);
-                    const T D00 = stv(f + 5 * Q3), D11 = stv(f + 6 * Q3), D22 = stv(f + 7 * Q3);
-                    const T D01 = stv(f + 8 * Q3), D02 = stv(f + 9 * Q3), D12 = stv(f + 10 * Q3);
+                    const T* F = st0 + sr.f(0, lq, iq + Q * jq);
+                    const int fs = sr.fstride;
+                    const T g0 = F[0], g1 = F[fs], g2 = F[2 * fs], muw = F[4 * fs];
+                    const T D00 = F[5 * fs], D11 = F[6 * fs], D22 = F[7 * fs];
+                    const T D01 = F[8 * fs], D02 = F[9 * fs], D12 = F[10 * fs];
                     const T bi = Tab<T>::B(iq, i), bj = Tab<T>::B(jq, j);
                     const T dbi = Bd<T>(iq, i), dbj = Bd<T>(jq, j);
                     const T ra[3] = {dbi * bj * Tab<T>::B(lq, l), bi * dbj * Tab<T>::B(lq, l), bi * bj * Bd<T>(lq, l)};
@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(256) schur_block_kernel(ColArgs a) {
     const int b2 = a.schur_full ? r - b1 * a.npr : r;
     const int ps = a.pspace;
     const T* st0 = static_cast<const T*>(a.state);
-    auto stv = [&](int slot) { return st0[state_index(e, slot, a.state_cpl)]; };
+    const StateRef sr(e, a.state_cpl);
     const int a0 = cPm[ps][b1][0], a1 = cPm[ps][b1][1], a2 = cPm[ps][b1][2];
     const int c0 = cPm[ps][b2][0], c1 = cPm[ps][b2][1], c2 = cPm[ps][b2][2];
     // arithmetic of the state's type (a preconditioner block), summed per
@@ -136,8 +136,8 @@ __global__ void __launch_bounds__(256) schur_block_kernel(ColArgs a) {
         for (int jq = 0; jq < Q; ++jq) {
             const T py = Tab<T>::P1(ps, jq, a1) * Tab<T>::P1(ps, jq, c1);
             for (int iq = 0; iq < Q; ++iq) {
-                const int qp = iq + Q * (jq + Q * lq);
-                const T wdj = stv(2 + 3 * Q3 + qp), muw = stv(2 + 4 * Q3 + qp);
+                const T* F = st0 + sr.f(3, lq, iq + Q * jq);
+                const T wdj = F[0], muw = F[sr.fstride];
                 sp += Tab<T>::P1(ps, iq, a0) * Tab<T>::P1(ps, iq, c0) * py * (wdj * (wdj / muw));
             }
         }

@@ -144,6 +144,12 @@ int precond_apply(stokes_solver* S, const void* v, void* z, cudaStream_t st) {
 
 // One FGMRES(m) cycle on A x = b with b = tin (inner precision), x0 = 0.
 // Adds Z y to the FP64 vector dl.  Returns the number of iterations in its.
+// Second Gram-Schmidt pass when the first removes more than (1 - theta) of
+// ||w||^2; above that the Pythagorean norm is accurate to about eps / theta.
+#ifndef STOKES_REORTH_THETA
+#define STOKES_REORTH_THETA 0.1
+#endif
+
 int fgmres_cycle(stokes_solver* S, bool trans, double tol_rel, int max_its, int& its, cudaStream_t st) {
     const int64_t n = S->n;
     const int m = std::min(S->o.restart, max_its);
@@ -182,7 +188,7 @@ int fgmres_cycle(stokes_solver* S, bool trans, double tol_rel, int max_its, int&
         for (int i = 0; i <= k; ++i) { H[size_t(i) * m + k] = h[i]; hh += h[i] * h[i]; }
         double hn2 = w2 - hh;
         const double* hdev = S->dsc;
-        if (hn2 < 0.49 * w2) {
+        if (hn2 < STOKES_REORTH_THETA * w2) {
             CU(vec_multiaxpy(n, ip, Vj(k + 1), S->V, S->ld, k + 1, S->dsc, 1.0, S->dsc + (m + 1), st),
                "orthogonalisation");
             CU(cudaMemcpyAsync(h.data(), S->dsc + (m + 1), sizeof(double) * (k + 2), cudaMemcpyDeviceToHost, st),
