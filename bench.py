@@ -84,6 +84,8 @@ def parse():
     ap.add_argument("--adjoint-check", type=int, default=0, metavar="N",
                     help="adjoint gradient of a surface misfit and N central-difference directional checks")
     ap.add_argument("--restart", type=int, default=30, help="FGMRES restart length of the solves")
+    ap.add_argument("--no-solve-profile", action="store_true",
+                    help="skip the traced FP32-inner solve (device time per kernel class)")
     ap.add_argument("--eta-max", type=float, default=0.1,
                     help="cap of the Eisenstat-Walker forcing term of the time-to-solution runs")
     ap.add_argument("--solve-precs", default="fp32_inner,fp64",
@@ -476,6 +478,32 @@ def run_ours(args):
                 solve["rel_diff_fp32_vs_fp64_solution"] = float(du)
         solve["eta_max"] = args.eta_max
         solve["restart"] = args.restart
+        if "fp32_inner" in want and not args.no_solve_profile:
+            # one more FP32-inner solve with the library's event tracing on:
+            # device time per class against the wall time of that solve
+            op = capi.stokes_solver_opts()
+            op.inner_prec = capi.STOKES_F32
+            op.restart = args.restart
+            op.max_krylov = 4000
+            op.max_newton = 60
+            op.rtol = 1e-10
+            op.eta_max = args.eta_max
+            sv = capi.stokes_solver_create(mesh.handle, op)
+            u0 = torch.zeros(ndof, dtype=torch.float64, device="cuda")
+            torch.cuda.synchronize()
+            capi.stokes_profile_begin(mesh.handle)
+            t0 = time.perf_counter()
+            rc, rep = capi.stokes_newton_solve(sv, p, u0, stream, check=False)
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t0
+            pr = capi.stokes_profile_end(mesh.handle)
+            capi.stokes_solver_destroy(sv)
+            dev_ms = sum(v[1] for v in pr.values())
+            solve["fp32_inner_traced"] = {
+                "seconds": round(wall, 4), "krylov_its": rep["krylov_its"],
+                "device_ms": {k: [v[0], round(v[1], 2)] for k, v in pr.items() if v[0]},
+                "device_ms_total": round(dev_ms, 2),
+                "not_in_kernels_ms": round(wall * 1e3 - dev_ms, 2)}
         if "fp32_inner" in solve and "fp64" in solve:
             solve["speedup_fp32_inner"] = round(solve["fp64"]["seconds"] / solve["fp32_inner"]["seconds"], 3)
 

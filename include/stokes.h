@@ -289,11 +289,11 @@ int stokes_linear_solve(stokes_solver* solver, const stokes_params* params, cons
                         stokes_solve_report* report, void* stream);
 
 /* Per-kernel timing (tracing).  Between stokes_profile_begin and
- * stokes_profile_end every operator call on this mesh records a CUDA event
- * pair around each of its launches, on the caller's stream; end synchronises
- * on the recorded events and returns launch counts and summed device times
- * per kernel class.  Recording costs a few microseconds of host time per
- * launch and no device work. */
+ * stokes_profile_end every operator call on this mesh, and every launch and
+ * transfer of a solver built on it, records a CUDA event pair around the
+ * work on the caller's stream; end synchronises on the recorded events and
+ * returns launch counts and summed device times per class.  Recording costs
+ * a few microseconds of host time per launch and no device work. */
 typedef struct {
     int64_t launches;
     double ms;
@@ -304,6 +304,13 @@ typedef struct {
     stokes_kernel_time element;     /* volume element kernel                     */
     stokes_kernel_time face;        /* basal Robin face kernel                   */
     stokes_kernel_time constraint;  /* (I - P) constraint kernel                 */
+    stokes_kernel_time precond;     /* solver: preconditioner apply (Schur
+                                       block, update, column solves)           */
+    stokes_kernel_time orthog;      /* solver: Gram-Schmidt passes, norms      */
+    stokes_kernel_time vector;      /* solver: vector updates and copies       */
+    stokes_kernel_time setup;       /* solver: preconditioner set-up per
+                                       linearisation (assembly, factorisation) */
+    stokes_kernel_time transfer;    /* solver: host <-> device scalar copies   */
 } stokes_profile;
 
 int stokes_profile_begin(const stokes_mesh* mesh);

@@ -63,8 +63,8 @@ class stokes_kernel_time(C.Structure):
 
 
 class stokes_profile(C.Structure):
-    _fields_ = [("clear", stokes_kernel_time), ("element", stokes_kernel_time),
-                ("face", stokes_kernel_time), ("constraint", stokes_kernel_time)]
+    _fields_ = [(name, stokes_kernel_time) for name in
+                ("clear", "element", "face", "constraint", "precond", "orthog", "vector", "setup", "transfer")]
 
 
 class stokes_solver_opts(C.Structure):
@@ -255,8 +255,7 @@ def stokes_profile_begin(h):
 def stokes_profile_end(h):
     p = stokes_profile()
     _check(lib().stokes_profile_end(h, C.byref(p)))
-    return {name: (getattr(p, name).launches, getattr(p, name).ms)
-            for name in ("clear", "element", "face", "constraint")}
+    return {name: (getattr(p, name).launches, getattr(p, name).ms) for name, _ in stokes_profile._fields_}
 
 
 def stokes_mesh_status(h):

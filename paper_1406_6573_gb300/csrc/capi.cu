@@ -50,19 +50,6 @@ int upload(T** dst, const std::vector<T>& src) {
     return STOKES_OK;
 }
 
-// Run `launch` between two recorded events when profiling (class c).
-template <typename F>
-int timed(const stokes_mesh* m, int c, cudaStream_t s, F&& launch) {
-    if (!m->prof.active) return launch();
-    cudaEvent_t a = m->prof.next(), b = m->prof.next();
-    if (!a || !b) return launch();
-    size_t ia = m->prof.used - 2;
-    cudaEventRecord(a, s);
-    int rc = launch();
-    cudaEventRecord(b, s);
-    m->prof.recs.push_back({c, ia});
-    return rc;
-}
 
 void free_mesh_device(stokes_mesh* m) {
     for (cudaEvent_t ev : m->prof.pool) cudaEventDestroy(ev);
@@ -301,7 +288,9 @@ int stokes_profile_end(const stokes_mesh* mesh, stokes_profile* out) {
     if (!mesh->prof.active) return fail(STOKES_E_INVAL, "profiling was not started");
     mesh->prof.active = false;
     DeviceGuard g(mesh->device);
-    stokes_kernel_time* slot[4] = {&out->clear, &out->element, &out->face, &out->constraint};
+    stokes_kernel_time* slot[PROF_CLASSES] = {&out->clear, &out->element, &out->face, &out->constraint,
+                                              &out->precond, &out->orthog, &out->vector, &out->setup,
+                                              &out->transfer};
     for (auto& r : mesh->prof.recs) {
         cudaEvent_t a = mesh->prof.pool[r.second], b = mesh->prof.pool[r.second + 1];
         cudaError_t ce = cudaEventSynchronize(b);
@@ -479,8 +468,10 @@ int stokes_linearize(stokes_state* state, const stokes_params* params, const dou
     a.ud = up_lin;
     a.state = state->d_state;
     a.state_cpl = state->cpl;
-    int e = launch_elem(mesh->h.k, MODE_LINEARIZE, STOKES_F64, state->prec, false, a,
-                        static_cast<cudaStream_t>(stream));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int e = timed(mesh, PROF_ELEMENT, s, [&] {
+        return launch_elem(mesh->h.k, MODE_LINEARIZE, STOKES_F64, state->prec, false, a, s);
+    });
     if (e) return cuda_fail(cudaError_t(e), "linearize kernel launch");
     state->params = *params;
     state->linearized = true;

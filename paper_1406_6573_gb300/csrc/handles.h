@@ -34,6 +34,12 @@ int fail(int code, const std::string& msg);
 int cuda_fail(cudaError_t e, const char* where);
 
 // Make `dev` current for the duration of a call, restoring the caller's device.
+// Profiler classes (the fields of stokes_profile, in order)
+enum ProfClass : int {
+    PROF_CLEAR = 0, PROF_ELEMENT, PROF_FACE, PROF_CONSTRAINT,
+    PROF_PRECOND, PROF_ORTHOG, PROF_VECTOR, PROF_SETUP, PROF_TRANSFER, PROF_CLASSES
+};
+
 struct DeviceGuard {
     int prev = -1;
     cudaError_t err = cudaSuccess;
@@ -80,6 +86,22 @@ struct stokes_mesh {
     int32_t* d_col_len = nullptr;
     int32_t* d_col_basal = nullptr;
 };
+
+namespace stokes {
+// Run `launch` between two recorded events when profiling (class c).
+template <typename F>
+int timed(const stokes_mesh* m, int c, cudaStream_t s, F&& launch) {
+    if (!m->prof.active) return launch();
+    cudaEvent_t a = m->prof.next(), b = m->prof.next();
+    if (!a || !b) return launch();
+    size_t ia = m->prof.used - 2;
+    cudaEventRecord(a, s);
+    int rc = launch();
+    cudaEventRecord(b, s);
+    m->prof.recs.push_back({c, ia});
+    return rc;
+}
+}  // namespace stokes
 
 struct stokes_state {
     const stokes_mesh* mesh = nullptr;

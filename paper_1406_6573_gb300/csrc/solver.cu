@@ -6,9 +6,9 @@
 //    inexact linear solves.
 //  * Krylov (Section 4.2): right-preconditioned flexible GMRES(m) with the
 //    block upper-triangular preconditioner of Eq. 4.1, F~ = vertical-column
-//    blocks of F, S~ = -diag M(1/mu) (Section 6).  Classical Gram-Schmidt
-//    with FP64 accumulation, one reorthogonalisation pass when the norm drops
-//    by more than a factor 0.7.
+//    blocks of F, S~ = -M(1/mu) (Section 6).  Classical Gram-Schmidt with
+//    FP64 accumulation, one reorthogonalisation pass when the first removes
+//    more than (1 - STOKES_REORTH_THETA) of ||w||^2.
 //  * Mixed precision: with inner precision FP32 the Krylov vectors, the
 //    operator applies and the preconditioner run in FP32; every restart
 //    recomputes the linear residual in FP64 with the FP64 state (iterative
@@ -72,12 +72,14 @@ void free_solver(stokes_solver* s) {
         int e_ = int(call);                                         \
         if (e_) return cuda_fail(cudaError_t(e_), what);            \
     } while (0)
+// CU with the work recorded under a profiler class when tracing is on
+#define TU(cls, call, what) CU(timed(S->mesh, cls, st, [&] { return int(call); }), what)
 
 // ||x||_2 of an FP64 device vector (synchronises)
 int norm64(stokes_solver* S, const double* x, int64_t n, double& out, cudaStream_t st) {
-    CU(vec_multidot(n, STOKES_F64, x, 0, 0, STOKES_F64, x, S->dsc, 1, st), "norm");
+    TU(PROF_VECTOR, vec_multidot(n, STOKES_F64, x, 0, 0, STOKES_F64, x, S->dsc, 1, st), "norm");
     double h = 0;
-    CU(cudaMemcpyAsync(&h, S->dsc, sizeof(double), cudaMemcpyDeviceToHost, st), "norm readback");
+    TU(PROF_TRANSFER, cudaMemcpyAsync(&h, S->dsc, sizeof(double), cudaMemcpyDeviceToHost, st), "norm readback");
     CU(cudaStreamSynchronize(st), "norm sync");
     out = std::sqrt(h);
     return STOKES_OK;
@@ -108,26 +110,26 @@ ColSolveArgs colsolve_args(stokes_solver* S, double scale) {
 // |diagonal| of the velocity block is returned before factorisation.
 int precond_setup(stokes_solver* S, const stokes_params* p, cudaStream_t st, double* scale_out = nullptr) {
     const stokes_mesh* m = S->mesh;
-    CU(cudaMemsetAsync(S->A, 0, S->band_elems * S->isz, st), "clearing column blocks");
+    TU(PROF_SETUP, cudaMemsetAsync(S->A, 0, S->band_elems * S->isz, st), "clearing column blocks");
     ColArgs a{};
     a.E = m->h.E; a.ncol = m->h.ncol; a.npr = m->h.npr; a.pspace = m->h.pspace; a.bw = S->bw;
     a.robin = p->robin && m->h.nF > 0;
     a.nodes = m->d_nodes; a.hang = m->d_hang; a.col_of = m->d_col_of; a.pos_of = m->d_pos_of;
     a.fidx = m->d_fidx; a.fmap = m->d_fmap; a.fgeo = m->d_fgeo; a.logbeta = p->logbeta;
     a.state = S->st_in->d_state; a.state_cpl = S->st_in->cpl; a.A = S->A; a.mblk = S->mblk; a.schur_full = schur_full(m);
-    CU(launch_precond_assembly(m->h.k, S->inner, a, st), "preconditioner assembly");
-    CU(launch_schur_invert(S->inner, m->h.E, m->h.npr, schur_full(m), S->mblk, S->md, st), "Schur inversion");
+    TU(PROF_SETUP, launch_precond_assembly(m->h.k, S->inner, a, st), "preconditioner assembly");
+    TU(PROF_SETUP, launch_schur_invert(S->inner, m->h.E, m->h.npr, schur_full(m), S->mblk, S->md, st), "Schur inversion");
     double scale = p->constraint_scale;
     if (scale_out) {
-        CU(launch_col_diag_sum(S->inner, colsolve_args(S, scale), S->dsc, st), "diagonal scale");
+        TU(PROF_SETUP, launch_col_diag_sum(S->inner, colsolve_args(S, scale), S->dsc, st), "diagonal scale");
         double sum = 0;
-        CU(cudaMemcpyAsync(&sum, S->dsc, sizeof(double), cudaMemcpyDeviceToHost, st), "readback");
+        TU(PROF_TRANSFER, cudaMemcpyAsync(&sum, S->dsc, sizeof(double), cudaMemcpyDeviceToHost, st), "readback");
         CU(cudaStreamSynchronize(st), "sync");
         scale = sum / double(3 * m->h.Nv);
         if (!(scale > 0)) scale = 1.0;
         *scale_out = scale;
     }
-    CU(launch_col_factor(S->inner, colsolve_args(S, scale), st), "column factorisation");
+    TU(PROF_SETUP, launch_col_factor(S->inner, colsolve_args(S, scale), st), "column factorisation");
     return STOKES_OK;
 }
 
@@ -135,10 +137,10 @@ int precond_setup(stokes_solver* S, const stokes_params* p, cudaStream_t st, dou
 // z_u = F~^{-1}(v_u - B^T z_p)
 int precond_apply(stokes_solver* S, const void* v, void* z, cudaStream_t st) {
     const stokes_mesh* m = S->mesh;
-    CU(launch_schur_apply(S->inner, m->h.Nv, m->h.E, m->h.npr, schur_full(m), S->md, v, z, st), "Schur apply");
+    TU(PROF_PRECOND, launch_schur_apply(S->inner, m->h.Nv, m->h.E, m->h.npr, schur_full(m), S->md, v, z, st), "Schur apply");
     CK(state_gradp(S->st_in, z, S->tz, st));
-    CU(vec_axpby(S->nu, 1.0, nullptr, S->inner, v, -1.0, S->inner, S->tz, st), "preconditioner update");
-    CU(launch_col_solve(S->inner, colsolve_args(S, 1.0), S->tz, z, st), "column solve");
+    TU(PROF_PRECOND, vec_axpby(S->nu, 1.0, nullptr, S->inner, v, -1.0, S->inner, S->tz, st), "preconditioner update");
+    TU(PROF_PRECOND, launch_col_solve(S->inner, colsolve_args(S, 1.0), S->tz, z, st), "column solve");
     return STOKES_OK;
 }
 
@@ -159,28 +161,28 @@ int fgmres_cycle(stokes_solver* S, bool trans, double tol_rel, int max_its, int&
     auto Zj = [&](int j) { return static_cast<char*>(S->Z) + size_t(j) * S->ld * isz; };
     std::vector<double> H(size_t(m + 1) * m, 0.0), cs(m, 0.0), sn(m, 0.0), g(m + 1, 0.0), h(m + 2, 0.0);
     // V_0 = b / ||b||
-    CU(vec_axpby(n, 1.0, nullptr, ip, S->tin, 0.0, ip, Vj(0), st), "copy");
-    CU(vec_multidot(n, ip, Vj(0), 0, 0, ip, Vj(0), S->dsc, 1, st), "dot");
-    CU(cudaMemcpyAsync(h.data(), S->dsc, sizeof(double), cudaMemcpyDeviceToHost, st), "readback");
+    TU(PROF_VECTOR, vec_axpby(n, 1.0, nullptr, ip, S->tin, 0.0, ip, Vj(0), st), "copy");
+    TU(PROF_ORTHOG, vec_multidot(n, ip, Vj(0), 0, 0, ip, Vj(0), S->dsc, 1, st), "dot");
+    TU(PROF_TRANSFER, cudaMemcpyAsync(h.data(), S->dsc, sizeof(double), cudaMemcpyDeviceToHost, st), "readback");
     CU(cudaStreamSynchronize(st), "sync");
     const double beta = std::sqrt(h[0]);
     its = 0;
     if (!(beta > 0)) return STOKES_OK;
-    CU(vec_normalize(n, ip, Vj(0), S->dsc, st), "normalize");
+    TU(PROF_ORTHOG, vec_normalize(n, ip, Vj(0), S->dsc, st), "normalize");
     g[0] = beta;
     int k = 0;
     for (; k < m; ++k) {
         CK(precond_apply(S, Vj(k), Zj(k), st));
         CK(op_inner(S, Zj(k), Vj(k + 1), trans, st));
         // Classical Gram-Schmidt with FP64-accurate sums.  Pass 1 gives
-        // h = V^T w and ||w||^2 together; when the projection removes less
-        // than about half of w the new norm follows from Pythagoras,
+        // h = V^T w and ||w||^2 together; when the projection leaves more
+        // than theta of ||w||^2 the new norm follows from Pythagoras,
         // ||w - V h||^2 = ||w||^2 - ||h||^2, and pass 2 subtracts and
         // normalises at once.  Otherwise (cancellation) w' = w - V h is
         // formed, V^T w' and ||w'||^2 are taken in one pass, and a last pass
         // subtracts the correction and normalises.
-        CU(vec_multidot(n, ip, S->V, S->ld, k + 1, ip, Vj(k + 1), S->dsc, 1, st), "orthogonalisation dots");
-        CU(cudaMemcpyAsync(h.data(), S->dsc, sizeof(double) * (k + 2), cudaMemcpyDeviceToHost, st), "readback");
+        TU(PROF_ORTHOG, vec_multidot(n, ip, S->V, S->ld, k + 1, ip, Vj(k + 1), S->dsc, 1, st), "orthogonalisation dots");
+        TU(PROF_TRANSFER, cudaMemcpyAsync(h.data(), S->dsc, sizeof(double) * (k + 2), cudaMemcpyDeviceToHost, st), "readback");
         CU(cudaStreamSynchronize(st), "sync");
         const double w2 = h[k + 1];
         if (!std::isfinite(w2)) return fail(STOKES_E_NONFINITE, "non-finite Krylov vector");
@@ -189,9 +191,9 @@ int fgmres_cycle(stokes_solver* S, bool trans, double tol_rel, int max_its, int&
         double hn2 = w2 - hh;
         const double* hdev = S->dsc;
         if (hn2 < STOKES_REORTH_THETA * w2) {
-            CU(vec_multiaxpy(n, ip, Vj(k + 1), S->V, S->ld, k + 1, S->dsc, 1.0, S->dsc + (m + 1), st),
+            TU(PROF_ORTHOG, vec_multiaxpy(n, ip, Vj(k + 1), S->V, S->ld, k + 1, S->dsc, 1.0, S->dsc + (m + 1), st),
                "orthogonalisation");
-            CU(cudaMemcpyAsync(h.data(), S->dsc + (m + 1), sizeof(double) * (k + 2), cudaMemcpyDeviceToHost, st),
+            TU(PROF_TRANSFER, cudaMemcpyAsync(h.data(), S->dsc + (m + 1), sizeof(double) * (k + 2), cudaMemcpyDeviceToHost, st),
                "readback");
             CU(cudaStreamSynchronize(st), "sync");
             hh = 0;
@@ -204,7 +206,7 @@ int fgmres_cycle(stokes_solver* S, bool trans, double tol_rel, int max_its, int&
         double hk1 = std::sqrt(std::max(hn2, 0.0));
         if (!(hk1 > 1e-14 * std::sqrt(w2))) hk1 = 0.0;
         if (hk1 > 0)
-            CU(vec_multiaxpy(n, ip, Vj(k + 1), S->V, S->ld, k + 1, hdev, 1.0 / hk1, nullptr, st),
+            TU(PROF_ORTHOG, vec_multiaxpy(n, ip, Vj(k + 1), S->V, S->ld, k + 1, hdev, 1.0 / hk1, nullptr, st),
                "orthogonalisation");
         // Givens rotations on column k
         for (int i = 0; i < k; ++i) {
@@ -230,8 +232,8 @@ int fgmres_cycle(stokes_solver* S, bool trans, double tol_rel, int max_its, int&
         for (int j = i + 1; j < k; ++j) s -= H[size_t(i) * m + j] * y[j];
         y[i] = s / H[size_t(i) * m + i];
     }
-    CU(cudaMemcpyAsync(S->dsc, y.data(), sizeof(double) * k, cudaMemcpyHostToDevice, st), "coefficients");
-    CU(vec_combine(n, ip, S->Z, S->ld, k, S->dsc, STOKES_F64, S->dl, st), "update");
+    TU(PROF_TRANSFER, cudaMemcpyAsync(S->dsc, y.data(), sizeof(double) * k, cudaMemcpyHostToDevice, st), "coefficients");
+    TU(PROF_VECTOR, vec_combine(n, ip, S->Z, S->ld, k, S->dsc, STOKES_F64, S->dl, st), "update");
     CU(cudaStreamSynchronize(st), "sync");
     return STOKES_OK;
 }
@@ -242,21 +244,21 @@ int fgmres_cycle(stokes_solver* S, bool trans, double tol_rel, int max_its, int&
 int linear_solve(stokes_solver* S, const double* rhs, double nrhs, double eta, bool trans, int& its_total,
                  cudaStream_t st) {
     const int64_t n = S->n;
-    CU(cudaMemsetAsync(S->dl, 0, sizeof(double) * n, st), "clear");
-    CU(vec_axpby(n, 1.0, nullptr, STOKES_F64, rhs, 0.0, STOKES_F64, S->rl, st), "copy");
+    TU(PROF_VECTOR, cudaMemsetAsync(S->dl, 0, sizeof(double) * n, st), "clear");
+    TU(PROF_VECTOR, vec_axpby(n, 1.0, nullptr, STOKES_F64, rhs, 0.0, STOKES_F64, S->rl, st), "copy");
     double nrl = nrhs;
     its_total = 0;
     const double floor_rel = S->inner == STOKES_F32 ? 1e-5 : 1e-13;
     while (its_total < S->o.max_krylov && nrl > eta * nrhs) {
-        CU(vec_axpby(n, 1.0, nullptr, STOKES_F64, S->rl, 0.0, S->inner, S->tin, st), "to inner precision");
+        TU(PROF_VECTOR, vec_axpby(n, 1.0, nullptr, STOKES_F64, S->rl, 0.0, S->inner, S->tin, st), "to inner precision");
         const double tol = std::max(eta * nrhs / nrl, floor_rel);
         int its = 0;
         CK(fgmres_cycle(S, trans, tol, S->o.max_krylov - its_total, its, st));
         its_total += its;
         // FP64 residual of the accumulated update (iterative refinement)
         CK(op64(S, S->dl, S->tmp64, trans, st));
-        CU(vec_axpby(n, 1.0, nullptr, STOKES_F64, rhs, 0.0, STOKES_F64, S->rl, st), "residual");
-        CU(vec_axpby(n, -1.0, nullptr, STOKES_F64, S->tmp64, 1.0, STOKES_F64, S->rl, st), "residual");
+        TU(PROF_VECTOR, vec_axpby(n, 1.0, nullptr, STOKES_F64, rhs, 0.0, STOKES_F64, S->rl, st), "residual");
+        TU(PROF_VECTOR, vec_axpby(n, -1.0, nullptr, STOKES_F64, S->tmp64, 1.0, STOKES_F64, S->rl, st), "residual");
         CK(norm64(S, S->rl, n, nrl, st));
         if (its == 0) break;
     }
@@ -379,7 +381,7 @@ int stokes_newton_solve(stokes_solver* S, const stokes_params* params, double* u
         if (S->st64 != S->st_in) CK(stokes_linearize(S->st64, params, up, st));
         CK(precond_setup(S, params, st));
         // rhs = -r
-        CU(vec_axpby(n, -1.0, nullptr, STOKES_F64, S->r, 0.0, STOKES_F64, S->trial, st), "rhs");
+        TU(PROF_VECTOR, vec_axpby(n, -1.0, nullptr, STOKES_F64, S->r, 0.0, STOKES_F64, S->trial, st), "rhs");
         int its = 0;
         CK(linear_solve(S, S->trial, nr, eta, false, its, st));
         R.krylov_its += its;
@@ -387,8 +389,8 @@ int stokes_newton_solve(stokes_solver* S, const stokes_params* params, double* u
         // backtracking line search on ||r||
         double alpha = 1.0, nrt = 0;
         for (int cut = 0;; ++cut) {
-            CU(vec_axpby(n, 1.0, nullptr, STOKES_F64, up, 0.0, STOKES_F64, S->trial, st), "trial");
-            CU(vec_axpby(n, alpha, nullptr, STOKES_F64, S->dl, 1.0, STOKES_F64, S->trial, st), "trial");
+            TU(PROF_VECTOR, vec_axpby(n, 1.0, nullptr, STOKES_F64, up, 0.0, STOKES_F64, S->trial, st), "trial");
+            TU(PROF_VECTOR, vec_axpby(n, alpha, nullptr, STOKES_F64, S->dl, 1.0, STOKES_F64, S->trial, st), "trial");
             CK(stokes_residual(mesh, params, S->trial, S->rt, STOKES_F64, st));
             CK(norm64(S, S->rt, n, nrt, st));
             if (nrt <= (1.0 - 1e-4 * alpha) * nr || cut >= 12) break;
@@ -401,8 +403,8 @@ int stokes_newton_solve(stokes_solver* S, const stokes_params* params, double* u
             if (rep) *rep = R;
             return fail(STOKES_E_NONFINITE, "non-finite residual after the Newton update (up left at the last iterate)");
         }
-        CU(cudaMemcpyAsync(up, S->trial, sizeof(double) * n, cudaMemcpyDeviceToDevice, st), "update");
-        CU(cudaMemcpyAsync(S->r, S->rt, sizeof(double) * n, cudaMemcpyDeviceToDevice, st), "update");
+        TU(PROF_VECTOR, cudaMemcpyAsync(up, S->trial, sizeof(double) * n, cudaMemcpyDeviceToDevice, st), "update");
+        TU(PROF_VECTOR, cudaMemcpyAsync(S->r, S->rt, sizeof(double) * n, cudaMemcpyDeviceToDevice, st), "update");
         nr_prev = nr;
         nr = nrt;
         if (k + 1 < 64) R.history[k + 1] = nr;
@@ -437,7 +439,7 @@ int stokes_linear_solve(stokes_solver* S, const stokes_params* params, const dou
     if (!std::isfinite(nb)) return fail(STOKES_E_NONFINITE, "the right-hand side is not finite");
     int its = 0;
     CK(linear_solve(S, b, nb, rtol, transpose != 0, its, st));
-    CU(cudaMemcpyAsync(x, S->dl, sizeof(double) * n, cudaMemcpyDeviceToDevice, st), "solution");
+    TU(PROF_VECTOR, cudaMemcpyAsync(x, S->dl, sizeof(double) * n, cudaMemcpyDeviceToDevice, st), "solution");
     double nrl = 0;
     CK(norm64(S, S->rl, n, nrl, st));
     R.krylov_its = its;

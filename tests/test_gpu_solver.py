@@ -168,3 +168,35 @@ def test_picard_iteration_reaches_oracle_solution(inner):
         assert r <= 1e-9 * r0, r / r0
     finally:
         capi.stokes_solver_destroy(s)
+
+
+def test_tracing_records_every_solver_class():
+    """Event tracing of a Newton solve: every class of solver work is
+    recorded, the launch counts follow the iteration counts, and the summed
+    device time does not exceed the wall time of the solve."""
+    import time
+    wl, o, m, lb = _setup("slab_5x3x3_q2p1")
+    p = params(wl.phys, torch.as_tensor(lb, dtype=torch.float64, device="cuda"))
+    s = capi.stokes_solver_create(m.handle, _opts(capi.STOKES_F32))
+    try:
+        up = torch.zeros(o.ndof, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        capi.stokes_profile_begin(m.handle)
+        t0 = time.perf_counter()
+        rc, rep = capi.stokes_newton_solve(s, p, up)
+        torch.cuda.synchronize()
+        wall_ms = (time.perf_counter() - t0) * 1e3
+        pr = capi.stokes_profile_end(m.handle)
+    finally:
+        capi.stokes_solver_destroy(s)
+    assert rc == 0 and rep["converged"]
+    for cls in ("clear", "element", "constraint", "precond", "orthog", "vector", "setup", "transfer"):
+        assert pr[cls][0] > 0 and pr[cls][1] > 0, (cls, pr)
+    # one preconditioner apply (Schur block, update, column solve) per Krylov iteration
+    assert pr["precond"][0] >= 3 * rep["krylov_its"], (pr, rep)
+    # linearisations (two states per Newton step), residuals and applies are element launches
+    assert pr["element"][0] >= 2 * rep["newton_its"] + rep["krylov_its"], (pr, rep)
+    assert sum(v[1] for v in pr.values()) <= wall_ms
+    # tracing is off again: nothing more is recorded
+    capi.stokes_profile_begin(m.handle)
+    assert all(v[0] == 0 for v in capi.stokes_profile_end(m.handle).values())
