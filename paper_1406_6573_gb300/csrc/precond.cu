@@ -6,7 +6,7 @@
 // and 7), so the velocity block is approximated by its vertical-column blocks,
 // each a banded SPD matrix factored exactly (LU without pivoting).  One thread
 // owns one column; band entries are stored column-interleaved so that the
-// threads of a warp touch consecutive addresses.
+// threads of a warp touch consecutive addresses (band_at).
 #include <type_traits>
 
 #include <cuda_runtime.h>
@@ -17,8 +17,8 @@ namespace stokes {
 namespace {
 
 template <typename T>
-__device__ __forceinline__ T& band(T* A, int64_t ncol, int W, int bw, int r, int q, int64_t c) {
-    return A[(int64_t(r) * W + (q - r + bw)) * ncol + c];
+__device__ __forceinline__ T& band(T* A, int rows, int W, int bw, int r, int q, int64_t c) {
+    return A[band_at(c, r, q - r + bw, W, rows)];
 }
 
 template <typename T>
@@ -37,30 +37,30 @@ __global__ void col_factor_kernel(ColSolveArgs a) {
         const int qmax = min(n - 1, 2 + bw);
         for (int q = 0; q <= qmax; ++q) {          // rows 0..2: P K
             T v[3];
-            for (int r = 0; r < 3; ++r) v[r] = (q - r <= bw) ? band(A, a.ncol, W, bw, r, q, c) : T(0);
+            for (int r = 0; r < 3; ++r) v[r] = (q - r <= bw) ? band(A, 3 * a.colmax, W, bw, r, q, c) : T(0);
             for (int r = 0; r < 3; ++r)
-                if (q - r <= bw) band(A, a.ncol, W, bw, r, q, c) = P[r][0] * v[0] + P[r][1] * v[1] + P[r][2] * v[2];
+                if (q - r <= bw) band(A, 3 * a.colmax, W, bw, r, q, c) = P[r][0] * v[0] + P[r][1] * v[1] + P[r][2] * v[2];
         }
         for (int r = 0; r <= qmax; ++r) {          // columns 0..2: K P
             T v[3];
-            for (int q = 0; q < 3; ++q) v[q] = (r - q <= bw) ? band(A, a.ncol, W, bw, r, q, c) : T(0);
+            for (int q = 0; q < 3; ++q) v[q] = (r - q <= bw) ? band(A, 3 * a.colmax, W, bw, r, q, c) : T(0);
             for (int q = 0; q < 3; ++q)
-                if (r - q <= bw) band(A, a.ncol, W, bw, r, q, c) = v[0] * P[0][q] + v[1] * P[1][q] + v[2] * P[2][q];
+                if (r - q <= bw) band(A, 3 * a.colmax, W, bw, r, q, c) = v[0] * P[0][q] + v[1] * P[1][q] + v[2] * P[2][q];
         }
         const T sc = T(a.scale);
         for (int r = 0; r < 3; ++r)
-            for (int q = 0; q < 3; ++q) band(A, a.ncol, W, bw, r, q, c) += sc * ((r == q ? T(1) : T(0)) - P[r][q]);
+            for (int q = 0; q < 3; ++q) band(A, 3 * a.colmax, W, bw, r, q, c) += sc * ((r == q ? T(1) : T(0)) - P[r][q]);
     }
     for (int p = 0; p < n; ++p) {
-        const T piv = band(A, a.ncol, W, bw, p, p, c);
+        const T piv = band(A, 3 * a.colmax, W, bw, p, p, c);
         const T ipiv = T(1) / piv;
         const int rmax = min(n - 1, p + bw);
         for (int r = p + 1; r <= rmax; ++r) {
-            T& lrp = band(A, a.ncol, W, bw, r, p, c);
+            T& lrp = band(A, 3 * a.colmax, W, bw, r, p, c);
             const T l = lrp * ipiv;
             lrp = l;
             if (l != T(0))
-                for (int q = p + 1; q <= rmax; ++q) band(A, a.ncol, W, bw, r, q, c) -= l * band(A, a.ncol, W, bw, p, q, c);
+                for (int q = p + 1; q <= rmax; ++q) band(A, 3 * a.colmax, W, bw, r, q, c) -= l * band(A, 3 * a.colmax, W, bw, p, q, c);
         }
     }
 }
@@ -81,14 +81,14 @@ __global__ void col_solve_kernel(ColSolveArgs a, const T* __restrict__ rhs, T* _
     }
     for (int r = 1; r < n; ++r) {                // L y = r (unit lower)
         T s = zc[r * nt + t];
-        for (int q = max(0, r - bw); q < r; ++q) s -= A[(int64_t(r) * W + (q - r + bw)) * a.ncol + c] * zc[q * nt + t];
+        for (int q = max(0, r - bw); q < r; ++q) s -= A[band_at(c, r, q - r + bw, W, 3 * a.colmax)] * zc[q * nt + t];
         zc[r * nt + t] = s;
     }
     for (int r = n - 1; r >= 0; --r) {           // U x = y
         T s = zc[r * nt + t];
         const int qmax = min(n - 1, r + bw);
-        for (int q = r + 1; q <= qmax; ++q) s -= A[(int64_t(r) * W + (q - r + bw)) * a.ncol + c] * zc[q * nt + t];
-        zc[r * nt + t] = s / A[(int64_t(r) * W + bw) * a.ncol + c];
+        for (int q = r + 1; q <= qmax; ++q) s -= A[band_at(c, r, q - r + bw, W, 3 * a.colmax)] * zc[q * nt + t];
+        zc[r * nt + t] = s / A[band_at(c, r, bw, W, 3 * a.colmax)];
     }
     for (int p = 0; p < len; ++p) {
         const int64_t g = a.col_nodes[int64_t(p) * a.ncol + c];
@@ -116,20 +116,20 @@ __global__ void col_solve_band_kernel(ColSolveArgs a, const T* __restrict__ rhs,
     constexpr int W = 2 * BW + 1;
     constexpr int R = CS_AHEAD + 1;
     const int64_t ncol = a.ncol;
-    const T* A = static_cast<const T*>(a.A) + c;
+    const T* A = static_cast<const T*>(a.A) + band_at(c, 0, 0, W, 3 * a.colmax);
     const int len = a.col_len[c], n = 3 * len;
     for (int p = 0; p < len; ++p) {
         const int64_t g = a.col_nodes[int64_t(p) * ncol + c];
         for (int k = 0; k < 3; ++k) zc[(3 * p + k) * nt + t] = rhs[3 * g + k];
     }
     if (n == 0) return;
-    auto row = [&](int r) { return A + int64_t(r) * W * ncol; };
+    auto row = [&](int r) { return A + int64_t(r) * W * BAND_CB; };
     // L y = r (unit lower): row r holds L[r][r - d] at band slot BW - d;
     // row r lives in ring slot r mod R
     T L[R][BW];
     auto loadL = [&](int r, T (&dst)[BW]) {
         #pragma unroll
-        for (int d = 1; d <= BW; ++d) dst[d - 1] = (r < n && r - d >= 0) ? row(r)[(BW - d) * ncol] : T(0);
+        for (int d = 1; d <= BW; ++d) dst[d - 1] = (r < n && r - d >= 0) ? row(r)[(BW - d) * BAND_CB] : T(0);
     };
     #pragma unroll
     for (int u = 1; u < R; ++u) loadL(u, L[u]);
@@ -152,7 +152,7 @@ __global__ void col_solve_band_kernel(ColSolveArgs a, const T* __restrict__ rhs,
     T U[R][BW + 1];
     auto loadU = [&](int r, T (&dst)[BW + 1]) {
         #pragma unroll
-        for (int d = 0; d <= BW; ++d) dst[d] = (r >= 0 && r + d < n) ? row(r)[(BW + d) * ncol] : T(0);
+        for (int d = 0; d <= BW; ++d) dst[d] = (r >= 0 && r + d < n) ? row(r)[(BW + d) * BAND_CB] : T(0);
     };
     #pragma unroll
     for (int u = 0; u < R - 1; ++u) loadU(n - 1 - u, U[u]);
@@ -240,7 +240,7 @@ __global__ void col_diag_kernel(ColSolveArgs a, double* out) {
     if (c < a.ncol) {
         const T* A = static_cast<const T*>(a.A);
         const int W = 2 * a.bw + 1, n = 3 * a.col_len[c];
-        for (int r = 0; r < n; ++r) s += fabs(double(A[(int64_t(r) * W + a.bw) * a.ncol + c]));
+        for (int r = 0; r < n; ++r) s += fabs(double(A[band_at(c, r, a.bw, W, 3 * a.colmax)]));
     }
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;

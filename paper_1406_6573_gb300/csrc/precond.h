@@ -15,6 +15,16 @@
 
 namespace stokes {
 
+// Banded column matrices: entry (row r, band slot s) of column c, with the
+// columns in blocks of BAND_CB; a block holds its rows and slots contiguously
+// ([ncol / BAND_CB][rows][W][BAND_CB], ncol rounded up to BAND_CB), so that
+// one warp's columns read one contiguous run of W BAND_CB values per row.
+constexpr int BAND_CB = 32;
+__host__ __device__ inline int64_t band_at(int64_t c, int r, int s, int W, int rows) {
+    return ((c / BAND_CB) * (int64_t(rows) * W) + int64_t(r) * W + s) * BAND_CB + (c % BAND_CB);
+}
+__host__ __device__ inline int64_t band_cols(int64_t ncol) { return (ncol + BAND_CB - 1) / BAND_CB * BAND_CB; }
+
 struct ColArgs {
     int64_t E, ncol;
     int npr, pspace, bw, robin;
@@ -27,6 +37,7 @@ struct ColArgs {
     const int32_t* fmap;       // [nF][n1^2]
     const double* fgeo;        // [nF][4][q^2]
     const double* logbeta;     // [Nb]
+    int rows;                  // rows of the band matrices (3 colmax)
     const void* state;         // linearised state (element type = prec)
     int state_cpl;             // the state is in the group layout of k = 2 FP32 states
     void* A;                   // [3 colmax][2 bw + 1][ncol] banded column matrices

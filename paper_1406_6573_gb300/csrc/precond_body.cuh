@@ -104,7 +104,7 @@ __global__ void __launch_bounds__(256) colblock_kernel(ColArgs a) {
             #pragma unroll
             for (int c2 = 0; c2 < 3; ++c2) {
                 const int r = 3 * pa + c, q = 3 * pb + c2;
-                atomic_add(A + (int64_t(r) * W + (q - r + bw)) * a.ncol + col, Kab[c][c2]);
+                atomic_add(A + band_at(col, r, q - r + bw, W, a.rows), Kab[c][c2]);
             }
     }
 }

@@ -113,6 +113,7 @@ int precond_setup(stokes_solver* S, const stokes_params* p, cudaStream_t st, dou
     TU(PROF_SETUP, cudaMemsetAsync(S->A, 0, S->band_elems * S->isz, st), "clearing column blocks");
     ColArgs a{};
     a.E = m->h.E; a.ncol = m->h.ncol; a.npr = m->h.npr; a.pspace = m->h.pspace; a.bw = S->bw;
+    a.rows = 3 * m->h.colmax;
     a.robin = p->robin && m->h.nF > 0;
     a.nodes = m->d_nodes; a.hang = m->d_hang; a.col_of = m->d_col_of; a.pos_of = m->d_pos_of;
     a.fidx = m->d_fidx; a.fmap = m->d_fmap; a.fgeo = m->d_fgeo; a.logbeta = p->logbeta;
@@ -301,7 +302,7 @@ int stokes_solver_create(const stokes_mesh* mesh, const stokes_solver_opts* opts
         else rc = stokes_state_create(mesh, STOKES_F64, &S->st64);
     }
     const size_t n = size_t(S->n);
-    S->band_elems = size_t(3) * mesh->h.colmax * size_t(2 * S->bw + 1) * size_t(mesh->h.ncol);
+    S->band_elems = size_t(3) * mesh->h.colmax * size_t(2 * S->bw + 1) * size_t(band_cols(mesh->h.ncol));
     auto alloc = [&](void** p, size_t bytes) {
         if (rc) return;
         if (cudaMalloc(p, bytes) != cudaSuccess) { *p = nullptr; rc = fail(STOKES_E_NOMEM, "solver workspace"); }
