@@ -22,6 +22,13 @@ factorisation, no fusion):
   solution does not depend on s).
   beta = exp(log beta) with log beta the basal nodal field interpolated by
   the face basis.
+  basal sliding (Eq. 2.3: the traction T(sigma n) balances a function of
+  |T u|; the linear law beta T u is Eq. 2.4a): traction
+      beta s(|T u|^2) T u,   s(x) = (x + eps_s)^{(m-1)/2},
+  m = phys.sliding_m, eps_s = phys.sliding_eps; s = 1 for m = 1 (the linear
+  law, exactly).  Its Newton derivative in the direction w is
+      beta (s T w + 2 s'(|T u|^2) (T u . T w) T u),
+  the Picard form keeps s and drops s'.
 
 Every function accepts complex arrays (only analytic operations are used), so
 complex-step derivatives of the residual are available to the tests.
@@ -113,6 +120,15 @@ def _tang(n, v):
     return v - n * np.einsum("eqc,eqc->eq", n, v)[..., None]
 
 
+def _sliding(phys, tu):
+    """s and ds/dx at x = |T u|^2 of the sliding law (s = 1, ds = 0 when m = 1)."""
+    m = phys.sliding_m
+    if m == 1.0:
+        return 1.0, 0.0
+    x = np.einsum("eqc,eqc->eq", tu, tu) + phys.sliding_eps
+    return x ** (0.5 * (m - 1.0)), 0.5 * (m - 1.0) * x ** (0.5 * (m - 3.0))
+
+
 def element_residual(mesh, phys, ue, pe, logbeta, body=True):
     """Unconstrained element residual vectors (velocity (E,A,3), pressure (E,npr))."""
     dt = np.result_type(ue, pe, logbeta, phys.A, np.float64)
@@ -134,7 +150,9 @@ def element_residual(mesh, phys, ue, pe, logbeta, body=True):
         rp[sl] = -np.einsum("qb,eq->eb", mesh.Psi, div * mesh.wdetJ[sl])
     if phys.robin:
         eb, bw, n, uf = _face_terms(mesh, phys, ue, logbeta)
-        t = _tang(n, uf) * bw[..., None]
+        tu = _tang(n, uf)
+        s, _ = _sliding(phys, tu)
+        t = tu * (bw * s)[..., None]
         rv[eb] += np.einsum("qa,eqc->eac", mesh.phiF, t)
     return rv, rp
 
@@ -164,7 +182,14 @@ def element_jacobian(mesh, phys, ue, we, qe, logbeta):
         yp[sl] = -np.einsum("qb,eq->eb", mesh.Psi, div * mesh.wdetJ[sl])
     if phys.robin:
         eb, bw, n, wf = _face_terms(mesh, phys, we, logbeta)
-        t = _tang(n, wf) * bw[..., None]
+        tw = _tang(n, wf)
+        t = tw * bw[..., None]
+        if phys.sliding_m != 1.0:
+            tu = _tang(n, np.einsum("qa,eac->eqc", mesh.phiF, ue[eb]))
+            s, ds = _sliding(phys, tu)
+            if phys.linearization == "picard":
+                ds = 0.0 * ds
+            t = bw[..., None] * (s[..., None] * tw + (2.0 * ds * np.einsum("eqc,eqc->eq", tu, tw))[..., None] * tu)
         yv[eb] += np.einsum("qa,eqc->eac", mesh.phiF, t)
     return yv, yp
 
@@ -204,7 +229,7 @@ def param_grad(mesh, phys, up, lam, logbeta=None):
     """Adjoint products with the parameter Jacobians of r_c.
 
     g_logbeta[j] = lam^T d r_c / d log(beta_j)
-                 = int_{Gamma_b} beta phi_j (T P lam) . (T P u) ds
+                 = int_{Gamma_b} beta s(|T P u|^2) phi_j (T P lam) . (T P u) ds
     g_A          = lam^T d r_c / d A = -(1/(n A)) int mu(P u) D(P lam) : D(P u) dx
     (d mu / d A = -mu / (n A) because C = C0 A^{-1/n}).
     """
@@ -225,7 +250,9 @@ def param_grad(mesh, phys, up, lam, logbeta=None):
     if phys.robin:
         eb, bw, n, uf = _face_terms(mesh, phys, ue, logbeta)
         lf = np.einsum("qa,eac->eqc", mesh.phiF, le[eb])
-        s = bw * np.einsum("eqc,eqc->eq", _tang(n, lf), _tang(n, uf))
+        tu = _tang(n, uf)
+        sl_s, _ = _sliding(phys, tu)
+        s = bw * sl_s * np.einsum("eqc,eqc->eq", _tang(n, lf), tu)
         full = np.zeros((mesh.E, mesh.A), dtype=g.dtype)
         full[eb] = np.einsum("qa,eq->ea", mesh.phiF, s)
         g = scatter(mesh, full)[mesh.basal]
@@ -236,7 +263,9 @@ def energy(mesh, phys, u, logbeta=None):
     """Convex energy whose gradient is the velocity residual (Appendix A).
 
     E(u) = int C / (2 gamma (1 + p_n)) (gamma D:D + delta)^{1 + p_n} dx
-           + 1/2 int_{Gamma_b} beta |T u|^2 ds - int b . u dx
+           + int_{Gamma_b} beta F(|T u|^2) ds - int b . u dx,
+    F(x) = x / 2 for the linear sliding law (m = 1), else
+    F(x) = (x + eps_s)^{(m+1)/2} / (m + 1), so that 2 F'(x) = s(x)
     (unconstrained, velocity only; u has shape (Nv, 3)).
     """
     logbeta = _logbeta(mesh, phys, logbeta)
@@ -255,5 +284,10 @@ def energy(mesh, phys, u, logbeta=None):
     if phys.robin:
         eb, bw, n, uf = _face_terms(mesh, phys, ue, logbeta)
         tu = _tang(n, uf)
-        total = total + 0.5 * np.sum(bw * np.einsum("eqc,eqc->eq", tu, tu))
+        x = np.einsum("eqc,eqc->eq", tu, tu)
+        if phys.sliding_m == 1.0:
+            total = total + 0.5 * np.sum(bw * x)
+        else:
+            m = phys.sliding_m
+            total = total + np.sum(bw * (x + phys.sliding_eps) ** (0.5 * (m + 1.0)) / (m + 1.0))
     return total

@@ -31,6 +31,10 @@ class PhysParams:
     logbeta: ModalField = None
     constraint_scale: float = 1.0   # s of the constraint rows s (I - P)
     linearization: str = "newton"   # Jacobian: 'newton' (Eq. 2.7) or 'picard' (viscosity frozen)
+    # basal sliding law: traction beta (|T u|^2 + sliding_eps)^((m - 1)/2) T u,
+    # m = sliding_m; m = 1 is the linear law beta T u of Eq. 2.4a
+    sliding_m: float = 1.0
+    sliding_eps: float = 1.0e-4
 
     def viscosity_prefactor(self):
         return self.C0 * self.A ** (-1.0 / self.n)
