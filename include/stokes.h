@@ -123,6 +123,17 @@ typedef struct {
                                      derivative of mu.  Affects the Jacobian
                                      applies, stokes_linearize and the solver
                                      (a Picard iteration); not the residual. */
+    double sliding_m;             /* basal sliding law: the Robin traction is
+                                     beta s(|T u|^2) T u with
+                                     s(x) = (x + sliding_eps)^((m-1)/2), a
+                                     Weertman-type power law (Eq. 2.3 leaves
+                                     the dependence on |T u| open); 0 or 1:
+                                     the linear law beta T u of Eq. 2.4a.
+                                     Otherwise m > 0 and sliding_eps > 0.  The
+                                     Newton Jacobian adds
+                                     2 beta s'(|T u|^2) (T u . T w) T u (the
+                                     Picard form keeps s and drops it). */
+    double sliding_eps;           /* regularisation of |T u|^2 (velocity^2)   */
 } stokes_params;
 
 #define STOKES_LIN_NEWTON 0

@@ -46,7 +46,7 @@ class stokes_params(C.Structure):
     _fields_ = [("n", C.c_double), ("A", C.c_double), ("C0", C.c_double),
                 ("gamma", C.c_double), ("delta", C.c_double), ("body", C.c_double * 3),
                 ("robin", C.c_int), ("logbeta", C.c_void_p), ("constraint_scale", C.c_double),
-                ("linearization", C.c_int)]
+                ("linearization", C.c_int), ("sliding_m", C.c_double), ("sliding_eps", C.c_double)]
 
 
 STOKES_LIN_NEWTON = 0

@@ -133,6 +133,8 @@ int check_params(const stokes_mesh* m, const stokes_params* p) {
         return fail(STOKES_E_INVAL, "params: need n >= 1, A > 0, C0 > 0, gamma > 0, delta > 0");
     if (p->robin && !p->logbeta && m->h.Nb > 0) return fail(STOKES_E_INVAL, "params: robin = 1 needs logbeta");
     if (!(p->constraint_scale > 0)) return fail(STOKES_E_INVAL, "params: constraint_scale must be > 0");
+    if (sliding_nonlinear(p) && !(p->sliding_m > 0 && p->sliding_eps > 0))
+        return fail(STOKES_E_INVAL, "params: the sliding law needs sliding_m > 0 and sliding_eps > 0");
     return STOKES_OK;
 }
 
@@ -163,6 +165,12 @@ FaceArgs face_args(const stokes_mesh* m, const stokes_params* p) {
     f.face_elem = m->d_face_elem; f.nodes = m->d_nodes; f.hang = m->d_hang;
     f.pidx = m->d_pidx; f.pel = m->d_pel; f.fgeo = m->d_fgeo; f.fmap = m->d_fmap;
     f.logbeta = p ? p->logbeta : nullptr;
+    if (sliding_nonlinear(p)) {
+        f.slide = 1;
+        f.slide_m = p->sliding_m;
+        f.slide_eps = p->sliding_eps;
+        f.slide_picard = p->linearization == STOKES_LIN_PICARD;
+    }
     return f;
 }
 
@@ -172,7 +180,7 @@ size_t vec_bytes(const stokes_mesh* m, int prec) {
 
 int operator_sequence(const stokes_mesh* m, const stokes_params* p, int mode, int prec, int state_prec,
                       bool trans, const void* x, const void* u, const void* cstate, void* y, cudaStream_t s,
-                      int state_cpl) {
+                      int state_cpl, const void* fstate) {
     int e = timed(m, 0, s, [&] { return int(cudaMemsetAsync(y, 0, vec_bytes(m, prec), s)); });
     if (e) return cuda_fail(cudaError_t(e), "clearing the output");
     ElemArgs a = elem_args(m, p);
@@ -184,6 +192,7 @@ int operator_sequence(const stokes_mesh* m, const stokes_params* p, int mode, in
         // constraint rows (one launch per apply)
         a.face = face_args(m, p);
         a.face.x = x; a.face.y = y;
+        a.face.fstate = fstate;   // the sliding law linearised with the state
         a.fuse_robin = robin;
         a.fuse_constraint = 1;
         a.Nb = m->h.Nb; a.basal_nodes = m->d_basal_nodes; a.basal_P = m->d_basal_P;
@@ -196,6 +205,7 @@ int operator_sequence(const stokes_mesh* m, const stokes_params* p, int mode, in
     if (robin) {
         FaceArgs f = face_args(m, p);
         f.x = x; f.y = y;
+        f.ulin = u;               // fused Jacobian: the linearisation point; residual: NULL (u = x)
         e = timed(m, 2, s, [&] { return launch_face(m->h.k, FACE_APPLY, prec, f, s); });
         if (e) return cuda_fail(cudaError_t(e), "basal face kernel launch");
     }
@@ -443,6 +453,15 @@ int stokes_state_create(const stokes_mesh* mesh, int prec, stokes_state** out) {
         delete st;
         return fail(STOKES_E_CUDA, "clearing the linearised state failed");
     }
+    if (mesh->h.nF > 0) {
+        const int q = mesh->h.k + 1;
+        const size_t fbytes = size_t(mesh->h.nF) * SLIDE_FIELDS * q * q * (prec == STOKES_F32 ? 4 : 8);
+        if (cudaMalloc(&st->d_fstate, fbytes) != cudaSuccess) {
+            cudaFree(st->d_state);
+            delete st;
+            return fail(STOKES_E_NOMEM, "cudaMalloc of the sliding state failed");
+        }
+    }
     *out = st;
     return STOKES_OK;
 }
@@ -451,6 +470,7 @@ int stokes_state_destroy(stokes_state* state) {
     if (!state) return STOKES_OK;
     DeviceGuard g(state->mesh->device);
     if (state->d_state) cudaFree(state->d_state);
+    if (state->d_fstate) cudaFree(state->d_fstate);
     delete state;
     return STOKES_OK;
 }
@@ -473,6 +493,15 @@ int stokes_linearize(stokes_state* state, const stokes_params* params, const dou
         return launch_elem(mesh->h.k, MODE_LINEARIZE, STOKES_F64, state->prec, false, a, s);
     });
     if (e) return cuda_fail(cudaError_t(e), "linearize kernel launch");
+    state->slide = sliding_nonlinear(params) && mesh->h.nF > 0;
+    if (state->slide) {
+        FaceArgs f = face_args(mesh, params);
+        f.u = up_lin;
+        f.fstate_out = state->d_fstate;
+        f.fstate_f32 = state->prec == STOKES_F32;
+        e = timed(mesh, PROF_FACE, s, [&] { return launch_face(mesh->h.k, FACE_LINEARIZE, STOKES_F64, f, s); });
+        if (e) return cuda_fail(cudaError_t(e), "sliding linearisation kernel launch");
+    }
     state->params = *params;
     state->linearized = true;
     return STOKES_OK;
@@ -490,7 +519,8 @@ static int state_apply_common(const stokes_state* state, const void* x, void* y,
     DeviceGuard g(mesh->device);
     if (g.err != cudaSuccess) return cuda_fail(g.err, "selecting the device");
     return operator_sequence(mesh, &state->params, mode, state->prec, state->prec, trans, x,
-                             nullptr, state->d_state, y, static_cast<cudaStream_t>(stream), state->cpl);
+                             nullptr, state->d_state, y, static_cast<cudaStream_t>(stream), state->cpl,
+                             state->slide ? state->d_fstate : nullptr);
 }
 
 int stokes_state_apply(const stokes_state* state, const void* x, void* y, void* stream) {

@@ -395,6 +395,14 @@ __device__ __forceinline__ void face_group(const FaceArgs& a, const LaneMap& L, 
     }
     const T bw = exp(lbq[0]) * wa;
 
+    // sliding law factor s(x) = (x + eps)^((m - 1)/2) and its derivative
+    auto slide_s = [&](T x2, T& ds) -> T {
+        const T xe = x2 + T(a.slide_eps);
+        const T sv = pow(xe, T(0.5) * (T(a.slide_m) - T(1)));
+        ds = a.slide_picard ? T(0) : T(0.5) * (T(a.slide_m) - T(1)) * sv / xe;
+        return sv;
+    };
+
     if constexpr (MODE == FACE_APPLY) {
         T v[3];
         face_gather<T>(a, static_cast<const T*>(a.x), e, active, ij, v);
@@ -402,7 +410,40 @@ __device__ __forceinline__ void face_group(const FaceArgs& a, const LaneMap& L, 
         T vq[3];
         face_interp<T, 3>(R, v, vq, i, j, sb);
         const T nv = n0 * vq[0] + n1 * vq[1] + n2 * vq[2];
-        T t[3] = {bw * (vq[0] - nv * n0), bw * (vq[1] - nv * n1), bw * (vq[2] - nv * n2)};
+        const T tw[3] = {vq[0] - nv * n0, vq[1] - nv * n1, vq[2] - nv * n2};
+        T t[3] = {bw * tw[0], bw * tw[1], bw * tw[2]};
+        if (a.slide) {
+            if (a.fstate) {
+                // stored linearisation: beta w s T w + (v . w) T u
+                if (active) {
+                    const T* sst = static_cast<const T*>(a.fstate) + f * SLIDE_FIELDS * Q2 + fq;
+                    const T bws = sst[0];
+                    const T vw = sst[Q2] * vq[0] + sst[2 * Q2] * vq[1] + sst[3 * Q2] * vq[2];
+                    #pragma unroll
+                    for (int c = 0; c < 3; ++c) t[c] = bws * tw[c] + vw * sst[(4 + c) * Q2];
+                }
+            } else if (a.ulin) {
+                // Jacobian at u: beta w (s T w + 2 s' (T u . T w) T u)
+                T uu[3];
+                face_gather<T>(a, static_cast<const T*>(a.ulin), e, active, ij, uu);
+                if (any_h) face_hanging<T, 3, false>(uu, h, active, i, j, sb);
+                T uq[3];
+                face_interp<T, 3>(R, uu, uq, i, j, sb);
+                const T nu = n0 * uq[0] + n1 * uq[1] + n2 * uq[2];
+                const T tu[3] = {uq[0] - nu * n0, uq[1] - nu * n1, uq[2] - nu * n2};
+                T ds;
+                const T sv = slide_s(tu[0] * tu[0] + tu[1] * tu[1] + tu[2] * tu[2], ds);
+                const T r = T(2) * ds * (tu[0] * tw[0] + tu[1] * tw[1] + tu[2] * tw[2]);
+                #pragma unroll
+                for (int c = 0; c < 3; ++c) t[c] = bw * (sv * tw[c] + r * tu[c]);
+            } else {
+                // residual (u = x): beta w s T u
+                T ds;
+                const T sv = slide_s(tw[0] * tw[0] + tw[1] * tw[1] + tw[2] * tw[2], ds);
+                #pragma unroll
+                for (int c = 0; c < 3; ++c) t[c] = bw * sv * tw[c];
+            }
+        }
         T o[3];
         face_interp_T<T, 3>(R, t, o, i, j, sb);
         if (any_h) face_hanging<T, 3, true>(o, h, active, i, j, sb);
@@ -415,8 +456,29 @@ __device__ __forceinline__ void face_group(const FaceArgs& a, const LaneMap& L, 
             atomic_add(y + 3 * g + 1, o[1]);
             atomic_add(y + 3 * g + 2, o[2]);
         }
+    } else if constexpr (MODE == FACE_LINEARIZE) {
+        // stored sliding state at the linearisation point a.u (FP64 arithmetic)
+        T v[3];
+        face_gather<T>(a, a.u, e, active, ij, v);
+        if (any_h) face_hanging<T, 3, false>(v, h, active, i, j, sb);
+        T uq[3];
+        face_interp<T, 3>(R, v, uq, i, j, sb);
+        const T nu = n0 * uq[0] + n1 * uq[1] + n2 * uq[2];
+        const T tu[3] = {uq[0] - nu * n0, uq[1] - nu * n1, uq[2] - nu * n2};
+        T ds;
+        const T sv = slide_s(tu[0] * tu[0] + tu[1] * tu[1] + tu[2] * tu[2], ds);
+        const T vals[SLIDE_FIELDS] = {bw * sv, T(2) * ds * bw * tu[0], T(2) * ds * bw * tu[1],
+                                      T(2) * ds * bw * tu[2], tu[0], tu[1], tu[2]};
+        if (active) {
+            const int64_t o0 = f * SLIDE_FIELDS * Q2 + fq;
+            #pragma unroll
+            for (int c = 0; c < SLIDE_FIELDS; ++c) {
+                if (a.fstate_f32) static_cast<float*>(a.fstate_out)[o0 + c * Q2] = float(vals[c]);
+                else static_cast<double*>(a.fstate_out)[o0 + c * Q2] = double(vals[c]);
+            }
+        }
     } else {
-        // g_j += int beta phi_j (T lambda) . (T u) ds
+        // g_j += int beta s(|T u|^2) phi_j (T lambda) . (T u) ds
         T v[3], w[3];
         face_gather<T>(a, a.u, e, active, ij, v);
         face_gather<T>(a, a.lam, e, active, ij, w);
@@ -429,8 +491,13 @@ __device__ __forceinline__ void face_group(const FaceArgs& a, const LaneMap& L, 
         face_interp<T, 3>(R, w, wq, i, j, sb);
         const T nu = n0 * vq[0] + n1 * vq[1] + n2 * vq[2];
         const T nl = n0 * wq[0] + n1 * wq[1] + n2 * wq[2];
-        const T s = bw * ((vq[0] - nu * n0) * (wq[0] - nl * n0) + (vq[1] - nu * n1) * (wq[1] - nl * n1) +
-                          (vq[2] - nu * n2) * (wq[2] - nl * n2));
+        const T tu[3] = {vq[0] - nu * n0, vq[1] - nu * n1, vq[2] - nu * n2};
+        T sl = T(1);
+        if (a.slide) {
+            T ds;
+            sl = slide_s(tu[0] * tu[0] + tu[1] * tu[1] + tu[2] * tu[2], ds);
+        }
+        const T s = bw * sl * (tu[0] * (wq[0] - nl * n0) + tu[1] * (wq[1] - nl * n1) + tu[2] * (wq[2] - nl * n2));
         T sv[1] = {s}, o[1];
         face_interp_T<T, 1>(R, sv, o, i, j, sb);
         if (any_h) face_hanging<T, 1, true>(o, h, active, i, j, sb);
@@ -800,6 +867,7 @@ inline int launch_elem_any(int mode, int prec, int state_prec, bool trans, const
 
 inline int launch_face_any(int mode, int prec, const FaceArgs& a, cudaStream_t s) {
     if (mode == FACE_GRAD_LOGBETA) return launch_face_t<double, FACE_GRAD_LOGBETA>(a, s);
+    if (mode == FACE_LINEARIZE) return launch_face_t<double, FACE_LINEARIZE>(a, s);
     return prec == 1 ? launch_face_t<float, FACE_APPLY>(a, s) : launch_face_t<double, FACE_APPLY>(a, s);
 }
 

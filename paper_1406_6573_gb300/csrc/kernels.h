@@ -46,10 +46,22 @@ struct FaceArgs {
     const double* logbeta;     // [Nb]
     const void* x;             // vector whose basal trace enters beta T x
     void* y;                   // output (accumulated)
-    const double* u;           // gradient: state
+    const double* u;           // gradient, linearisation: state (FP64)
     const double* lam;         // gradient: adjoint
     double* g;                 // gradient output [Nb] (accumulated)
+    // nonlinear sliding law (slide = 1): traction beta s(|T u|^2) T u,
+    // s(x) = (x + slide_eps)^((slide_m - 1)/2)
+    int slide, slide_picard;
+    double slide_m, slide_eps;
+    const void* ulin;          // apply: linearisation point u (type of x); NULL: the residual (u = x)
+    const void* fstate;        // apply: stored sliding state [nF][7][q^2] (type of x), used when set
+    void* fstate_out;          // linearisation output (fstate_f32: float, else double)
+    int fstate_f32;
 };
+// stored sliding state per basal Gauss point: beta w s, then
+// v = 2 beta w s' T u (3) and T u (3): the Jacobian's face term on w is
+// beta w s T w + (v . w) T u
+constexpr int SLIDE_FIELDS = 7;
 
 struct ElemArgs {
     int64_t E, Nv;
@@ -91,7 +103,7 @@ struct ElemArgs {
 };
 
 
-enum FaceMode : int { FACE_APPLY = 0, FACE_GRAD_LOGBETA = 1 };
+enum FaceMode : int { FACE_APPLY = 0, FACE_GRAD_LOGBETA = 1, FACE_LINEARIZE = 2 };
 
 // Per-degree launchers (one translation unit per degree).  prec: 0 f64, 1 f32.
 // Return a cudaError_t value.

@@ -38,6 +38,7 @@ struct ColArgs {
     const double* fgeo;        // [nF][4][q^2]
     const double* logbeta;     // [Nb]
     int rows;                  // rows of the band matrices (3 colmax)
+    const void* fstate;        // stored sliding state of the state (NULL: linear sliding law)
     const void* state;         // linearised state (element type = prec)
     int state_cpl;             // the state is in the group layout of k = 2 FP32 states
     void* A;                   // [3 colmax][2 bw + 1][ncol] banded column matrices

@@ -91,7 +91,11 @@ __global__ void __launch_bounds__(256) colblock_kernel(ColArgs a) {
                             lbq += Tab<T>::B(iq, i2) * Tab<T>::B(jq, j2) * T(a.logbeta[a.fmap[fcs * N2 + i2 + N1 * j2]]);
                     const double* fg = a.fgeo + fcs * 4 * Q * Q + fq;
                     const T phi = Tab<T>::B(iq, i) * Tab<T>::B(jq, j);
-                    const T w = exp(lbq) * T(fg[0]) * phi * phi;
+                    // nonlinear sliding: beta w s from the stored sliding state
+                    // (the rank-one term of its derivative is left out here)
+                    const T bws = a.fstate ? static_cast<const T*>(a.fstate)[fcs * SLIDE_FIELDS * Q * Q + fq]
+                                           : exp(lbq) * T(fg[0]);
+                    const T w = bws * phi * phi;
                     const T n[3] = {T(fg[Q * Q]), T(fg[2 * Q * Q]), T(fg[3 * Q * Q])};
                     #pragma unroll
                     for (int c = 0; c < 3; ++c)

@@ -114,6 +114,7 @@ int precond_setup(stokes_solver* S, const stokes_params* p, cudaStream_t st, dou
     ColArgs a{};
     a.E = m->h.E; a.ncol = m->h.ncol; a.npr = m->h.npr; a.pspace = m->h.pspace; a.bw = S->bw;
     a.rows = 3 * m->h.colmax;
+    a.fstate = S->st_in->slide ? S->st_in->d_fstate : nullptr;
     a.robin = p->robin && m->h.nF > 0;
     a.nodes = m->d_nodes; a.hang = m->d_hang; a.col_of = m->d_col_of; a.pos_of = m->d_pos_of;
     a.fidx = m->d_fidx; a.fmap = m->d_fmap; a.fgeo = m->d_fgeo; a.logbeta = p->logbeta;

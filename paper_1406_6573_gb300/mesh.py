@@ -92,6 +92,8 @@ def params(phys, logbeta=None, constraint_scale=None):
     p._logbeta_tensor = logbeta
     p.constraint_scale = phys.constraint_scale if constraint_scale is None else constraint_scale
     p.linearization = capi.STOKES_LIN_PICARD if phys.linearization == "picard" else capi.STOKES_LIN_NEWTON
+    p.sliding_m = getattr(phys, "sliding_m", 1.0)
+    p.sliding_eps = getattr(phys, "sliding_eps", 1.0e-4)
     return p
 
 
