@@ -38,7 +38,7 @@ STATE_FIELDS = 11
 # DRAM bytes (read + write) of one launch of the stored-state apply kernel,
 # from the ncu capture summarised under profiles/ for that workload; only
 # valid for the kernel source that capture was taken from.
-STATE_APPLY_TRAFFIC = {"slab_128x128x8_q2p1": 210132992 + 9590784}
+STATE_APPLY_TRAFFIC = {"slab_128x128x8_q2p1": 210148608 + 10277120}
 
 
 def state_stride(k):
