@@ -96,3 +96,42 @@ def test_wrong_energy_constant_is_caught(cmesh, monkeypatch):
     bad = dataclasses.replace(phys, gamma=2.0 * phys.gamma)   # energy with the wrong gamma
     dE = stokes.energy(m, bad, u + 1j * H * w, lb).imag / H
     assert abs(dE - ref) > 1e-6 * abs(ref)
+
+
+# ------------------------------------------------------ nonlinear sliding
+def _sliding_mesh():
+    wl = synth.workload("slab_5x3x3_q2p1")
+    return OracleMesh(dataclasses.replace(wl, phys=dataclasses.replace(wl.phys, sliding_m=1.0 / 3.0)))
+
+
+def _sliding_cs_error(m):
+    lb = np.zeros(m.Nb) if m.wl.phys.logbeta is None else m.wl.phys.logbeta(*m.basal_coords()[:, :2].T)
+    up = synth.uniform_vector(1, m.ndof)
+    x = synth.uniform_vector(1, m.ndof, stream=1)
+    y = stokes.jacobian_apply(m, m.wl.phys, up, x, lb)
+    yc = stokes.residual(m, m.wl.phys, up + 1j * H * x, lb).imag / H
+    return np.linalg.norm(y - yc) / np.linalg.norm(yc)
+
+
+def test_sliding_derivative_without_its_factor_two_is_caught(monkeypatch):
+    m = _sliding_mesh()
+    assert _sliding_cs_error(m) < 1e-13
+    good = stokes._sliding
+    monkeypatch.setattr(stokes, "_sliding", lambda phys, tu: (good(phys, tu)[0], 0.5 * good(phys, tu)[1]))
+    assert _sliding_cs_error(m) > 1e-6
+
+
+def test_sliding_exponent_without_the_half_is_caught(monkeypatch):
+    """s(x) = (x + eps)^(m - 1) instead of (x + eps)^((m - 1)/2): the closed
+    form of uniform sliding fails."""
+    from tests.test_oracle_sliding import test_uniform_sliding_flow_closed_form as closed_form
+    closed_form(1.0 / 3.0, 1.7)
+
+    def wrong(phys, tu):
+        x = np.einsum("eqc,eqc->eq", tu, tu) + phys.sliding_eps
+        mm = phys.sliding_m
+        return x ** (mm - 1.0), (mm - 1.0) * x ** (mm - 2.0)
+
+    monkeypatch.setattr(stokes, "_sliding", wrong)
+    with pytest.raises(AssertionError):
+        closed_form(1.0 / 3.0, 1.7)
