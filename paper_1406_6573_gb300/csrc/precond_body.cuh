@@ -91,16 +91,20 @@ __global__ void __launch_bounds__(256) colblock_kernel(ColArgs a) {
                             lbq += Tab<T>::B(iq, i2) * Tab<T>::B(jq, j2) * T(a.logbeta[a.fmap[fcs * N2 + i2 + N1 * j2]]);
                     const double* fg = a.fgeo + fcs * 4 * Q * Q + fq;
                     const T phi = Tab<T>::B(iq, i) * Tab<T>::B(jq, j);
-                    // nonlinear sliding: beta w s from the stored sliding state
-                    // (the rank-one term of its derivative is left out here)
-                    const T bws = a.fstate ? static_cast<const T*>(a.fstate)[fcs * SLIDE_FIELDS * Q * Q + fq]
-                                           : exp(lbq) * T(fg[0]);
+                    // nonlinear sliding: beta w s and the rank-one term
+                    // v (T u)^T of its derivative from the stored sliding state
+                    const T* sst = a.fstate ? static_cast<const T*>(a.fstate) + fcs * SLIDE_FIELDS * Q * Q + fq
+                                            : nullptr;
+                    const T bws = sst ? sst[0] : exp(lbq) * T(fg[0]);
                     const T w = bws * phi * phi;
                     const T n[3] = {T(fg[Q * Q]), T(fg[2 * Q * Q]), T(fg[3 * Q * Q])};
                     #pragma unroll
                     for (int c = 0; c < 3; ++c)
                         #pragma unroll
-                        for (int c2 = 0; c2 < 3; ++c2) Kab[c][c2] += w * ((c == c2 ? T(1) : T(0)) - n[c] * n[c2]);
+                        for (int c2 = 0; c2 < 3; ++c2) {
+                            Kab[c][c2] += w * ((c == c2 ? T(1) : T(0)) - n[c] * n[c2]);
+                            if (sst) Kab[c][c2] += phi * phi * sst[(4 + c) * Q * Q] * sst[(1 + c2) * Q * Q];
+                        }
                 }
         }
         #pragma unroll
