@@ -230,7 +230,14 @@ int stokes_param_grad_A_fixed_order(const stokes_mesh* mesh, const stokes_params
 /* Linearised state: the per-quadrature-point Newton coefficients at up_lin
  * (geometry, mu, and the rank-one term of Eq. 2.7), evaluated in FP64 and
  * stored in `prec`, so that repeated Jacobian applies (Krylov iterations)
- * stream them instead of recomputing the viscosity. */
+ * stream them instead of recomputing the viscosity.  With a nonlinear
+ * sliding law (params->sliding_m not 0 or 1) the linearisation also stores,
+ * per basal Gauss point, beta w s, 2 beta w s' T u and T u, which the basal
+ * term of the applies uses.  The state owns its device arrays (about
+ * 1200 bytes per Q2 element in FP32, plus 7 values per basal Gauss point);
+ * the FP32 state of a conforming k = 2 mesh is stored in groups of 10
+ * elements for the component-per-lane apply kernel, every other state
+ * element by element (the layout is internal to the library). */
 int stokes_state_create(const stokes_mesh* mesh, int prec, stokes_state** out);
 int stokes_state_destroy(stokes_state* state);
 /* up_lin: device FP64 [3Nv+Np]. params is copied into the state; the device
