@@ -135,3 +135,15 @@ def test_sliding_exponent_without_the_half_is_caught(monkeypatch):
     monkeypatch.setattr(stokes, "_sliding", wrong)
     with pytest.raises(AssertionError):
         closed_form(1.0 / 3.0, 1.7)
+
+
+def test_doubled_viscosity_stops_the_convergence(monkeypatch):
+    """mu -> 2 mu in the oracle's viscous term: the discrete solutions no
+    longer converge to the manufactured solution."""
+    from tests.test_oracle_convergence import errors
+    good = [errors(2, "P", n)[0] for n in (4, 8)]
+    assert good[1] < 0.3 * good[0]
+    orig = stokes._viscosity
+    monkeypatch.setattr(stokes, "_viscosity", lambda phys, DD: 2.0 * orig(phys, DD))
+    bad = [errors(2, "P", n)[0] for n in (4, 8)]
+    assert bad[1] > 0.6 * bad[0]
