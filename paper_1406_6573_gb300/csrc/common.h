@@ -10,9 +10,12 @@
 
 namespace stokes {
 
-constexpr int KMAX = 5;           // highest supported velocity degree
+constexpr int KMAX = 9;           // highest velocity degree of the host mesh builder and tables
+                                  // (the GPU kernels are built for k = 2, 3, 4)
 constexpr int N1MAX = KMAX + 1;   // nodes (and Gauss points) per direction
-constexpr int NPRMAX = 35;        // P_{k-1} with k = 5: 5*6*7/6
+constexpr int NPRMAX = (KMAX - 1) * (KMAX - 1) * (KMAX - 1);   // largest pressure space: Q_{k-2} at
+                                  // k = 9, (k - 1)^3 = 512 modes (P_{k-1} has 165)
+static_assert(NPRMAX >= KMAX * (KMAX + 1) * (KMAX + 2) / 6, "P_{k-1} fits");
 
 // Hanging-node code of an element (one 32-bit word).
 //   bits 0..5   face f = 2 d + s hanging (d axis, s = 0 minus side, 1 plus side)

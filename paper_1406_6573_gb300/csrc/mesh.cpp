@@ -122,7 +122,7 @@ inline int slot(int n1, int i, int j, int l) { return i + n1 * (j + n1 * l); }
 
 int build_host_mesh(const stokes_mesh_desc& d, HostMesh& m, std::string& err) {
     if (d.nx < 1 || d.ny < 1 || d.nz < 1) { err = "grid sizes must be >= 1"; return STOKES_E_INVAL; }
-    if (d.k < 1 || d.k > KMAX) { err = "velocity degree k must be in 1..5"; return STOKES_E_INVAL; }
+    if (d.k < 1 || d.k > KMAX) { err = "velocity degree k must be in 1..9"; return STOKES_E_INVAL; }
     if (d.pressure_space != STOKES_PRESSURE_P && d.pressure_space != STOKES_PRESSURE_Q) {
         err = "unknown pressure space"; return STOKES_E_INVAL;
     }

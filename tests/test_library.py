@@ -30,7 +30,7 @@ def test_library_exports_every_declared_symbol():
 def test_invalid_arguments_are_rejected():
     wl = synth.workload("box_4x4x2_q2p1")
     d, keep = mesh_desc(wl, device=-1)
-    d.k = 9
+    d.k = 10
     with pytest.raises(capi.StokesError) as e:
         capi.stokes_mesh_create(d)
     assert e.value.code == -1 and "degree" in str(e.value)
@@ -56,9 +56,35 @@ MESHES = ["box_4x4x2_q2p1", "slab_8x8x2_q2p1", "slab_5x3x3_q2p1", "forest_4x4x2_
           "cbox_3x3x2_q3q1", "slab_6x6x2_q3q1"]
 
 
+HIGH_K = [("box_4x4x2_q2p1", 5, "P"), ("slab_5x3x3_q2p1", 6, "Q"), ("cforest_3x3x2_q3p2", 6, "P"),
+          ("box_4x4x2_q2p1", 9, "Q")]
+
+
+def _high_k(base, k, ps):
+    import dataclasses
+    wl = synth.workload(base)
+    return dataclasses.replace(wl, name=f"{base}_k{k}{ps}", k=k, pspace=ps)
+
+
+@pytest.mark.parametrize("base,k,ps", HIGH_K)
+def test_host_mesh_matches_oracle_high_degree(base, k, ps):
+    """Degrees 5..9 (the paper's range, Section 7): the host mesh builder and
+    the oracle agree on counts, coordinates and basal nodes, including
+    hanging nodes; device meshes stay limited to the kernels' k = 2, 3, 4."""
+    wl = _high_k(base, k, ps)
+    _compare_with_oracle(wl)
+    d, keep = mesh_desc(wl, device=0)
+    with pytest.raises(capi.StokesError) as e:
+        capi.stokes_mesh_create(d)
+    assert e.value.code == -1
+
+
 @pytest.mark.parametrize("name", MESHES)
 def test_host_mesh_matches_oracle(name):
-    wl = synth.workload(name)
+    _compare_with_oracle(synth.workload(name))
+
+
+def _compare_with_oracle(wl):
     m = Mesh(wl, device=-1)
     o = OracleMesh(wl)
     assert (m.E, m.Nv, m.Np, m.Nb) == (o.E, o.Nv, o.Np, o.Nb)
