@@ -147,3 +147,21 @@ def test_doubled_viscosity_stops_the_convergence(monkeypatch):
     monkeypatch.setattr(stokes, "_viscosity", lambda phys, DD: 2.0 * orig(phys, DD))
     bad = [errors(2, "P", n)[0] for n in (4, 8)]
     assert bad[1] > 0.6 * bad[0]
+
+
+def test_infsup_without_the_jacobian_weight_in_k_is_caught(monkeypatch):
+    """K assembled without w detJ: the inf-sup constant is no longer
+    invariant under a scaling of the domain."""
+    from oracle import infsup
+    orig = infsup.operators
+
+    def bad(o):
+        KI, B, M, I = orig(o)
+        return KI / np.mean(o.wdetJ), B, M, I     # drops the volume scaling of K
+    b1 = infsup.infsup(infsup.cube_mesh(2, "P", 2, side=1.0))[0]
+    b7 = infsup.infsup(infsup.cube_mesh(2, "P", 2, side=7.0))[0]
+    assert abs(b1 - b7) <= 1e-10 * b1
+    monkeypatch.setattr(infsup, "operators", bad)
+    c1 = infsup.infsup(infsup.cube_mesh(2, "P", 2, side=1.0))[0]
+    c7 = infsup.infsup(infsup.cube_mesh(2, "P", 2, side=7.0))[0]
+    assert abs(c1 - c7) > 1e-3 * c1
