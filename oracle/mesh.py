@@ -34,6 +34,33 @@ from . import basis
 KEYSCALE = 1.0e8
 
 
+def face_normals(dF, Xb):
+    """Area-scaled normal N = t1 x t2 of the basal faces (zeta = -1) at the
+    face Gauss points, t_m = dX/dxi_m from the tangential derivative tables
+    dF[m] (Section 3.2.1: isoparametric map); |N| = |J_s| and N / |N| is the
+    unit normal (sign irrelevant)."""
+    t1 = np.einsum("qa,ead->eqd", dF[0], Xb)
+    t2 = np.einsum("qa,ead->eqd", dF[1], Xb)
+    return np.cross(t1, t2)
+
+
+def nodal_normals(mesh):
+    """int_{Gamma_b} phi_i n ds at the basal nodes, assembled through R (the
+    area-weighted nodal normal of the slip condition u . n = 0, Eq. 2.4b)."""
+    eb = mesh.basal_elems
+    contrib = np.einsum("qa,eqd->ead", mesh.phiF, mesh.nF * mesh.wareaF[..., None])
+    full = np.zeros((mesh.E, mesh.A, 3))
+    full[eb] = contrib
+    nodal = mesh.R.T @ full.reshape(mesh.E * mesh.A, 3)
+    return nodal[mesh.basal]
+
+
+def slip_projector(n):
+    """P = I - n n^T at each basal node (n unit): the tangential projector T of
+    Eq. 2.4, which imposes u . n = 0 when applied to the basal velocity."""
+    return np.eye(3)[None] - n[:, :, None] * n[:, None, :]
+
+
 class OracleMesh:
     def __init__(self, wl):
         self.wl = wl
@@ -261,10 +288,7 @@ class OracleMesh:
         self.phiF = f3(B, B, Lm1)                           # (Qf, A)
         dF = np.stack([f3(Dd, B, Lm1), f3(B, Dd, Lm1)])      # tangential derivatives
         self.WF = np.einsum("a,b->ba", W1, W1).ravel()
-        Xb = self.X[self.basal_elems]
-        t1 = np.einsum("qa,ead->eqd", dF[0], Xb)
-        t2 = np.einsum("qa,ead->eqd", dF[1], Xb)
-        N = np.cross(t1, t2)
+        N = face_normals(dF, self.X[self.basal_elems])
         self.areaF = np.linalg.norm(N, axis=-1)              # |J_s|
         self.nF = N / self.areaF[..., None]                  # unit normal (sign irrelevant)
         self.wareaF = self.areaF * self.WF[None, :]
@@ -276,18 +300,13 @@ class OracleMesh:
         The slip normal is the normalised area-weighted nodal normal
         int phi_i n ds, assembled through R.
         """
-        eb = self.basal_elems
-        contrib = np.einsum("qa,eqd->ead", self.phiF, self.nF * self.wareaF[..., None])
-        full = np.zeros((self.E, self.A, 3))
-        full[eb] = contrib
-        nodal = self.R.T @ full.reshape(self.E * self.A, 3)
-        nb = nodal[self.basal]
+        nb = nodal_normals(self)
+        self.basal_nodal_vec = nb                            # int phi_i n ds (unnormalised)
         self.basal_normal = nb / np.linalg.norm(nb, axis=1)[:, None]
         if self.wl.phys.basal_bc == "noslip":
             self.basal_P = np.zeros((self.Nb, 3, 3))
         else:
-            n = self.basal_normal
-            self.basal_P = np.eye(3)[None] - n[:, :, None] * n[:, None, :]
+            self.basal_P = slip_projector(self.basal_normal)
 
     # ---------------------------------------------------------------- helpers
     @property

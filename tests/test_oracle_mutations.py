@@ -165,3 +165,65 @@ def test_infsup_without_the_jacobian_weight_in_k_is_caught(monkeypatch):
     c1 = infsup.infsup(infsup.cube_mesh(2, "P", 2, side=1.0))[0]
     c7 = infsup.infsup(infsup.cube_mesh(2, "P", 2, side=7.0))[0]
     assert abs(c1 - c7) > 1e-3 * c1
+
+
+# ------------------------------------------------- basal face geometry pins
+def _nodal_normal_error(name="cbox_3x3x2_q2p1"):
+    from test_oracle_face_geometry import closed_form_nodal_normals
+    wl = synth.workload(name)
+    m = OracleMesh(wl)
+    xs, ys, acc = closed_form_nodal_normals(wl)
+    bc = m.basal_coords()
+    ref = acc[np.searchsorted(xs, bc[:, 0] - 1e-12), np.searchsorted(ys, bc[:, 1] - 1e-12)]
+    nref = ref / np.linalg.norm(ref, axis=1)[:, None]
+    return np.abs(m.basal_normal - nref).max()
+
+
+def _tilted_projector_error():
+    from test_oracle_face_geometry import tilted
+    alpha, beta = 0.3, -0.2
+    m = OracleMesh(tilted("mut", alpha, beta))
+    n = np.array([-alpha, -beta, 1.0]) / np.sqrt(1.0 + alpha ** 2 + beta ** 2)
+    return np.abs(np.einsum("nij,j->ni", m.basal_P, n)).max()
+
+
+def test_face_geometry_baseline_pins_hold():
+    assert _nodal_normal_error() < 1e-13
+    assert _tilted_projector_error() < 1e-14
+
+
+def test_nodal_normal_without_face_area_is_caught(monkeypatch):
+    import oracle.mesh as om
+
+    def bad(mesh):   # weights w instead of w |J_s|
+        contrib = np.einsum("qa,eqd->ead", mesh.phiF, mesh.nF * mesh.WF[None, :, None])
+        full = np.zeros((mesh.E, mesh.A, 3))
+        full[mesh.basal_elems] = contrib
+        return (mesh.R.T @ full.reshape(mesh.E * mesh.A, 3))[mesh.basal]
+    monkeypatch.setattr(om, "nodal_normals", bad)
+    assert _nodal_normal_error() > 1e-6
+
+
+def test_transposed_tangent_table_is_caught(monkeypatch):
+    import oracle.mesh as om
+
+    def bad(dF, Xb):  # face Gauss points of the eta tangent taken in transposed order
+        nq = int(round(np.sqrt(dF.shape[1])))
+        d1 = dF[1].reshape(nq, nq, -1).transpose(1, 0, 2).reshape(nq * nq, -1)
+        t1 = np.einsum("qa,ead->eqd", dF[0], Xb)
+        t2 = np.einsum("qa,ead->eqd", d1, Xb)
+        return np.cross(t1, t2)
+    monkeypatch.setattr(om, "face_normals", bad)
+    assert _nodal_normal_error() > 1e-6
+
+
+def test_projector_from_unnormalised_normal_is_caught(monkeypatch):
+    import oracle.mesh as om
+    orig_build = om.OracleMesh._build_constraints
+
+    def bad_build(self):   # plant: P = I - v v^T with v = int phi_i n ds, not normalised
+        orig_build(self)
+        if self.wl.phys.basal_bc != "noslip":
+            self.basal_P = om.slip_projector(self.basal_nodal_vec)
+    monkeypatch.setattr(om.OracleMesh, "_build_constraints", bad_build)
+    assert _tilted_projector_error() > 1e-6
