@@ -220,7 +220,11 @@ int stokes_param_grad(const stokes_mesh* mesh, const stokes_params* params,
  * race on it and both results are undefined; callers serialise them.
  * Set-up: the first call on each device resolves the scratch address with
  * cudaGetSymbolAddress and caches it; make that first call before beginning
- * any stream capture on that device.
+ * any stream capture on that device.  The cached address lives as long as
+ * the process and belongs to the device's primary context at the time of
+ * that first call: after cudaDeviceReset (or anything else that destroys
+ * and recreates the primary context) the address is stale, so do not call
+ * this entry point again in that process after a device reset.
  * up, lambda: device FP64 [3Nv+Np]; g_A: device, 1 double, overwritten. */
 #define STOKES_GRAD_A_MAX_PARTIALS 131072
 int stokes_param_grad_A_fixed_order(const stokes_mesh* mesh, const stokes_params* params,
@@ -285,11 +289,18 @@ typedef struct {
     double constraint_scale;     /* s used by stokes_newton_solve (see stokes_params) */
     double history[64];          /* ||r_j||, j = 0 .. newton_its (first 64)          */
     int krylov_per_newton[64];
+    int line_search_failed;      /* 1: twelve step halvings gave no decrease of ||r||;
+                                    the step was rejected, up holds the last accepted
+                                    iterate and the solve returned STOKES_E_NOCONV */
 } stokes_solve_report;
 
 int stokes_solver_create(const stokes_mesh* mesh, const stokes_solver_opts* opts, stokes_solver** out);
 int stokes_solver_destroy(stokes_solver* solver);
-/* Solve r_c(up) = 0 starting from the device FP64 state up (overwritten).
+/* Both solvers read the mesh's device status word (stokes_mesh_status) after
+ * every restart cycle and every Newton step: if a kernel gave up waiting for
+ * a staged copy the word is cleared and the solve returns STOKES_E_CUDA.
+ *
+ * Solve r_c(up) = 0 starting from the device FP64 state up (overwritten).
  * The solver replaces params->constraint_scale by the mean diagonal of the
  * velocity block at the first linearisation (reported in the report); the
  * residual norms it reports use that scale.
@@ -305,6 +316,27 @@ int stokes_newton_solve(stokes_solver* solver, const stokes_params* params, doub
 int stokes_linear_solve(stokes_solver* solver, const stokes_params* params, const double* up_lin,
                         const double* b, double* x, int transpose, double rtol,
                         stokes_solve_report* report, void* stream);
+
+/* Test hooks (failure injection on the host side; no kernel is made to
+ * fault or hang).
+ *
+ * stokes_debug_wait_limit: poll limit of the first wait of the stored-state
+ * applies (stokes_state_apply*, stokes_state_apply_pressure_block) for the
+ * staged state of each element group; default STOKES_WAIT_POLLS_DEFAULT.
+ * With a small limit (0: give up at once) the warps that run out set the
+ * mesh's status word, wait for their own copies in flight with the default
+ * limit and return, so the apply's output is incomplete and
+ * stokes_mesh_status (and the solvers) report STOKES_E_CUDA.  Restore the
+ * default after the test.  Returns STOKES_E_INVAL for a host-only mesh.
+ *
+ * stokes_debug_fail_alloc_after: the library's next n device allocations
+ * succeed and the one after fails as if the device were out of memory (the
+ * entry point making it returns STOKES_E_NOMEM and frees what it had
+ * allocated); n < 0 switches the hook off (the default).  Process-wide;
+ * returns the previous setting. */
+#define STOKES_WAIT_POLLS_DEFAULT 4194304u
+int stokes_debug_wait_limit(stokes_mesh* mesh, uint32_t polls);
+int64_t stokes_debug_fail_alloc_after(int64_t n);
 
 /* Per-kernel timing (tracing).  Between stokes_profile_begin and
  * stokes_profile_end every operator call on this mesh, and every launch and

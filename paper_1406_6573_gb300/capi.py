@@ -12,6 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "lib", "libstokes_gb300.so")
 
 STOKES_OK = 0
+STOKES_WAIT_POLLS_DEFAULT = 4194304
 STOKES_F64 = 0
 STOKES_F32 = 1
 STOKES_PRESSURE_P = 0
@@ -76,7 +77,7 @@ class stokes_solve_report(C.Structure):
     _fields_ = [("converged", C.c_int), ("newton_its", C.c_int), ("krylov_its", C.c_int),
                 ("line_search_cuts", C.c_int), ("res0", C.c_double), ("res_final", C.c_double),
                 ("seconds", C.c_double), ("constraint_scale", C.c_double), ("history", C.c_double * 64),
-                ("krylov_per_newton", C.c_int * 64)]
+                ("krylov_per_newton", C.c_int * 64), ("line_search_failed", C.c_int)]
 
     def as_dict(self):
         n = min(self.newton_its + 1, 64)
@@ -85,7 +86,8 @@ class stokes_solve_report(C.Structure):
                 "res0": self.res0, "res_final": self.res_final, "seconds": self.seconds,
                 "constraint_scale": self.constraint_scale,
                 "history": list(self.history[:n]),
-                "krylov_per_newton": list(self.krylov_per_newton[:max(n - 1, 0)])}
+                "krylov_per_newton": list(self.krylov_per_newton[:max(n - 1, 0)]),
+                "line_search_failed": bool(self.line_search_failed)}
 
 
 # every symbol declared in include/stokes.h, with its ctypes signature
@@ -121,6 +123,8 @@ _SIGS = {
     "stokes_profile_begin": (C.c_int, [C.c_void_p]),
     "stokes_profile_end": (C.c_int, [C.c_void_p, C.POINTER(stokes_profile)]),
     "stokes_last_error": (C.c_char_p, []),
+    "stokes_debug_wait_limit": (C.c_int, [C.c_void_p, C.c_uint32]),
+    "stokes_debug_fail_alloc_after": (C.c_int64, [C.c_int64]),
 }
 
 _lib = None
@@ -190,6 +194,14 @@ def stokes_mesh_node_coords(h, out):
 
 def stokes_mesh_basal_nodes(h, out):
     _check(lib().stokes_mesh_basal_nodes(h, _ptr(out)))
+
+
+def stokes_debug_wait_limit(h, polls):
+    _check(lib().stokes_debug_wait_limit(h, polls))
+
+
+def stokes_debug_fail_alloc_after(n):
+    return int(lib().stokes_debug_fail_alloc_after(n))
 
 
 def stokes_residual(h, params, up, r, prec, stream=None):

@@ -1,5 +1,6 @@
 // C-ABI entry points (include/stokes.h): argument checking, device memory of
 // the mesh handle, and the launch sequence of each operator.
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -43,7 +44,7 @@ template <typename T>
 int upload(T** dst, const std::vector<T>& src) {
     *dst = nullptr;
     if (src.empty()) return STOKES_OK;
-    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(dst), src.size() * sizeof(T));
+    cudaError_t e = dev_alloc(reinterpret_cast<void**>(dst), src.size() * sizeof(T));
     if (e != cudaSuccess) { *dst = nullptr; return fail(STOKES_E_NOMEM, "cudaMalloc of mesh data failed"); }
     e = cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(e, "uploading mesh data");
@@ -71,6 +72,21 @@ int fail(int code, const std::string& msg) {
 
 int cuda_fail(cudaError_t e, const char* where) {
     return fail(STOKES_E_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+static_assert(STOKES_WAIT_POLLS_DEFAULT == WAIT_POLLS_DEFAULT, "header and kernels agree on the poll limit");
+
+// allocation-failure test hook: number of device allocations still allowed
+// before the next one fails (-1: never fail)
+std::atomic<int64_t> g_alloc_budget{-1};
+
+cudaError_t dev_alloc(void** p, size_t bytes) {
+    int64_t b = g_alloc_budget.load();
+    while (b >= 0) {
+        if (b == 0) { *p = nullptr; return cudaErrorMemoryAllocation; }
+        if (g_alloc_budget.compare_exchange_weak(b, b - 1)) break;
+    }
+    return cudaMalloc(p, bytes);
 }
 
 int launch_elem(int k, int mode, int prec, int state_prec, bool trans, const ElemArgs& a, cudaStream_t s) {
@@ -145,6 +161,7 @@ ElemArgs elem_args(const stokes_mesh* m, const stokes_params* p) {
     a.nodes = m->d_nodes; a.hang = m->d_hang; a.geo = m->d_geo; a.pidx = m->d_pidx; a.pel = m->d_pel;
     a.pel_f = m->d_pel_f;
     a.err = m->d_err;
+    a.wait_polls = m->wait_polls;
     if (m->h.lattice) {
         a.lat_nx = m->h.nx; a.lat_ny = m->h.ny; a.lat_NX = m->h.latNX; a.lat_NY = m->h.latNY;
     }
@@ -331,6 +348,16 @@ int stokes_mesh_status(const stokes_mesh* mesh) {
     return STOKES_OK;
 }
 
+int stokes_debug_wait_limit(stokes_mesh* mesh, uint32_t polls) {
+    if (!mesh || !mesh->on_device) return fail(STOKES_E_INVAL, "the wait-limit hook needs a device mesh");
+    mesh->wait_polls = polls;
+    return STOKES_OK;
+}
+
+int64_t stokes_debug_fail_alloc_after(int64_t n) {
+    return g_alloc_budget.exchange(n < 0 ? -1 : n);
+}
+
 int stokes_mesh_destroy(stokes_mesh* mesh) {
     if (!mesh) return STOKES_OK;
     if (mesh->on_device) {
@@ -443,7 +470,7 @@ int stokes_state_create(const stokes_mesh* mesh, int prec, stokes_state** out) {
     const size_t values = st->cpl ? size_t((mesh->h.E + CPL_GROUP_ELEMS - 1) / CPL_GROUP_ELEMS) * CPL_GROUP_VALUES
                                   : size_t(mesh->h.E) * size_t(state_stride(mesh->h.k));
     const size_t bytes = values * (prec == STOKES_F32 ? 4 : 8);
-    if (cudaMalloc(&st->d_state, bytes) != cudaSuccess) {
+    if (dev_alloc(&st->d_state, bytes) != cudaSuccess) {
         delete st;
         return fail(STOKES_E_NOMEM, "cudaMalloc of the linearised state failed");
     }
@@ -456,7 +483,7 @@ int stokes_state_create(const stokes_mesh* mesh, int prec, stokes_state** out) {
     if (mesh->h.nF > 0) {
         const int q = mesh->h.k + 1;
         const size_t fbytes = size_t(mesh->h.nF) * SLIDE_FIELDS * q * q * (prec == STOKES_F32 ? 4 : 8);
-        if (cudaMalloc(&st->d_fstate, fbytes) != cudaSuccess) {
+        if (dev_alloc(&st->d_fstate, fbytes) != cudaSuccess) {
             cudaFree(st->d_state);
             delete st;
             return fail(STOKES_E_NOMEM, "cudaMalloc of the sliding state failed");

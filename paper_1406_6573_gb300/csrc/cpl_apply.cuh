@@ -280,8 +280,9 @@ __global__ void __launch_bounds__(32 * CplCfg::W, CPL_MINB) cpl_state_apply_kern
             cpl_forward(w, Gx, Gy, Gz);
         }
 
-        if (!mbar_wait_bounded(bar, uint32_t(it & 1))) {
-            // the staged state never arrived: report, let the copy drain, stop
+        if (!mbar_wait_polls(bar, uint32_t(it & 1), a.wait_polls)) {
+            // the staged state never arrived: report, let the copy (the only
+            // one this warp has in flight) drain, stop
             if (lane == 0) atomicOr(a.err, 1);
             mbar_wait_bounded(bar, uint32_t(it & 1));
             return;

@@ -678,10 +678,13 @@ __global__ void __launch_bounds__(32 * StateApplyCfg<T>::W, StateApplyCfg<T>::MI
                     for (int lq = 0; lq < Q; ++lq) G[c][m][lq] = T(0);
         }
 
-        if (!mbar_wait_bounded(&bar[buf], uint32_t((it >> 1) & 1))) {
-            // the staged state never arrived: report, let the copy drain, stop
+        if (!mbar_wait_polls(&bar[buf], uint32_t((it >> 1) & 1), a.wait_polls)) {
+            // the staged state never arrived: report, let this warp's copies
+            // drain (this group's, and the next group's issued into the other
+            // buffer at the top of this iteration), stop
             if (lane == 0) atomicOr(a.err, 1);
             mbar_wait_bounded(&bar[buf], uint32_t((it >> 1) & 1));
+            if (g + gstride < ngroups) mbar_wait_bounded(&bar[buf ^ 1], uint32_t(((it + 1) >> 1) & 1));
             return;
         }
         const T* st = stage(buf) + (es < EPW ? es : 0) * SSTRIDE;

@@ -31,6 +31,8 @@ struct Profiler {
 };
 
 int fail(int code, const std::string& msg);
+// cudaMalloc through the allocation-failure test hook (stokes_debug_fail_alloc_after)
+cudaError_t dev_alloc(void** p, size_t bytes);
 int cuda_fail(cudaError_t e, const char* where);
 
 // Make `dev` current for the duration of a call, restoring the caller's device.
@@ -79,6 +81,7 @@ struct stokes_mesh {
     int32_t* d_basal_nodes = nullptr;
     double* d_basal_P = nullptr;
     int* d_err = nullptr;          // status word written by kernels (bounded waits)
+    uint32_t wait_polls = stokes::WAIT_POLLS_DEFAULT;   // first-wait poll limit (test hook)
     // vertical node columns (preconditioner)
     int32_t* d_col_of = nullptr;
     int32_t* d_pos_of = nullptr;

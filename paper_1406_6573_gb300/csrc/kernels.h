@@ -7,6 +7,10 @@
 
 namespace stokes {
 
+// polls of an mbarrier before a kernel gives up waiting for a staged copy
+// (each poll may suspend the thread for a hardware-chosen interval)
+constexpr uint32_t WAIT_POLLS_DEFAULT = 1u << 22;
+
 enum ElemMode : int {
     MODE_RESIDUAL = 0,     // r  = R^T(int sigma(u, p) : grad v - b . v) , -(q, div u)
     MODE_APPLY = 1,        // y  = J(u) x, linearisation recomputed per quadrature point
@@ -90,6 +94,9 @@ struct ElemArgs {
     int64_t lat_nx, lat_ny, lat_NX, lat_NY;   // conforming lattice (lat_nx > 0): node index
                                // computed as I + NX (J + NY L) instead of read from nodes
     int* err;                  // device status word (bounded waits that expired)
+    uint32_t wait_polls;       // poll limit of the first wait for a group's staged state
+                               // (WAIT_POLLS_DEFAULT; smaller only through the test hook);
+                               // the drain after a give-up always uses WAIT_POLLS_DEFAULT
     int persistent_blocks;     // grid size of the persistent state-apply kernel
     // basal terms done by the stored-state kernel after its element groups
     // (one launch per apply): the Robin term (face, fuse_robin) and the

@@ -85,6 +85,23 @@ int norm64(stokes_solver* S, const double* x, int64_t n, double& out, cudaStream
     return STOKES_OK;
 }
 
+// The mesh's device status word, set by a kernel whose bounded wait for a
+// staged copy expired (its contribution to the output is then missing).
+// Read after every restart cycle and every Newton step; if set it is cleared
+// and the solve returns STOKES_E_CUDA rather than a result built on a wrong
+// operator product.
+int device_status(stokes_solver* S, cudaStream_t st) {
+    int flag = 0;
+    TU(PROF_TRANSFER, cudaMemcpyAsync(&flag, S->mesh->d_err, sizeof(int), cudaMemcpyDeviceToHost, st), "status readback");
+    CU(cudaStreamSynchronize(st), "status sync");
+    if (flag) {
+        CU(cudaMemsetAsync(S->mesh->d_err, 0, sizeof(int), st), "clearing the status word");
+        CU(cudaStreamSynchronize(st), "status sync");
+        return fail(STOKES_E_CUDA, "a kernel gave up waiting for a staged copy during the solve (status word set)");
+    }
+    return STOKES_OK;
+}
+
 int op_inner(stokes_solver* S, const void* x, void* y, bool trans, cudaStream_t st) {
     return trans ? stokes_state_apply_transpose(S->st_in, x, y, st) : stokes_state_apply(S->st_in, x, y, st);
 }
@@ -262,6 +279,7 @@ int linear_solve(stokes_solver* S, const double* rhs, double nrhs, double eta, b
         TU(PROF_VECTOR, vec_axpby(n, 1.0, nullptr, STOKES_F64, rhs, 0.0, STOKES_F64, S->rl, st), "residual");
         TU(PROF_VECTOR, vec_axpby(n, -1.0, nullptr, STOKES_F64, S->tmp64, 1.0, STOKES_F64, S->rl, st), "residual");
         CK(norm64(S, S->rl, n, nrl, st));
+        CK(device_status(S, st));
         if (its == 0) break;
     }
     return STOKES_OK;
@@ -306,7 +324,7 @@ int stokes_solver_create(const stokes_mesh* mesh, const stokes_solver_opts* opts
     S->band_elems = size_t(3) * mesh->h.colmax * size_t(2 * S->bw + 1) * size_t(band_cols(mesh->h.ncol));
     auto alloc = [&](void** p, size_t bytes) {
         if (rc) return;
-        if (cudaMalloc(p, bytes) != cudaSuccess) { *p = nullptr; rc = fail(STOKES_E_NOMEM, "solver workspace"); }
+        if (dev_alloc(p, bytes) != cudaSuccess) { *p = nullptr; rc = fail(STOKES_E_NOMEM, "solver workspace"); }
     };
     alloc(reinterpret_cast<void**>(&S->r), n * 8);
     alloc(reinterpret_cast<void**>(&S->dl), n * 8);
@@ -399,11 +417,18 @@ int stokes_newton_solve(stokes_solver* S, const stokes_params* params, double* u
             alpha *= 0.5;
             R.line_search_cuts++;
         }
+        CK(device_status(S, st));
         if (!std::isfinite(nrt)) {
             R.newton_its = k + 1;
             R.res_final = nrt;
             if (rep) *rep = R;
             return fail(STOKES_E_NONFINITE, "non-finite residual after the Newton update (up left at the last iterate)");
+        }
+        if (!(nrt < nr)) {
+            // twelve halvings without any decrease: the step is rejected, up
+            // keeps the last iterate and the solve stops (E_NOCONV)
+            R.line_search_failed = 1;
+            break;
         }
         TU(PROF_VECTOR, cudaMemcpyAsync(up, S->trial, sizeof(double) * n, cudaMemcpyDeviceToDevice, st), "update");
         TU(PROF_VECTOR, cudaMemcpyAsync(S->r, S->rt, sizeof(double) * n, cudaMemcpyDeviceToDevice, st), "update");

@@ -63,12 +63,16 @@ __device__ __forceinline__ void prefetch_l1(const void* p) {
     asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
 }
 
-constexpr uint32_t MBAR_POLL_LIMIT = 1u << 22;
+constexpr uint32_t MBAR_POLL_LIMIT = WAIT_POLLS_DEFAULT;
+
+__device__ __forceinline__ bool mbar_wait_polls(uint64_t* bar, uint32_t parity, uint32_t limit) {
+    bool ok = false;
+    for (uint32_t it = 0; it < limit && !ok; ++it) ok = mbar_try_wait(bar, parity);
+    return __all_sync(0xffffffffu, ok) != 0;
+}
 
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-    bool ok = false;
-    for (uint32_t it = 0; it < MBAR_POLL_LIMIT && !ok; ++it) ok = mbar_try_wait(bar, parity);
-    return __all_sync(0xffffffffu, ok) != 0;
+    return mbar_wait_polls(bar, parity, MBAR_POLL_LIMIT);
 }
 
 }  // namespace dev

@@ -139,12 +139,20 @@ def _build():
     w["forest_4x4x2_q2p1"] = _slab("forest_4x4x2_q2p1", 4, 4, 2, 2, "P",
                                     refine_frac=0.3, seed=5)
     w["box_3x2x2_q3q1"] = _box("box_3x2x2_q3q1", 3, 2, 2, 3, "Q")
+    # the aspect-robust Q_k x Q_(k-2) pairing (Section 3.2.2) at k = 2 and 4
+    w["slab_128x128x8_q2q0"] = _slab("slab_128x128x8_q2q0", 128, 128, 8, 2, "Q")
+    w["slab_5x3x3_q2q0"] = _slab("slab_5x3x3_q2q0", 5, 3, 3, 2, "Q", seed=7)
+    w["slab_4x4x2_q4q2"] = _slab("slab_4x4x2_q4q2", 4, 4, 2, 4, "Q", grf_beta=True, seed=2)
+    w["forest_4x4x2_q2q0"] = _slab("forest_4x4x2_q2q0", 4, 4, 2, 2, "Q",
+                                    refine_frac=0.3, grf_beta=True, seed=6)
     # curved non-periodic boxes (conforming and with hanging nodes)
     w["cbox_3x3x2_q2p1"] = _cbox("cbox_3x3x2_q2p1", 3, 3, 2, 2, "P")
     w["cbox_3x3x2_q3q1"] = _cbox("cbox_3x3x2_q3q1", 3, 3, 2, 3, "Q")
     w["cforest_3x3x2_q2p1"] = _cbox("cforest_3x3x2_q2p1", 3, 3, 2, 2, "P", refine_frac=0.4)
     w["cforest_3x3x2_q3p2"] = _cbox("cforest_3x3x2_q3p2", 3, 3, 2, 3, "P", refine_frac=0.4)
     w["cforest_4x3x2_q4p3"] = _cbox("cforest_4x3x2_q4p3", 4, 3, 2, 4, "P", refine_frac=0.3, seed=4)
+    w["cbox_3x3x2_q2q0"] = _cbox("cbox_3x3x2_q2q0", 3, 3, 2, 2, "Q")
+    w["cforest_4x3x2_q4q2"] = _cbox("cforest_4x3x2_q4q2", 4, 3, 2, 4, "Q", refine_frac=0.3, seed=4)
     return w
 
 

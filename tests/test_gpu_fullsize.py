@@ -27,8 +27,8 @@ def rel_blocks(o, got, ref):
     return out
 
 
-@pytest.mark.parametrize("name", ["slab_128x128x8_q2p1", "slab_64x64x4_q3q1", "slab_64x64x4_q4p3",
-                                  "forest_64x64x4_q3p2"])
+@pytest.mark.parametrize("name", ["slab_128x128x8_q2p1", "slab_128x128x8_q2q0", "slab_64x64x4_q3q1",
+                                  "slab_64x64x4_q4p3", "forest_64x64x4_q3p2"])
 def test_full_size_parity(name):
     wl = synth.workload(name)
     o = OracleMesh(wl)

@@ -35,6 +35,12 @@ CASES = [
     "forest_6x6x2_q3p2",   # hanging nodes + random log(beta)
     "cforest_3x3x2_q3p2",  # hanging nodes on a curved box
     "cforest_4x3x2_q4p3",  # hanging nodes, degree 4
+    # Q_k x Q_(k-2) pressure (Section 3.2.2), the pairing preferred on anisotropic meshes
+    "slab_5x3x3_q2q0",     # Q2 x Q0: component-per-lane kernel with Q pressure
+    "cbox_3x3x2_q2q0",     # Q2 x Q0 on a curved box, slip base
+    "forest_4x4x2_q2q0",   # Q2 x Q0 with hanging faces and edges
+    "slab_4x4x2_q4q2",     # Q4 x Q2
+    "cforest_4x3x2_q4q2",  # Q4 x Q2 with hanging nodes on a curved box
 ]
 
 _cache = {}

@@ -53,7 +53,8 @@ def _periodic_dist(a, b, L):
 
 MESHES = ["box_4x4x2_q2p1", "slab_8x8x2_q2p1", "slab_5x3x3_q2p1", "forest_4x4x2_q2p1",
           "cforest_3x3x2_q3p2", "forest_6x6x2_q3p2", "cforest_4x3x2_q4p3", "slab_4x4x2_q4p3",
-          "cbox_3x3x2_q3q1", "slab_6x6x2_q3q1"]
+          "cbox_3x3x2_q3q1", "slab_6x6x2_q3q1", "slab_5x3x3_q2q0", "forest_4x4x2_q2q0",
+          "slab_4x4x2_q4q2", "cforest_4x3x2_q4q2", "cbox_3x3x2_q2q0"]
 
 
 HIGH_K = [("box_4x4x2_q2p1", 5, "P"), ("slab_5x3x3_q2p1", 6, "Q"), ("cforest_3x3x2_q3p2", 6, "P"),
@@ -121,3 +122,25 @@ def test_forest_full_size_builds():
     nref = int(wl.refine_mask().sum())
     assert m.E == wl.n_coarse + 7 * nref
     assert m.n_hanging > 0 and m.Np == m.E * 10
+
+
+def test_allocation_failure_hook_settings():
+    """The allocation-failure hook is process-wide and returns its previous
+    setting; host-only meshes allocate no device memory and are unaffected."""
+    prev = capi.stokes_debug_fail_alloc_after(0)
+    try:
+        assert prev == -1
+        m = Mesh(synth.workload("box_4x4x2_q2p1"), device=-1)
+        m.close()
+        assert capi.stokes_debug_fail_alloc_after(7) == 0
+        assert capi.stokes_debug_fail_alloc_after(-5) == 7
+    finally:
+        capi.stokes_debug_fail_alloc_after(-1)
+    assert capi.stokes_debug_fail_alloc_after(-1) == -1
+
+
+def test_wait_limit_hook_needs_a_device_mesh():
+    m = Mesh(synth.workload("box_4x4x2_q2p1"), device=-1)
+    with pytest.raises(capi.StokesError) as e:
+        capi.stokes_debug_wait_limit(m.handle, 0)
+    assert e.value.code == -1
