@@ -49,105 +49,111 @@ struct CplCfg {
     static_assert(PER_WARP % 16 == 0, "stage buffers 16-byte aligned");
 };
 
-// d_xi, d_eta, d_zeta of the Q2 interpolant of the nodal values w at the 27
-// Gauss points (index qi + 3 qj + 9 lq; nodes a + 3 b + 9 l)
-__device__ __forceinline__ void cpl_forward(const float (&w)[27], float (&Gx)[27], float (&Gy)[27],
-                                            float (&Gz)[27]) {
+// Q2 1-D tables as compile-time constants: GLL nodes (-1, 0, 1), Gauss
+// points (-s, 0, s) with s = sqrt(3/5).  B[q][i] = l_i(g_q) and
+// Bd[q][i] = l_i'(g_q) are centro-symmetric (B[2-q][2-i] = B[q][i]) and
+// centro-antisymmetric (Bd[2-q][2-i] = -Bd[q][i]), so each 3-point line is
+// applied through its even part w0 + w2 and odd part w0 - w2 (the even-odd
+// decomposition of symmetric collocation matrices; Solomonoff, "A fast
+// algorithm for spectral differentiation", J. Comput. Phys. 98, 1992), and
+// the zero and unit entries of the middle row fold away:
+//   B  = [[0.3 + s/2, 0.4, 0.3 - s/2], [0, 1, 0], [0.3 - s/2, 0.4, 0.3 + s/2]]
+//   Bd = [[-s - 1/2, 2 s, 1/2 - s], [-1/2, 0, 1/2], [s - 1/2, -2 s, s + 1/2]]
+// The library checks, when it uploads its tables, that its own (computed)
+// tables equal these.
+namespace q2c {
+constexpr float S = 0.774596669241483377f;   // sqrt(3/5)
+constexpr float HS = 0.5f * S;
+// pressure basis at the Gauss points: P_{k-1} = span{1, xi, eta, zeta}
+// (Legendre P_1 = x, modes in the order of the host tables) or Q_0 = {1}
+__device__ __forceinline__ constexpr float gq(int i) { return i == 0 ? -S : (i == 1 ? 0.f : S); }
+template <int PS>
+__device__ __forceinline__ constexpr float psi(int b, int qp) {
+    return PS == 1 ? 1.f : (b == 0 ? 1.f : (b == 1 ? gq(qp % 3) : (b == 2 ? gq((qp / 3) % 3) : gq(qp / 9))));
+}
+}  // namespace q2c
+
+// q = B w (values at the Gauss points of a line)
+__device__ __forceinline__ void q2_b(float w0, float w1, float w2, float& q0, float& q1, float& q2) {
+    const float e = w0 + w2, o = w0 - w2;
+    const float t = fmaf(0.3f, e, 0.4f * w1);
+    q0 = fmaf(q2c::HS, o, t);
+    q2 = fmaf(-q2c::HS, o, t);
+    q1 = w1;
+}
+// d = Bd w (derivatives at the Gauss points of a line)
+__device__ __forceinline__ void q2_d(float w0, float w1, float w2, float& d0, float& d1, float& d2) {
+    const float e = w0 + w2, o = w0 - w2;
+    const float u = q2c::S * fmaf(-2.f, w1, e);
+    const float v = -0.5f * o;
+    d0 = v - u;
+    d1 = v;
+    d2 = v + u;
+}
+// n = B^T s
+__device__ __forceinline__ void q2_bt(float s0, float s1, float s2, float& n0, float& n1, float& n2) {
+    const float E = s0 + s2, O = s0 - s2;
+    const float a = 0.3f * E;
+    n0 = fmaf(q2c::HS, O, a);
+    n2 = fmaf(-q2c::HS, O, a);
+    n1 = fmaf(0.4f, E, s1);
+}
+// n = Bd^T t
+__device__ __forceinline__ void q2_dt(float t0, float t1, float t2, float& n0, float& n1, float& n2) {
+    const float m = q2c::S * (t0 - t2);
+    const float h = 0.5f * (t0 + t1 + t2);
+    n0 = -m - h;
+    n1 = m + m;
+    n2 = h - m;
+}
+
+// zeta and eta stages of the forward sweeps of the nodal values w (nodes
+// a + 3 b + 9 l): BB = (B x B) w, BD = (Bd x B) w, DB = (B x Bd) w along
+// (eta, zeta), indexed a + 3 qj + 9 lq; the xi stage (Bd, B, B along xi)
+// then gives d_xi, d_eta, d_zeta of the Q2 interpolant at the Gauss point
+// qi + 3 qj + 9 lq, one line of three points at a time
+__device__ __forceinline__ void cpl_forward_ze(const float (&w)[27], float (&BB)[27], float (&BD)[27],
+                                               float (&DB)[27]) {
     float Bw[27], Dw[27];   // [a + 3 b + 9 lq]: zeta interpolated / differentiated
     #pragma unroll
-    for (int ab = 0; ab < 9; ++ab)
-        #pragma unroll
-        for (int lq = 0; lq < 3; ++lq) {
-            float sb = 0.f, sd = 0.f;
-            #pragma unroll
-            for (int l = 0; l < 3; ++l) {
-                sb += fB[lq][l] * w[ab + 9 * l];
-                sd += fBd[lq][l] * w[ab + 9 * l];
-            }
-            Bw[ab + 9 * lq] = sb;
-            Dw[ab + 9 * lq] = sd;
-        }
-    float BB[27], BD[27], DB[27];   // [a + 3 qj + 9 lq]
+    for (int ab = 0; ab < 9; ++ab) {
+        q2_b(w[ab], w[ab + 9], w[ab + 18], Bw[ab], Bw[ab + 9], Bw[ab + 18]);
+        q2_d(w[ab], w[ab + 9], w[ab + 18], Dw[ab], Dw[ab + 9], Dw[ab + 18]);
+    }
     #pragma unroll
     for (int a = 0; a < 3; ++a)
         #pragma unroll
-        for (int lq = 0; lq < 3; ++lq)
-            #pragma unroll
-            for (int qj = 0; qj < 3; ++qj) {
-                float s1 = 0.f, s2 = 0.f, s3 = 0.f;
-                #pragma unroll
-                for (int b = 0; b < 3; ++b) {
-                    const float bw = Bw[a + 3 * b + 9 * lq];
-                    s1 += fB[qj][b] * bw;
-                    s2 += fBd[qj][b] * bw;
-                    s3 += fB[qj][b] * Dw[a + 3 * b + 9 * lq];
-                }
-                BB[a + 3 * qj + 9 * lq] = s1;
-                BD[a + 3 * qj + 9 * lq] = s2;
-                DB[a + 3 * qj + 9 * lq] = s3;
-            }
-    #pragma unroll
-    for (int r = 0; r < 9; ++r)          // r = qj + 3 lq
-        #pragma unroll
-        for (int qi = 0; qi < 3; ++qi) {
-            float gx = 0.f, gy = 0.f, gz = 0.f;
-            #pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                gx += fBd[qi][a] * BB[a + 3 * r];
-                gy += fB[qi][a] * BD[a + 3 * r];
-                gz += fB[qi][a] * DB[a + 3 * r];
-            }
-            Gx[qi + 3 * r] = gx;
-            Gy[qi + 3 * r] = gy;
-            Gz[qi + 3 * r] = gz;
+        for (int lq = 0; lq < 3; ++lq) {
+            const int o = a + 9 * lq;
+            q2_b(Bw[o], Bw[o + 3], Bw[o + 6], BB[o], BB[o + 3], BB[o + 6]);
+            q2_d(Bw[o], Bw[o + 3], Bw[o + 6], BD[o], BD[o + 3], BD[o + 6]);
+            q2_b(Dw[o], Dw[o + 3], Dw[o + 6], DB[o], DB[o + 3], DB[o + 6]);
         }
 }
 
-// transpose of cpl_forward: nodal values from the reference stresses
-__device__ __forceinline__ void cpl_transpose(const float (&Sx)[27], const float (&Sy)[27], const float (&Sz)[27],
-                                              float (&out)[27]) {
-    float Ux[27], Uy[27], Uz[27];   // [a + 3 qj + 9 lq]
-    #pragma unroll
-    for (int r = 0; r < 9; ++r)
-        #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            float ux = 0.f, uy = 0.f, uz = 0.f;
-            #pragma unroll
-            for (int qi = 0; qi < 3; ++qi) {
-                ux += fBd[qi][a] * Sx[qi + 3 * r];
-                uy += fB[qi][a] * Sy[qi + 3 * r];
-                uz += fB[qi][a] * Sz[qi + 3 * r];
-            }
-            Ux[a + 3 * r] = ux;
-            Uy[a + 3 * r] = uy;
-            Uz[a + 3 * r] = uz;
-        }
+// eta and zeta stages of the transposed sweeps: nodal values from the xi-
+// transposed reference stresses U (indexed a + 3 qj + 9 lq)
+__device__ __forceinline__ void cpl_transpose_ez(const float (&Ux)[27], const float (&Uy)[27],
+                                                 const float (&Uz)[27], float (&out)[27]) {
     float VB[27], VD[27];   // [a + 3 b + 9 lq]
     #pragma unroll
     for (int a = 0; a < 3; ++a)
         #pragma unroll
-        for (int lq = 0; lq < 3; ++lq)
-            #pragma unroll
-            for (int b = 0; b < 3; ++b) {
-                float vb = 0.f, vd = 0.f;
-                #pragma unroll
-                for (int qj = 0; qj < 3; ++qj) {
-                    const int r = a + 3 * qj + 9 * lq;
-                    vb += fB[qj][b] * Ux[r] + fBd[qj][b] * Uy[r];
-                    vd += fB[qj][b] * Uz[r];
-                }
-                VB[a + 3 * b + 9 * lq] = vb;
-                VD[a + 3 * b + 9 * lq] = vd;
-            }
-    #pragma unroll
-    for (int ab = 0; ab < 9; ++ab)
-        #pragma unroll
-        for (int l = 0; l < 3; ++l) {
-            float s = 0.f;
-            #pragma unroll
-            for (int lq = 0; lq < 3; ++lq) s += fB[lq][l] * VB[ab + 9 * lq] + fBd[lq][l] * VD[ab + 9 * lq];
-            out[ab + 9 * l] = s;
+        for (int lq = 0; lq < 3; ++lq) {
+            const int o = a + 9 * lq;
+            float b0, b1, b2, d0, d1, d2;
+            q2_bt(Ux[o], Ux[o + 3], Ux[o + 6], b0, b1, b2);
+            q2_dt(Uy[o], Uy[o + 3], Uy[o + 6], d0, d1, d2);
+            VB[o] = b0 + d0; VB[o + 3] = b1 + d1; VB[o + 6] = b2 + d2;
+            q2_bt(Uz[o], Uz[o + 3], Uz[o + 6], VD[o], VD[o + 3], VD[o + 6]);
         }
+    #pragma unroll
+    for (int ab = 0; ab < 9; ++ab) {
+        float b0, b1, b2, d0, d1, d2;
+        q2_bt(VB[ab], VB[ab + 9], VB[ab + 18], b0, b1, b2);
+        q2_dt(VD[ab], VD[ab + 9], VD[ab + 18], d0, d1, d2);
+        out[ab] = b0 + d0; out[ab + 9] = b1 + d1; out[ab + 18] = b2 + d2;
+    }
 }
 
 // Basal projector P on the bottom-plane nodes (l = 0) of the lane's element,
@@ -271,13 +277,15 @@ __global__ void __launch_bounds__(32 * CplCfg::W, CPL_MINB) cpl_state_apply_kern
         #pragma unroll
         for (int b = 0; b < NPR; ++b) pv[b] = pvn[b];
 
-        float Gx[27], Gy[27], Gz[27];
+        // zeta and eta stages of the forward sweeps (before the wait: they
+        // overlap the arrival of the staged state)
+        float BB[27], BD[27], DB[27];
         if constexpr (!PONLY) {
             float w[27];
             #pragma unroll
             for (int n = 0; n < 27; ++n) w[n] = wn[n];
             if (any_basal) cpl_project(a, w, pi, c, l1, l2);
-            cpl_forward(w, Gx, Gy, Gz);
+            cpl_forward_ze(w, BB, BD, DB);
         }
 
         if (!mbar_wait_polls(bar, uint32_t(it & 1), a.wait_polls)) {
@@ -294,31 +302,42 @@ __global__ void __launch_bounds__(32 * CplCfg::W, CPL_MINB) cpl_state_apply_kern
         float rows[NPR];
         #pragma unroll
         for (int b = 0; b < NPR; ++b) rows[b] = 0.f;
+        // per line r = qj + 3 lq of three Gauss points along xi: xi stage of
+        // the forward sweeps, pointwise stress, xi stage of the transposed
+        // sweeps (U indexed a + 3 qj + 9 lq)
+        float Ux[27], Uy[27], Uz[27];
         #pragma unroll
-        for (int lq = 0; lq < 3; ++lq)
+        for (int r = 0; r < 9; ++r) {
+            const int lq = r / 3, o = 3 * r;
+            float gx[3], gy[3], gz[3];
+            if constexpr (!PONLY) {
+                q2_d(BB[o], BB[o + 1], BB[o + 2], gx[0], gx[1], gx[2]);
+                q2_b(BD[o], BD[o + 1], BD[o + 2], gy[0], gy[1], gy[2]);
+                q2_b(DB[o], DB[o + 1], DB[o + 2], gz[0], gz[1], gz[2]);
+            }
+            float sx[3], sy[3], sz[3];
             #pragma unroll
-            for (int q9 = 0; q9 < 9; ++q9) {
-                const int qp = q9 + 9 * lq;
+            for (int qi = 0; qi < 3; ++qi) {
+                const int qp = qi + o, q9 = qi + 3 * (r % 3);
                 const float* F = buf + CPL_HDR + lq * CPL_PL + els * N2 + q9;
                 const float wdj = F[3 * CPL_FS];
                 const float z0 = F[c * CPL_FS], z1 = F[fz1 * CPL_FS], z2 = F[fz2 * CPL_FS];
                 float p = 0.f;
                 #pragma unroll
-                for (int b = 0; b < NPR; ++b) p += fPsi[PS][b][qp] * pv[b];
+                for (int b = 0; b < NPR; ++b) p += q2c::psi<PS>(b, qp) * pv[b];
                 const float pw = p * wdj;
                 if constexpr (PONLY) {
                     // tau = -p w detJ I: reference stress of component c is -pw Jinv[m][c]
-                    Gx[qp] = -pw * A0;
-                    Gy[qp] = -pw * B0;
-                    Gz[qp] = -pw * z0;
+                    sx[qi] = -pw * A0;
+                    sy[qi] = -pw * B0;
+                    sz[qi] = -pw * z0;
                 } else {
                     const float muw = F[4 * CPL_FS];
                     const float D0 = F[fd0 * CPL_FS], D1 = F[fd1 * CPL_FS], D2 = F[fd2 * CPL_FS];
-                    const float gx = Gx[qp], gy = Gy[qp], gz = Gz[qp];
                     // d_{c+d'} w_c
-                    const float dv0 = A0 * gx + B0 * gy + z0 * gz;
-                    const float dv1 = A1 * gx + B1 * gy + z1 * gz;
-                    const float dv2 = A2 * gx + B2 * gy + z2 * gz;
+                    const float dv0 = A0 * gx[qi] + B0 * gy[qi] + z0 * gz[qi];
+                    const float dv1 = A1 * gx[qi] + B1 * gy[qi] + z1 * gz[qi];
+                    const float dv2 = A2 * gx[qi] + B2 * gy[qi] + z2 * gz[qi];
                     // Dhat : D(w) = sum_c sum_d Dhat_cd d_d w_c (Dhat symmetric)
                     const float sc = D0 * dv0 + D1 * dv1 + D2 * dv2;
                     const float s = sc + __shfl_sync(0xffffffffu, sc, l1) + __shfl_sync(0xffffffffu, sc, l2);
@@ -330,15 +349,19 @@ __global__ void __launch_bounds__(32 * CplCfg::W, CPL_MINB) cpl_state_apply_kern
                     const float tau1 = 0.5f * muw * (dv1 + t1) - s * D1;
                     const float tau2 = 0.5f * muw * (dv2 + t2) - s * D2;
                     // reference stress of component c: sum_d Jinv[m][d] tau[c][d]
-                    Gx[qp] = A0 * tau0 + A1 * tau1 + A2 * tau2;
-                    Gy[qp] = B0 * tau0 + B1 * tau1 + B2 * tau2;
-                    Gz[qp] = z0 * tau0 + z1 * tau1 + z2 * tau2;
+                    sx[qi] = A0 * tau0 + A1 * tau1 + A2 * tau2;
+                    sy[qi] = B0 * tau0 + B1 * tau1 + B2 * tau2;
+                    sz[qi] = z0 * tau0 + z1 * tau1 + z2 * tau2;
                     // pressure rows -(psi_b, div w): this lane's share d_c w_c
                     const float gq = -wdj * dv0;
                     #pragma unroll
-                    for (int b = 0; b < NPR; ++b) rows[b] += fPsi[PS][b][qp] * gq;
+                    for (int b = 0; b < NPR; ++b) rows[b] += q2c::psi<PS>(b, qp) * gq;
                 }
             }
+            q2_dt(sx[0], sx[1], sx[2], Ux[o], Ux[o + 1], Ux[o + 2]);
+            q2_bt(sy[0], sy[1], sy[2], Uy[o], Uy[o + 1], Uy[o + 2]);
+            q2_bt(sz[0], sz[1], sz[2], Uz[o], Uz[o + 1], Uz[o + 2]);
+        }
         // the buffer has been read: refill it with the warp's next group
         __syncwarp();
         if (lane == 0 && g + gstride < ngroups) {
@@ -358,7 +381,7 @@ __global__ void __launch_bounds__(32 * CplCfg::W, CPL_MINB) cpl_state_apply_kern
         load_inputs(g + gstride);
 #endif
         float out[27];
-        cpl_transpose(Gx, Gy, Gz, out);
+        cpl_transpose_ez(Ux, Uy, Uz, out);
         if (any_basal) cpl_project(a, out, pi, c, l1, l2);
         if (active) cpl_nodes(a, e, true, [&](int n, int64_t gn) { atomic_add(y + 3 * gn + c, out[n]); });
     }

@@ -546,7 +546,12 @@ constexpr bool STATE_SHFL = K >= STOKES_STATE_SHFL_MIN_K;
 #define STOKES_STATE_PACKED 1
 #endif
 template <typename T> constexpr int STATE_PITCH = STOKES_STATE_PACKED ? N1 : LP<T>;
-template <typename T> constexpr int STATE_SLOT = STOKES_STATE_PACKED ? SLOT_PACKED<T> : SLOT<T>;
+// exchange slot of one element (the shuffle variant needs it only for the
+// pressure rows, 3 N3 values, the hanging-node sweeps and the basal tail;
+// consecutive slots start 16 banks apart)
+constexpr int SHFL_SLOT = (3 * N3 + 3) / 4 * 4 + ((((3 * N3 + 3) / 4 * 4) % 32 == 0) ? 16 : 0);
+template <typename T> constexpr int STATE_SLOT =
+    STATE_SHFL ? SHFL_SLOT : (STOKES_STATE_PACKED ? SLOT_PACKED<T> : SLOT<T>);
 // latency of the next group's gather hidden behind the current group:
 // 0 none, 1 L1 prefetch of the node lines (conforming lattice meshes)
 #ifndef STOKES_STATE_PREFETCH
@@ -560,10 +565,18 @@ template <typename T> constexpr int STATE_SLOT = STOKES_STATE_PACKED ? SLOT_PACK
 // contractions of the current group.
 template <typename T>
 struct StateApplyCfg {
+#ifdef STATE_W_F32
+    static constexpr int W = sizeof(T) == 8 ? 4 : STATE_W_F32;
+#else
     static constexpr int W = sizeof(T) == 8 ? 4 : 8;        // warps per block
+#endif
     // resident blocks per SM asked of the compiler: two for FP32 Q2 (128
     // registers); shared memory allows only one for k >= 3 and for FP64
+#ifdef STATE_MINB_F32
+    static constexpr int MINB = sizeof(T) == 4 ? STATE_MINB_F32 : 1;
+#else
     static constexpr int MINB = (sizeof(T) == 4 && K == 2) ? 2 : 1;
+#endif
     static constexpr int BUF = EPW * SSTRIDE;                // values per stage buffer
     static constexpr int SCR = (EPW + 1) * STATE_SLOT<T>;    // scratch per warp
     static constexpr int PER_WARP = ((2 * BUF + SCR) * int(sizeof(T)) + 127) / 128 * 128;
@@ -926,6 +939,22 @@ inline int upload_tables_any(const void* p) {
                             psi[sp][m][ii + Q * (jj + Q * l)] =
                                 float(P1[sp][ii][pm[sp][m][0]] * P1[sp][jj][pm[sp][m][1]] * P1[sp][l][pm[sp][m][2]]);
         if (e == cudaSuccess) e = cudaMemcpyToSymbol(fPsi, psi, sizeof(psi));
+        // the component-per-lane apply uses these tables as compile-time
+        // constants (q2c): refuse to run if the computed ones differ
+        const double S = std::sqrt(0.6);
+        const double Bx[3][3] = {{0.3 + 0.5 * S, 0.4, 0.3 - 0.5 * S}, {0, 1, 0}, {0.3 - 0.5 * S, 0.4, 0.3 + 0.5 * S}};
+        const double Dx[3][3] = {{-S - 0.5, 2 * S, 0.5 - S}, {-0.5, 0, 0.5}, {S - 0.5, -2 * S, S + 0.5}};
+        const double G[3] = {-S, 0.0, S};
+        bool same = t[0].npr == 4 && t[1].npr == 1;
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b)
+                same = same && std::fabs(B[a][b] - Bx[a][b]) < 1e-13 && std::fabs(Bdv[a][b] - Dx[a][b]) < 1e-13;
+        for (int qp = 0; qp < Q3 && same; ++qp) {
+            const double ex[4] = {1.0, G[qp % 3], G[(qp / 3) % 3], G[qp / 9]};
+            for (int m = 0; m < 4; ++m) same = same && std::fabs(psi[0][m][qp] - ex[m]) < 1e-6;
+            same = same && std::fabs(psi[1][0][qp] - 1.0) < 1e-6;
+        }
+        if (e == cudaSuccess && !same) e = cudaErrorInvalidValue;
     }
 #endif
     return int(e);
