@@ -88,17 +88,33 @@ typedef struct {
 /* Mesh description (all host memory, read during stokes_mesh_create only).
  * Geometry: x = Lx X / nx, y = Ly Y / ny, z = bed + (Z / nz)(surface - bed),
  * evaluated at the GLL nodes of each coarse cell (isoparametric map); refined
- * children inherit the parent map (Section 3.1). */
+ * children inherit the parent map (Section 3.1).
+ * Meshes are extruded columns: x and y are affine in each cell and only z
+ * follows the bed and surface, so the inverse Jacobian has the rows
+ * (1/a, 0, 0), (0, 1/b, 0) and one general third row; the stored linearised
+ * state and its applies rely on this (p6est-type meshes of thin ice).
+ * Bed and surface come from the modal fields, or, when bed_nodes and
+ * surface_nodes are non-NULL, from heights given on the horizontal GLL
+ * lattice of the coarse grid: point (X, Y), X = k cx + i, Y = k cy + j, at
+ * x = Lx (cx + (xi_i + 1)/2) / nx, y = Ly (cy + (xi_j + 1)/2) / ny (xi_i the
+ * GLL nodes of degree k), stored [Y][X] with X fastest; NX = k nx + 1,
+ * NY = k ny + 1 points, or k nx and k ny on periodic meshes (X = k nx is
+ * X = 0).  A gridded bed is interpolated by the degree-k map like any
+ * other. */
 typedef struct {
     int nx, ny, nz;               /* coarse hexahedral grid                     */
-    int k;                        /* velocity degree, 1 <= k <= 5                */
+    int k;                        /* velocity degree: 1 <= k <= 9 for host-only
+                                     meshes (device = -1), 2 <= k <= 4 on a
+                                     device (the kernels' degrees)              */
     int pressure_space;           /* STOKES_PRESSURE_P or STOKES_PRESSURE_Q      */
     int periodic_xy;              /* 1: periodic in x and y                      */
     double Lx, Ly;                /* horizontal extent                           */
     stokes_field bed, surface;
     const uint8_t* refine;        /* [nx*ny*nz] 1 = split once into 8, or NULL   */
     int basal_bc;                 /* STOKES_BASE_NOSLIP or STOKES_BASE_SLIP      */
-    int device;                   /* CUDA device ordinal                         */
+    int device;                   /* CUDA device ordinal, or -1: host-only mesh  */
+    const double* bed_nodes;      /* optional gridded bed [NY][NX], or NULL      */
+    const double* surface_nodes;  /* optional gridded surface [NY][NX], or NULL  */
 } stokes_mesh_desc;
 
 /* Physical parameters.  mu = C0 A^(-1/n) (gamma D:D + delta)^((1-n)/(2n));

@@ -40,7 +40,8 @@ class stokes_mesh_desc(C.Structure):
                 ("pressure_space", C.c_int), ("periodic_xy", C.c_int),
                 ("Lx", C.c_double), ("Ly", C.c_double),
                 ("bed", stokes_field), ("surface", stokes_field),
-                ("refine", C.POINTER(C.c_uint8)), ("basal_bc", C.c_int), ("device", C.c_int)]
+                ("refine", C.POINTER(C.c_uint8)), ("basal_bc", C.c_int), ("device", C.c_int),
+                ("bed_nodes", C.POINTER(C.c_double)), ("surface_nodes", C.POINTER(C.c_double))]
 
 
 class stokes_params(C.Structure):

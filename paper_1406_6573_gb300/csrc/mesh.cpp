@@ -137,6 +137,9 @@ int build_host_mesh(const stokes_mesh_desc& d, HostMesh& m, std::string& err) {
         (d.surface.n_modes > 0 && (!d.surface.amp || !d.surface.kx || !d.surface.ky || !d.surface.phase))) {
         err = "field with modes but NULL coefficient arrays"; return STOKES_E_INVAL;
     }
+    if ((d.bed_nodes == nullptr) != (d.surface_nodes == nullptr)) {
+        err = "bed_nodes and surface_nodes must be given together"; return STOKES_E_INVAL;
+    }
     const int64_t ncoarse = int64_t(d.nx) * d.ny * d.nz;
     if (ncoarse > (int64_t(1) << 31) / 8) { err = "grid too large"; return STOKES_E_INVAL; }
 
@@ -308,8 +311,17 @@ int build_host_mesh(const stokes_mesh_desc& d, HostMesh& m, std::string& err) {
         for (int64_t hx = 0; hx < HX; ++hx) {
             int cx = int(hx / n1), i = int(hx % n1);
             double x = m.Lx * (double(cx) + B.t[i]) / m.nx;
-            bedH[size_t(hy * HX + hx)] = eval_field(d.bed, x, y);
-            surfH[size_t(hy * HX + hx)] = eval_field(d.surface, x, y);
+            if (d.bed_nodes) {
+                // gridded heights on the horizontal GLL lattice
+                const int64_t NXg = int64_t(m.nx) * k + (m.periodic ? 0 : 1);
+                int64_t X = int64_t(cx) * k + i, Y = int64_t(cy) * k + j;
+                if (m.periodic) { X %= int64_t(m.nx) * k; Y %= int64_t(m.ny) * k; }
+                bedH[size_t(hy * HX + hx)] = d.bed_nodes[size_t(Y * NXg + X)];
+                surfH[size_t(hy * HX + hx)] = d.surface_nodes[size_t(Y * NXg + X)];
+            } else {
+                bedH[size_t(hy * HX + hx)] = eval_field(d.bed, x, y);
+                surfH[size_t(hy * HX + hx)] = eval_field(d.surface, x, y);
+            }
         }
     }
     m.geo.assign(size_t(E) * 10 * Q3, 0.0);

@@ -16,8 +16,10 @@ def _field(f, keep):
     return capi.stokes_field(float(f.mean), int(arrs[0].size), *ptrs)
 
 
-def mesh_desc(wl, device=0, force_general=False):
-    """stokes_mesh_desc of a workload (stokes_synth.Workload); returns (desc, keepalive)."""
+def mesh_desc(wl, device=0, force_general=False, grid=None):
+    """stokes_mesh_desc of a workload (stokes_synth.Workload); returns (desc, keepalive).
+    grid: optional (bed_nodes, surface_nodes) height arrays on the horizontal GLL
+    lattice ([NY][NX], X fastest), used instead of the workload's modal fields."""
     keep = []
     d = capi.stokes_mesh_desc()
     d.nx, d.ny, d.nz, d.k = wl.nx, wl.ny, wl.nz, wl.k
@@ -33,15 +35,20 @@ def mesh_desc(wl, device=0, force_general=False):
         d.refine = mask.ctypes.data_as(C.POINTER(C.c_uint8))
     d.basal_bc = capi.STOKES_BASE_NOSLIP if wl.phys.basal_bc == "noslip" else capi.STOKES_BASE_SLIP
     d.device = device
+    if grid is not None:
+        P = C.POINTER(C.c_double)
+        arrs = [np.ascontiguousarray(g, dtype=np.float64).ravel() for g in grid]
+        keep.extend(arrs)
+        d.bed_nodes, d.surface_nodes = (a.ctypes.data_as(P) for a in arrs)
     return d, keep
 
 
 class Mesh:
     """Owns a stokes_mesh handle (device = -1: host-only, for inspection)."""
 
-    def __init__(self, wl, device=0, force_general=False):
+    def __init__(self, wl, device=0, force_general=False, grid=None):
         self.wl = wl
-        d, keep = mesh_desc(wl, device, force_general)
+        d, keep = mesh_desc(wl, device, force_general, grid)
         self.handle = capi.stokes_mesh_create(d)
         del keep
         s = capi.stokes_mesh_sizes(self.handle)

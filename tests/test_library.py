@@ -144,3 +144,51 @@ def test_wait_limit_hook_needs_a_device_mesh():
     with pytest.raises(capi.StokesError) as e:
         capi.stokes_debug_wait_limit(m.handle, 0)
     assert e.value.code == -1
+
+
+class _GridLookup:
+    """Bed or surface heights given at the horizontal lattice points (x, y)
+    of a mesh, looked up by position (a callable like a modal field)."""
+
+    def __init__(self, xy, values, period=None):
+        self.period = period
+        self.table = {(round(float(x), 9), round(float(y), 9)): float(v) for (x, y), v in zip(xy, values)}
+
+    def __call__(self, x, y):
+        x, y = np.broadcast_arrays(np.asarray(x, dtype=np.float64), np.asarray(y, dtype=np.float64))
+        if self.period is not None:      # periodic meshes evaluate at x = Lx, y = Ly too
+            x = np.where(np.isclose(x, self.period[0]), 0.0, x)
+            y = np.where(np.isclose(y, self.period[1]), 0.0, y)
+        out = np.array([self.table[(round(float(a), 9), round(float(b), 9))] for a, b in zip(x.ravel(), y.ravel())])
+        return out.reshape(x.shape)
+
+
+@pytest.mark.parametrize("name", ["cbox_3x3x2_q2p1", "slab_5x3x3_q2p1", "cbox_3x3x2_q3q1"])
+def test_gridded_geometry(name):
+    """Heights given on the horizontal GLL lattice (stokes_mesh_desc.bed_nodes,
+    surface_nodes): sampled from the modal fields they give the modal mesh
+    exactly; a random gridded bed gives the oracle's mesh built on the same
+    heights."""
+    import dataclasses
+    wl = synth.workload(name)
+    a = Mesh(wl, device=-1)
+    xyz = a.node_coords()
+    bxy = xyz[a.basal_nodes(), :2]            # the lattice, [Y][X] order (X fastest)
+    bed = wl.bed(bxy[:, 0], bxy[:, 1])
+    surf = wl.surface(bxy[:, 0], bxy[:, 1])
+    b = Mesh(wl, device=-1, grid=(bed, surf))
+    # equal up to the rounding of the modal series at x = Lx vs its wrapped x = 0
+    np.testing.assert_allclose(a.node_coords(), b.node_coords(), rtol=0,
+                               atol=1e-12 * max(wl.Lx, np.abs(surf).max()))
+    rng = np.random.default_rng(9)
+    rbed = bed + rng.uniform(-0.02, 0.02, size=bed.shape) * (surf - bed)
+    c = Mesh(wl, device=-1, grid=(rbed, surf))
+    per = (wl.Lx, wl.Ly) if wl.periodic else None
+    o = OracleMesh(dataclasses.replace(wl, bed=_GridLookup(bxy, rbed, per), surface=_GridLookup(bxy, surf, per)))
+    assert c.Nv == o.Nv
+    assert np.abs(c.node_coords()[:, 2] - o.node_coords()[:, 2]).max() < 1e-12 * max(1.0, np.abs(surf).max())
+    np.testing.assert_array_equal(c.basal_nodes(), o.basal)
+    with pytest.raises(capi.StokesError):
+        d, keep = mesh_desc(wl, device=-1, grid=(rbed, surf))
+        d.surface_nodes = None
+        capi.stokes_mesh_create(d)
