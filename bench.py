@@ -362,7 +362,17 @@ def run_ours(args):
     refined = bool(wl.refine_mask().any())
     n_faces = int(wl.nx * wl.ny + 3 * mask.sum())
     q2 = (wl.k + 1) ** 2
-    bytes_basal = (n_faces * (4 * q2 * 8 + q2 * 4) + mesh.Nb * (8 + 4 + 48)) if wl.phys.robin else mesh.Nb * 52
+    cpl = wl.k == 2 and not refined
+    if cpl:
+        # component-per-lane kernel: basal Robin term of the basal elements in
+        # the element pass from the FP32 basal state (beta w |J_s|, n: 4 values
+        # per face Gauss point; 10 with the nonlinear sliding law), the face
+        # index and the FP32 projector rows of the basal elements; constraint
+        # rows: basal node list and FP64 projector
+        nf = 10 if getattr(wl.phys, "sliding_m", 1.0) not in (0.0, 1.0) else 4
+        bytes_basal = (n_faces * (nf * q2 * 4 + 4 + 6 * q2 * 4) if wl.phys.robin else 0) + mesh.Nb * (4 + 48)
+    else:
+        bytes_basal = (n_faces * (4 * q2 * 8 + q2 * 4) + mesh.Nb * (8 + 4 + 48)) if wl.phys.robin else mesh.Nb * 52
     bytes_desc = mesh.E * 4 + (mesh.E * (n3 * 4 + 4) if refined else 0)
     bytes_alg = mesh.E * sstride * 4 + 2 * ndof * 4 + bytes_desc + bytes_basal
     achieved = bytes_alg / el_avg_s / 1e9

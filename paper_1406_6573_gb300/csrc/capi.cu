@@ -197,7 +197,7 @@ size_t vec_bytes(const stokes_mesh* m, int prec) {
 
 int operator_sequence(const stokes_mesh* m, const stokes_params* p, int mode, int prec, int state_prec,
                       bool trans, const void* x, const void* u, const void* cstate, void* y, cudaStream_t s,
-                      int state_cpl, const void* fstate) {
+                      int state_cpl, const void* fstate, const void* fstate_elements) {
     int e = timed(m, 0, s, [&] { return int(cudaMemsetAsync(y, 0, vec_bytes(m, prec), s)); });
     if (e) return cuda_fail(cudaError_t(e), "clearing the output");
     ElemArgs a = elem_args(m, p);
@@ -211,6 +211,14 @@ int operator_sequence(const stokes_mesh* m, const stokes_params* p, int mode, in
         a.face.x = x; a.face.y = y;
         a.face.fstate = fstate;   // the sliding law linearised with the state
         a.fuse_robin = robin;
+        if (robin && fstate_elements) {
+            // the component-per-lane kernel adds the face term of its basal
+            // elements in the element pass, from the stored basal state
+            a.face.fstate = fstate_elements;
+            a.face_in_elements = 1;
+            a.fuse_robin = 0;
+            a.fidx = m->d_fidx;
+        }
         a.fuse_constraint = 1;
         a.Nb = m->h.Nb; a.basal_nodes = m->d_basal_nodes; a.basal_P = m->d_basal_P;
         a.cscale = p->constraint_scale;
@@ -521,13 +529,14 @@ int stokes_linearize(stokes_state* state, const stokes_params* params, const dou
     });
     if (e) return cuda_fail(cudaError_t(e), "linearize kernel launch");
     state->slide = sliding_nonlinear(params) && mesh->h.nF > 0;
-    if (state->slide) {
+    state->face_lin = params->robin && mesh->h.nF > 0;
+    if (state->face_lin) {
         FaceArgs f = face_args(mesh, params);
         f.u = up_lin;
         f.fstate_out = state->d_fstate;
         f.fstate_f32 = state->prec == STOKES_F32;
         e = timed(mesh, PROF_FACE, s, [&] { return launch_face(mesh->h.k, FACE_LINEARIZE, STOKES_F64, f, s); });
-        if (e) return cuda_fail(cudaError_t(e), "sliding linearisation kernel launch");
+        if (e) return cuda_fail(cudaError_t(e), "basal linearisation kernel launch");
     }
     state->params = *params;
     state->linearized = true;
@@ -547,7 +556,8 @@ static int state_apply_common(const stokes_state* state, const void* x, void* y,
     if (g.err != cudaSuccess) return cuda_fail(g.err, "selecting the device");
     return operator_sequence(mesh, &state->params, mode, state->prec, state->prec, trans, x,
                              nullptr, state->d_state, y, static_cast<cudaStream_t>(stream), state->cpl,
-                             state->slide ? state->d_fstate : nullptr);
+                             state->slide ? state->d_fstate : nullptr,
+                             state->cpl && state->face_lin ? state->d_fstate : nullptr);
 }
 
 int stokes_state_apply(const stokes_state* state, const void* x, void* y, void* stream) {

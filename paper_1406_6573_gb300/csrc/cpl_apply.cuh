@@ -41,9 +41,16 @@ namespace STOKES_NS {
 #ifndef CPL_PREFETCH
 #define CPL_PREFETCH 1
 #endif
+// the streamed state is copied with an L2 evict-first policy, so that x and
+// y stay in L2 (128x128x8 Q2xP1 slab: 0.0685 -> 0.0649 ms)
+#ifndef CPL_STATE_EVICT_FIRST
+#define CPL_STATE_EVICT_FIRST 1
+#endif
 struct CplCfg {
     static constexpr int W = CPL_WARPS;                  // warps per block
-    static constexpr int TAIL = (EPW + 1) * 4 * N2;      // basal face scratch per warp (values)
+    // basal face scratch per warp (values): the face tail's element slots,
+    // or 9 bottom-plane values per lane for the face term in the element pass
+    static constexpr int TAIL = (EPW + 1) * 4 * N2 > 9 * 32 ? (EPW + 1) * 4 * N2 : 9 * 32;
     static constexpr int PER_WARP = (CPL_GROUP + TAIL) * 4;   // bytes
     static constexpr int SMEM = W * PER_WARP + W * 8;
     static_assert(PER_WARP % 16 == 0, "stage buffers 16-byte aligned");
@@ -171,6 +178,55 @@ __device__ __forceinline__ void cpl_project(const ElemArgs& a, float (&v)[27], i
     }
 }
 
+// Basal Robin term (Eqs. 2.4-2.5) of the lane's element, component c, from
+// the projected nodal values w (bottom plane l = 0 of a basal element): the
+// values at the 3 x 3 face Gauss points (B x B), the traction
+// t_c = bws (v_c - (n . v) n_c) + (vv . v) Tu_c with the stored basal state
+// (bws = beta w |J_s| s, vv = 2 beta w |J_s| s' T u and T u of the nonlinear
+// sliding law, n the unit normal), and the transposed interpolation back to
+// the 9 bottom-plane nodes, written to the lane's scratch scr[n * 32].  The
+// whole warp executes it (the n . v and vv . v sums are lane-triplet
+// shuffles); lanes of elements without a basal face write zeros.
+__device__ __forceinline__ void cpl_face(const ElemArgs& a, const float (&w)[27], int64_t e, bool active, int c,
+                                         int l1, int l2, float* scr) {
+    const int f = active ? a.fidx[e] : -1;
+    const bool has = f >= 0;
+    float T[9], vq[9];
+    #pragma unroll
+    for (int a3 = 0; a3 < 3; ++a3) q2_b(w[a3], w[a3 + 3], w[a3 + 6], T[a3], T[a3 + 3], T[a3 + 6]);
+    #pragma unroll
+    for (int qj = 0; qj < 3; ++qj)
+        q2_b(T[3 * qj], T[3 * qj + 1], T[3 * qj + 2], vq[3 * qj], vq[3 * qj + 1], vq[3 * qj + 2]);
+    const float* F = static_cast<const float*>(a.face.fstate) + int64_t(has ? f : 0) * SLIDE_FIELDS * 9;
+    float t[9];
+    #pragma unroll
+    for (int q = 0; q < 9; ++q) {
+        const float bws = has ? ld(F + q) : 0.f;
+        const float nc = has ? ld(F + (7 + c) * 9 + q) : 0.f;
+        const float nv0 = nc * vq[q];
+        const float nv = nv0 + __shfl_sync(0xffffffffu, nv0, l1) + __shfl_sync(0xffffffffu, nv0, l2);
+        float tq = bws * fmaf(-nv, nc, vq[q]);
+        if (a.face.slide) {
+            const float vvc = has ? ld(F + (1 + c) * 9 + q) : 0.f;
+            const float tuc = has ? ld(F + (4 + c) * 9 + q) : 0.f;
+            const float vw0 = vvc * vq[q];
+            const float vw = vw0 + __shfl_sync(0xffffffffu, vw0, l1) + __shfl_sync(0xffffffffu, vw0, l2);
+            tq = fmaf(vw, tuc, tq);
+        }
+        t[q] = tq;
+    }
+    #pragma unroll
+    for (int qj = 0; qj < 3; ++qj) q2_bt(t[3 * qj], t[3 * qj + 1], t[3 * qj + 2], T[3 * qj], T[3 * qj + 1], T[3 * qj + 2]);
+    #pragma unroll
+    for (int a3 = 0; a3 < 3; ++a3) {
+        float o0, o1, o2;
+        q2_bt(T[a3], T[a3 + 3], T[a3 + 6], o0, o1, o2);
+        scr[a3 * 32] = o0;
+        scr[(a3 + 3) * 32] = o1;
+        scr[(a3 + 6) * 32] = o2;
+    }
+}
+
 // f(n, global node) for the 27 local nodes n = a + 3 b + 9 l of element e:
 // from the lattice (conforming structured meshes) or the element map
 template <typename F>
@@ -238,7 +294,11 @@ __global__ void __launch_bounds__(32 * CplCfg::W, CPL_MINB) cpl_state_apply_kern
                 bulk_g2s(buf + CPL_HDR + lq * CPL_PL, src + CPL_HDR + lq * CPL_PL, 4 * CPL_FS * 4, bar);
         } else {
             mbar_arrive_expect_tx(bar, uint32_t(CPL_GROUP) * 4u);
+#if CPL_STATE_EVICT_FIRST
+            bulk_g2s_hint(buf, src, CPL_GROUP * 4, bar, l2_evict_first_policy());
+#else
             bulk_g2s(buf, src, CPL_GROUP * 4, bar);
+#endif
         }
     };
     if (lane == 0) {
@@ -280,11 +340,15 @@ __global__ void __launch_bounds__(32 * CplCfg::W, CPL_MINB) cpl_state_apply_kern
         // zeta and eta stages of the forward sweeps (before the wait: they
         // overlap the arrival of the staged state)
         float BB[27], BD[27], DB[27];
+        // basal Robin term in the element pass (face scratch of the lane)
+        const bool face_here = !PONLY && a.face_in_elements && any_basal;
+        float* fscr = reinterpret_cast<float*>(smem_raw + warp * C::PER_WARP) + CPL_GROUP + lane;
         if constexpr (!PONLY) {
             float w[27];
             #pragma unroll
             for (int n = 0; n < 27; ++n) w[n] = wn[n];
             if (any_basal) cpl_project(a, w, pi, c, l1, l2);
+            if (face_here) cpl_face(a, w, e, active, c, l1, l2, fscr);
             cpl_forward_ze(w, BB, BD, DB);
         }
 
@@ -382,6 +446,10 @@ __global__ void __launch_bounds__(32 * CplCfg::W, CPL_MINB) cpl_state_apply_kern
 #endif
         float out[27];
         cpl_transpose_ez(Ux, Uy, Uz, out);
+        if (face_here) {
+            #pragma unroll
+            for (int n = 0; n < 9; ++n) out[n] += fscr[n * 32];
+        }
         if (any_basal) cpl_project(a, out, pi, c, l1, l2);
         if (active) cpl_nodes(a, e, true, [&](int n, int64_t gn) { atomic_add(y + 3 * gn + c, out[n]); });
     }

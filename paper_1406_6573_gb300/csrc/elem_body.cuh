@@ -465,10 +465,10 @@ __device__ __forceinline__ void face_group(const FaceArgs& a, const LaneMap& L, 
         face_interp<T, 3>(R, v, uq, i, j, sb);
         const T nu = n0 * uq[0] + n1 * uq[1] + n2 * uq[2];
         const T tu[3] = {uq[0] - nu * n0, uq[1] - nu * n1, uq[2] - nu * n2};
-        T ds;
-        const T sv = slide_s(tu[0] * tu[0] + tu[1] * tu[1] + tu[2] * tu[2], ds);
+        T ds = T(0), sv = T(1);       // linear law: s = 1, s' = 0
+        if (a.slide) sv = slide_s(tu[0] * tu[0] + tu[1] * tu[1] + tu[2] * tu[2], ds);
         const T vals[SLIDE_FIELDS] = {bw * sv, T(2) * ds * bw * tu[0], T(2) * ds * bw * tu[1],
-                                      T(2) * ds * bw * tu[2], tu[0], tu[1], tu[2]};
+                                      T(2) * ds * bw * tu[2], tu[0], tu[1], tu[2], n0, n1, n2};
         if (active) {
             const int64_t o0 = f * SLIDE_FIELDS * Q2 + fq;
             #pragma unroll
@@ -557,6 +557,11 @@ template <typename T> constexpr int STATE_SLOT =
 #ifndef STOKES_STATE_PREFETCH
 #define STOKES_STATE_PREFETCH 1
 #endif
+// the streamed state copied with an L2 evict-first policy (off: on the
+// 64x64x4 Q3xQ1 slab 0.0491 ms with it against 0.0472 ms without)
+#ifndef STOKES_STATE_EVICT_FIRST
+#define STOKES_STATE_EVICT_FIRST 0
+#endif
 // y = J x from the stored linearised state.  Persistent: each warp walks its
 // element groups (EPW consecutive elements); the state block of the next
 // group (contiguous, 16-byte multiple) is staged into shared memory by a bulk
@@ -565,17 +570,20 @@ template <typename T> constexpr int STATE_SLOT =
 // contractions of the current group.
 template <typename T>
 struct StateApplyCfg {
+    // warps per block and resident blocks per SM asked of the compiler
+    // (measured on the 64x64x4 slabs and forest): FP32 k = 2 (hanging-node
+    // meshes) 8 x 2 at 128 registers; FP32 k = 3 4 x 4 (128 registers, 16
+    // warps per SM: 0.059 -> 0.048 ms on the Q3xQ1 slab, forest 0.381 ->
+    // 0.284 ms); FP32 k = 4 4 x 3 (168 registers: 0.196 -> 0.166 ms); FP64 4 x 1
 #ifdef STATE_W_F32
     static constexpr int W = sizeof(T) == 8 ? 4 : STATE_W_F32;
 #else
-    static constexpr int W = sizeof(T) == 8 ? 4 : 8;        // warps per block
+    static constexpr int W = sizeof(T) == 8 ? 4 : (K == 2 ? 8 : 4);
 #endif
-    // resident blocks per SM asked of the compiler: two for FP32 Q2 (128
-    // registers); shared memory allows only one for k >= 3 and for FP64
 #ifdef STATE_MINB_F32
     static constexpr int MINB = sizeof(T) == 4 ? STATE_MINB_F32 : 1;
 #else
-    static constexpr int MINB = (sizeof(T) == 4 && K == 2) ? 2 : 1;
+    static constexpr int MINB = sizeof(T) == 8 ? 1 : (K == 2 ? 2 : (K == 3 ? 4 : 3));
 #endif
     static constexpr int BUF = EPW * SSTRIDE;                // values per stage buffer
     static constexpr int SCR = (EPW + 1) * STATE_SLOT<T>;    // scratch per warp
@@ -630,7 +638,11 @@ __global__ void __launch_bounds__(32 * StateApplyCfg<T>::W, StateApplyCfg<T>::MI
         } else {
             const uint32_t nb = uint32_t(ne * SSTRIDE * int64_t(sizeof(T)));
             mbar_arrive_expect_tx(&bar[b], nb);
+#if STOKES_STATE_EVICT_FIRST
+            bulk_g2s_hint(stage(b), S + gg * EPW * SSTRIDE, nb, &bar[b], l2_evict_first_policy());
+#else
             bulk_g2s(stage(b), S + gg * EPW * SSTRIDE, nb, &bar[b]);
+#endif
         }
     };
     if (lane == 0) {

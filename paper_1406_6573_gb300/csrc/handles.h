@@ -113,6 +113,8 @@ struct stokes_state {
     int cpl = 0;               // group layout, applied by the component-per-lane kernel
     void* d_fstate = nullptr;  // stored sliding state [nF][SLIDE_FIELDS][q^2] (nonlinear sliding law)
     int slide = 0;             // the last linearisation used the nonlinear sliding law
+    int face_lin = 0;          // d_fstate holds the basal state of the last linearisation
+                               // (Robin term on; both sliding laws)
     stokes_params params{};
     bool linearized = false;
 };
@@ -127,7 +129,8 @@ size_t vec_bytes(const stokes_mesh* m, int prec);
 // y = (element terms of x) + Robin(x) + (I - P) x ; mode selects the element term
 int operator_sequence(const stokes_mesh* m, const stokes_params* p, int mode, int prec, int state_prec,
                       bool trans, const void* x, const void* u, const void* cstate, void* y, cudaStream_t s,
-                      int state_cpl = 0, const void* fstate = nullptr);
+                      int state_cpl = 0, const void* fstate = nullptr,
+                      const void* fstate_elements = nullptr);
 // the nonlinear sliding law is in use (robin term, sliding_m not 0 or 1)
 inline bool sliding_nonlinear(const stokes_params* p) {
     return p && p->robin && p->sliding_m != 0.0 && p->sliding_m != 1.0;

@@ -62,10 +62,12 @@ struct FaceArgs {
     void* fstate_out;          // linearisation output (fstate_f32: float, else double)
     int fstate_f32;
 };
-// stored sliding state per basal Gauss point: beta w s, then
+// stored basal state per basal Gauss point: beta w s, then
 // v = 2 beta w s' T u (3) and T u (3): the Jacobian's face term on w is
-// beta w s T w + (v . w) T u
-constexpr int SLIDE_FIELDS = 7;
+// beta w s T w + (v . w) T u; then the unit normal n (3) of the face at the
+// point (read by the component-per-lane apply, which adds the face term of
+// its basal elements in the element pass).  Linear law: s = 1, v = 0.
+constexpr int SLIDE_FIELDS = 10;
 
 struct ElemArgs {
     int64_t E, Nv;
@@ -102,6 +104,11 @@ struct ElemArgs {
     // (one launch per apply): the Robin term (face, fuse_robin) and the
     // constraint rows s (I - P) x at the Nb basal nodes (fuse_constraint)
     int fuse_robin, fuse_constraint;
+    // component-per-lane apply: basal Robin term of the basal elements added
+    // in the element pass from the stored basal state (face.fstate), instead
+    // of the face tail; fidx: basal face of each element (-1 if none)
+    int face_in_elements;
+    const int32_t* fidx;
     FaceArgs face;
     int64_t Nb;
     const int32_t* basal_nodes;
