@@ -35,10 +35,46 @@ UNIT = "MDoF/s"
 STATE_FIELDS = 11
 
 
-# DRAM bytes (read + write) of one launch of the stored-state apply kernel,
-# from the ncu capture summarised under profiles/ for that workload; only
-# valid for the kernel source that capture was taken from.
-STATE_APPLY_TRAFFIC = {"slab_128x128x8_q2p1": 210148608 + 10277120}
+# Sources that define the stored-state apply kernels: a capture's DRAM
+# traffic is reported only while their hash equals the one recorded with it.
+KERNEL_SOURCES = ["include/stokes.h"] + [
+    "paper_1406_6573_gb300/csrc/" + f for f in
+    ("common.h", "kernels.h", "hanging.h", "tma.cuh", "elem_kernels.cuh", "elem_body.cuh", "cpl_apply.cuh",
+     "k2.cu", "k3.cu", "k4.cu", "capi.cu")]
+
+
+def kernel_source_sha():
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def captured_traffic(kernel, workload):
+    """DRAM bytes (read + write) per launch of `kernel` on `workload` from the
+    ncu summaries under profiles/ (a line 'traffic-record: {json}' written
+    with the capture), or (None, reason) if no capture of the current kernel
+    source exists."""
+    sha = kernel_source_sha()
+    pdir = os.path.join(ROOT, "profiles")
+    stale = None
+    for name in sorted(os.listdir(pdir)) if os.path.isdir(pdir) else []:
+        if not name.endswith(".md"):
+            continue
+        for line in open(os.path.join(pdir, name)):
+            if not line.startswith("traffic-record:"):
+                continue
+            try:
+                rec = json.loads(line.split(":", 1)[1])
+            except ValueError:
+                continue
+            if rec.get("kernel") == kernel and rec.get("workload") == workload:
+                if rec.get("source_sha") == sha:
+                    return int(rec["dram_bytes_per_launch"]), f"profiles/{name}"
+                stale = f"profiles/{name} (kernel source changed since that capture)"
+    return None, stale or "no capture of this kernel and workload"
 
 
 def state_stride(k):
@@ -376,6 +412,9 @@ def run_ours(args):
     bytes_desc = mesh.E * 4 + (mesh.E * (n3 * 4 + 4) if refined else 0)
     bytes_alg = mesh.E * sstride * 4 + 2 * ndof * 4 + bytes_desc + bytes_basal
     achieved = bytes_alg / el_avg_s / 1e9
+    kname = ("cpl_state_apply_kernel<%d,false>" % (0 if wl.pspace == "P" else 1)
+             if (wl.k == 2 and not refined) else "state_apply_kernel<float,false>")
+    traffic, traffic_src = captured_traffic(kname, wl.name)
     shares = {k: v[1] for k, v in prof.items()}
     tot = sum(shares.values())
 
@@ -543,9 +582,9 @@ def run_ours(args):
             "gpu_launches": int(prof["element"][0] + prof["face"][0] + prof["constraint"][0]),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                          "frac": achieved / hbm_peak,
-                         "traffic": STATE_APPLY_TRAFFIC.get(wl.name),
-                         "kernel": ("cpl_state_apply_kernel<%d,false>" % (0 if wl.pspace == "P" else 1)
-                                    if (wl.k == 2 and not refined) else "state_apply_kernel<float,false>"),
+                         "traffic": traffic,
+                         "traffic_source": traffic_src,
+                         "kernel": kname,
                          "bytes_per_launch": bytes_alg, "avg_launch_ms": el_avg_s * 1e3,
                          "peak_source": f"{peak_src} hbm_gbs"},
             "kernel_time_share": {k: round(v / tot, 4) for k, v in shares.items()} if tot > 0 else {},
