@@ -297,6 +297,12 @@ typedef struct {
     int max_newton;      /* Newton steps (default 50)                                 */
     double rtol;         /* Newton stop: ||r|| <= rtol ||r_0|| (default 1e-10)        */
     double eta_max;      /* cap of the forcing term (default 0.1)                     */
+    int velocity_mg;     /* 1: the velocity block of the preconditioner is a geometric
+                            multigrid V-cycle (horizontal semi-coarsening that keeps the
+                            node columns, as the paper's column-preserving aggregation
+                            of Section 5; column-block smoother) on conforming Q2 meshes
+                            with nx, ny even and >= 4; other meshes, and 0 (default),
+                            use the column blocks alone                            */
 } stokes_solver_opts;
 
 typedef struct {
@@ -308,6 +314,7 @@ typedef struct {
     int line_search_failed;      /* 1: twelve step halvings gave no decrease of ||r||;
                                     the step was rejected, up holds the last accepted
                                     iterate and the solve returned STOKES_E_NOCONV */
+    int mg_levels;               /* levels of the velocity multigrid (0: column blocks) */
 } stokes_solve_report;
 
 int stokes_solver_create(const stokes_mesh* mesh, const stokes_solver_opts* opts, stokes_solver** out);

@@ -71,14 +71,15 @@ class stokes_profile(C.Structure):
 
 class stokes_solver_opts(C.Structure):
     _fields_ = [("inner_prec", C.c_int), ("restart", C.c_int), ("max_krylov", C.c_int),
-                ("max_newton", C.c_int), ("rtol", C.c_double), ("eta_max", C.c_double)]
+                ("max_newton", C.c_int), ("rtol", C.c_double), ("eta_max", C.c_double),
+                ("velocity_mg", C.c_int)]
 
 
 class stokes_solve_report(C.Structure):
     _fields_ = [("converged", C.c_int), ("newton_its", C.c_int), ("krylov_its", C.c_int),
                 ("line_search_cuts", C.c_int), ("res0", C.c_double), ("res_final", C.c_double),
                 ("seconds", C.c_double), ("constraint_scale", C.c_double), ("history", C.c_double * 64),
-                ("krylov_per_newton", C.c_int * 64), ("line_search_failed", C.c_int)]
+                ("krylov_per_newton", C.c_int * 64), ("line_search_failed", C.c_int), ("mg_levels", C.c_int)]
 
     def as_dict(self):
         n = min(self.newton_its + 1, 64)
@@ -88,7 +89,7 @@ class stokes_solve_report(C.Structure):
                 "constraint_scale": self.constraint_scale,
                 "history": list(self.history[:n]),
                 "krylov_per_newton": list(self.krylov_per_newton[:max(n - 1, 0)]),
-                "line_search_failed": bool(self.line_search_failed)}
+                "line_search_failed": bool(self.line_search_failed), "mg_levels": self.mg_levels}
 
 
 # every symbol declared in include/stokes.h, with its ctypes signature

@@ -161,6 +161,7 @@ int launch_precond_assembly_t(const ColArgs& a, cudaStream_t s) {
     colblock_kernel<T><<<unsigned((n1 + 255) / 256), 256, 0, s>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return int(e);
+    if (!a.mblk) return int(cudaSuccess);       // column blocks only (multigrid levels)
     schur_block_kernel<T><<<unsigned((n2 + 255) / 256), 256, 0, s>>>(a);
     return int(cudaGetLastError());
 }

@@ -24,6 +24,7 @@
 #include <cuda_runtime.h>
 
 #include "handles.h"
+#include "mg.h"
 #include "vec.h"
 
 using namespace stokes;
@@ -44,6 +45,8 @@ struct stokes_solver {
     double* dsc = nullptr;             // device scalars
     size_t band_elems = 0;
     int bw = 0;
+    Multigrid mg;                      // velocity-block multigrid (velocity_mg on an eligible mesh)
+    bool use_mg = false;
 };
 
 namespace {
@@ -55,6 +58,7 @@ void dfree(T*& p) {
 }
 
 void free_solver(stokes_solver* s) {
+    mg_destroy(s->mg);
     dfree(s->r); dfree(s->dl); dfree(s->rl); dfree(s->trial); dfree(s->rt); dfree(s->tmp64);
     dfree(s->V); dfree(s->Z); dfree(s->tin); dfree(s->tz); dfree(s->A); dfree(s->md); dfree(s->mblk); dfree(s->dsc);
     if (s->st_in) stokes_state_destroy(s->st_in);
@@ -125,7 +129,8 @@ ColSolveArgs colsolve_args(stokes_solver* S, double scale) {
 // preconditioner set-up from the inner state: column blocks of F, their
 // factorisation, and the Schur diagonal.  With scale_out, the mean
 // |diagonal| of the velocity block is returned before factorisation.
-int precond_setup(stokes_solver* S, const stokes_params* p, cudaStream_t st, double* scale_out = nullptr) {
+int precond_setup(stokes_solver* S, const stokes_params* p, const double* up, cudaStream_t st,
+                  double* scale_out = nullptr) {
     const stokes_mesh* m = S->mesh;
     TU(PROF_SETUP, cudaMemsetAsync(S->A, 0, S->band_elems * S->isz, st), "clearing column blocks");
     ColArgs a{};
@@ -149,6 +154,7 @@ int precond_setup(stokes_solver* S, const stokes_params* p, cudaStream_t st, dou
         *scale_out = scale;
     }
     TU(PROF_SETUP, launch_col_factor(S->inner, colsolve_args(S, scale), st), "column factorisation");
+    if (S->use_mg) CK(timed(S->mesh, PROF_SETUP, st, [&] { return mg_setup(S->mg, p, up, scale, st); }));
     return STOKES_OK;
 }
 
@@ -159,7 +165,10 @@ int precond_apply(stokes_solver* S, const void* v, void* z, cudaStream_t st) {
     TU(PROF_PRECOND, launch_schur_apply(S->inner, m->h.Nv, m->h.E, m->h.npr, schur_full(m), S->md, v, z, st), "Schur apply");
     CK(state_gradp(S->st_in, z, S->tz, st));
     TU(PROF_PRECOND, vec_axpby(S->nu, 1.0, nullptr, S->inner, v, -1.0, S->inner, S->tz, st), "preconditioner update");
-    TU(PROF_PRECOND, launch_col_solve(S->inner, colsolve_args(S, 1.0), S->tz, z, st), "column solve");
+    if (S->use_mg)
+        CK(timed(S->mesh, PROF_PRECOND, st, [&] { return mg_apply(S->mg, S->tz, z, st); }));
+    else
+        TU(PROF_PRECOND, launch_col_solve(S->inner, colsolve_args(S, 1.0), S->tz, z, st), "column solve");
     return STOKES_OK;
 }
 
@@ -297,7 +306,7 @@ int stokes_solver_create(const stokes_mesh* mesh, const stokes_solver_opts* opts
     stokes_solver* S = new (std::nothrow) stokes_solver();
     if (!S) return fail(STOKES_E_NOMEM, "host allocation failed");
     S->mesh = mesh;
-    stokes_solver_opts o{STOKES_F32, 30, 1000, 50, 1e-10, 0.1};
+    stokes_solver_opts o{STOKES_F32, 30, 1000, 50, 1e-10, 0.1, 0};
     if (opts) o = *opts;
     if (o.restart < 1) o.restart = 30;
     if (o.restart > 31) o.restart = 31;   // multi-dot / multi-axpy handle at most 32 vectors
@@ -340,6 +349,10 @@ int stokes_solver_create(const stokes_mesh* mesh, const stokes_solver_opts* opts
     alloc(&S->md, std::max<size_t>(1, size_t(mesh->h.Np) * size_t(mesh->h.npr)) * S->isz);
     alloc(reinterpret_cast<void**>(&S->mblk), std::max<size_t>(1, size_t(mesh->h.Np) * size_t(mesh->h.npr)) * 8);
     alloc(reinterpret_cast<void**>(&S->dsc), sizeof(double) * size_t(2 * o.restart + 8));
+    if (!rc && o.velocity_mg && mg_eligible(mesh)) {
+        rc = mg_create(S->mg, mesh, S->st_in, S->A, S->bw, S->inner);
+        S->use_mg = rc == STOKES_OK;
+    }
     if (rc) { free_solver(S); delete S; return rc; }
     *out = S;
     return STOKES_OK;
@@ -372,7 +385,7 @@ int stokes_newton_solve(stokes_solver* S, const stokes_params* params, double* u
     // the solution does not depend on s.
     stokes_params P = *params;
     CK(stokes_linearize(S->st_in, &P, up, st));
-    CK(precond_setup(S, &P, st, &P.constraint_scale));
+    CK(precond_setup(S, &P, up, st, &P.constraint_scale));
     R.constraint_scale = P.constraint_scale;
     params = &P;
     CK(stokes_residual(mesh, params, up, S->r, STOKES_F64, st));
@@ -399,7 +412,7 @@ int stokes_newton_solve(stokes_solver* S, const stokes_params* params, double* u
         }
         CK(stokes_linearize(S->st_in, params, up, st));
         if (S->st64 != S->st_in) CK(stokes_linearize(S->st64, params, up, st));
-        CK(precond_setup(S, params, st));
+        CK(precond_setup(S, params, up, st));
         // rhs = -r
         TU(PROF_VECTOR, vec_axpby(n, -1.0, nullptr, STOKES_F64, S->r, 0.0, STOKES_F64, S->trial, st), "rhs");
         int its = 0;
@@ -440,6 +453,7 @@ int stokes_newton_solve(stokes_solver* S, const stokes_params* params, double* u
     CU(cudaStreamSynchronize(st), "sync");
     R.newton_its = k;
     R.res_final = nr;
+    R.mg_levels = S->use_mg ? int(S->mg.L.size()) : 0;
     R.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     if (rep) *rep = R;
     return R.converged ? STOKES_OK : fail(STOKES_E_NOCONV, "Newton did not reach rtol");
@@ -460,7 +474,7 @@ int stokes_linear_solve(stokes_solver* S, const stokes_params* params, const dou
     auto t0 = std::chrono::steady_clock::now();
     CK(stokes_linearize(S->st_in, params, up_lin, st));
     if (S->st64 != S->st_in) CK(stokes_linearize(S->st64, params, up_lin, st));
-    CK(precond_setup(S, params, st));
+    CK(precond_setup(S, params, up_lin, st));
     double nb = 0;
     CK(norm64(S, b, n, nb, st));
     if (!std::isfinite(nb)) return fail(STOKES_E_NONFINITE, "the right-hand side is not finite");
@@ -471,6 +485,7 @@ int stokes_linear_solve(stokes_solver* S, const stokes_params* params, const dou
     CK(norm64(S, S->rl, n, nrl, st));
     R.krylov_its = its;
     R.res0 = nb;
+    R.mg_levels = S->use_mg ? int(S->mg.L.size()) : 0;
     R.res_final = nrl;
     R.converged = nrl <= rtol * nb;
     if (!std::isfinite(nrl)) {

@@ -200,3 +200,76 @@ def test_tracing_records_every_solver_class():
     # tracing is off again: nothing more is recorded
     capi.stokes_profile_begin(m.handle)
     assert all(v[0] == 0 for v in capi.stokes_profile_end(m.handle).values())
+
+
+# ----------------------------------------------------- velocity multigrid
+def _mg_opts(inner, rtol=1e-11):
+    op = _opts(inner, rtol)
+    op.velocity_mg = 1
+    return op
+
+
+@pytest.mark.parametrize("name", ["slab_8x8x2_q2p1", "box_4x4x2_q2p1"])
+@pytest.mark.parametrize("inner", [capi.STOKES_F64, capi.STOKES_F32])
+def test_multigrid_newton_reaches_oracle_solution(name, inner):
+    """Velocity block by the column-preserving geometric multigrid: the same
+    discrete solution (end point against the oracle's residual)."""
+    wl, o, m, lb = _setup(name)
+    p = params(wl.phys, torch.as_tensor(lb, dtype=torch.float64, device="cuda"))
+    s = capi.stokes_solver_create(m.handle, _mg_opts(inner))
+    try:
+        up = torch.zeros(o.ndof, dtype=torch.float64, device="cuda")
+        rc, rep = capi.stokes_newton_solve(s, p, up, check=False)
+        assert rc == 0 and rep["converged"] and rep["mg_levels"] >= 2, (rc, capi.lib().stokes_last_error(), rep)
+        r0 = np.linalg.norm(ostokes.residual(o, wl.phys, np.zeros(o.ndof), lb))
+        r = np.linalg.norm(ostokes.residual(o, wl.phys, up.cpu().numpy(), lb))
+        assert r <= 1e-10 * r0, (r / r0, rep)
+    finally:
+        capi.stokes_solver_destroy(s)
+
+
+@pytest.mark.parametrize("transpose", [False, True])
+@pytest.mark.parametrize("inner", [capi.STOKES_F64, capi.STOKES_F32])
+def test_multigrid_linear_solve(transpose, inner):
+    wl, o, m, lb, up = _lin_point("slab_8x8x2_q2p1")
+    phys = dataclasses.replace(wl.phys, constraint_scale=1e10)
+    p = params(phys, torch.as_tensor(lb, dtype=torch.float64, device="cuda"))
+    b = synth.uniform_vector(22, o.ndof, stream=1)
+    s = capi.stokes_solver_create(m.handle, _mg_opts(inner))
+    try:
+        x = torch.zeros(o.ndof, dtype=torch.float64, device="cuda")
+        rc, rep = capi.stokes_linear_solve(s, p, torch.as_tensor(up, device="cuda"),
+                                           torch.as_tensor(b, device="cuda"), x, transpose, 1e-9)
+        assert rc == 0 and rep["mg_levels"] == 3, rep
+        res = b - ostokes.jacobian_apply(o, phys, up, x.cpu().numpy(), lb)
+        assert np.linalg.norm(res) <= 2e-9 * np.linalg.norm(b), (np.linalg.norm(res) / np.linalg.norm(b), rep)
+    finally:
+        capi.stokes_solver_destroy(s)
+
+
+def test_multigrid_cuts_krylov_iterations():
+    """On the 32 x 32 x 4 slab (5 levels) the multigrid velocity block needs
+    far fewer FGMRES iterations than the column blocks alone for the same
+    Newton solve, and both reach the same solution."""
+    wl = synth.workload("slab_32x32x4_q2p1")
+    m = Mesh(wl, device=0)
+    xyz = m.node_coords()
+    bn = m.basal_nodes()
+    lb = torch.as_tensor(wl.phys.logbeta(xyz[bn, 0], xyz[bn, 1]), dtype=torch.float64, device="cuda")
+    p = params(wl.phys, lb)
+    out = {}
+    for mg in (0, 1):
+        op = _opts(capi.STOKES_F32, rtol=1e-10)
+        op.velocity_mg = mg
+        s = capi.stokes_solver_create(m.handle, op)
+        try:
+            up = torch.zeros(m.ndof, dtype=torch.float64, device="cuda")
+            rc, rep = capi.stokes_newton_solve(s, p, up, check=False)
+            assert rc == 0 and rep["converged"], (mg, rep)
+            out[mg] = (rep, up)
+        finally:
+            capi.stokes_solver_destroy(s)
+    assert out[1][0]["mg_levels"] == 5 and out[0][0]["mg_levels"] == 0
+    assert out[1][0]["krylov_its"] < 0.5 * out[0][0]["krylov_its"], (out[0][0], out[1][0])
+    du = float((out[1][1] - out[0][1]).norm() / out[0][1].norm())
+    assert du < 1e-8, du
