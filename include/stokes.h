@@ -301,8 +301,8 @@ typedef struct {
                             multigrid V-cycle (horizontal semi-coarsening that keeps the
                             node columns, as the paper's column-preserving aggregation
                             of Section 5; column-block smoother) on conforming Q2 meshes
-                            with nx, ny even and >= 4; other meshes, and 0 (default),
-                            use the column blocks alone                            */
+                            with nx, ny even and >= 4 (the default when opts is NULL);
+                            other meshes, and 0, use the column blocks alone       */
 } stokes_solver_opts;
 
 typedef struct {

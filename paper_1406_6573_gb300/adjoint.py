@@ -65,7 +65,7 @@ class StokesProblem:
     """Mesh + physics + solver bundle used by StokesForward."""
 
     def __init__(self, mesh, phys, inner_prec=capi.STOKES_F32, rtol=1e-12, adjoint_rtol=1e-10,
-                 restart=30, max_krylov=4000, max_newton=60):
+                 restart=30, max_krylov=4000, max_newton=60, velocity_mg=1, eta_max=1e-4):
         import dataclasses
         self.mesh = mesh
         self.phys = phys
@@ -76,7 +76,8 @@ class StokesProblem:
         op.max_krylov = max_krylov
         op.max_newton = max_newton
         op.rtol = rtol
-        op.eta_max = 0.1
+        op.eta_max = eta_max
+        op.velocity_mg = velocity_mg     # multigrid velocity block where the mesh allows it
         self.solver = capi.stokes_solver_create(mesh.handle, op)
         self.adjoint_rtol = adjoint_rtol
         self.last_forward = None

@@ -306,7 +306,7 @@ int stokes_solver_create(const stokes_mesh* mesh, const stokes_solver_opts* opts
     stokes_solver* S = new (std::nothrow) stokes_solver();
     if (!S) return fail(STOKES_E_NOMEM, "host allocation failed");
     S->mesh = mesh;
-    stokes_solver_opts o{STOKES_F32, 30, 1000, 50, 1e-10, 0.1, 0};
+    stokes_solver_opts o{STOKES_F32, 30, 1000, 50, 1e-10, 0.1, 1};
     if (opts) o = *opts;
     if (o.restart < 1) o.restart = 30;
     if (o.restart > 31) o.restart = 31;   // multi-dot / multi-axpy handle at most 32 vectors

@@ -7,9 +7,13 @@ import torch
 from . import capi
 
 
-def _field(f, keep):
-    """stokes_field from an object with mean/amp/kx/ky/phase (numpy arrays)."""
+def _field(f, keep, x0=0.0, y0=0.0):
+    """stokes_field from an object with mean/amp/kx/ky/phase (numpy arrays);
+    (x0, y0): physical position of the mesh origin, folded into the phases
+    (f(x0 + x, y0 + y) is the same cosine series with phases + kx x0 + ky y0)."""
     arrs = [np.ascontiguousarray(getattr(f, n), dtype=np.float64) for n in ("amp", "kx", "ky", "phase")]
+    if x0 or y0:
+        arrs[3] = arrs[3] + arrs[1] * x0 + arrs[2] * y0
     keep.extend(arrs)
     P = C.POINTER(C.c_double)
     ptrs = [a.ctypes.data_as(P) if a.size else None for a in arrs]
@@ -26,8 +30,9 @@ def mesh_desc(wl, device=0, force_general=False, grid=None):
     d.pressure_space = capi.STOKES_PRESSURE_P if wl.pspace == "P" else capi.STOKES_PRESSURE_Q
     d.periodic_xy = 1 if wl.periodic else 0
     d.Lx, d.Ly = wl.Lx, wl.Ly
-    d.bed = _field(wl.bed, keep)
-    d.surface = _field(wl.surface, keep)
+    x0, y0 = getattr(wl, "x0", 0.0), getattr(wl, "y0", 0.0)
+    d.bed = _field(wl.bed, keep, x0, y0)
+    d.surface = _field(wl.surface, keep, x0, y0)
     mask = wl.refine_mask()
     if mask.any() or force_general:
         mask = np.ascontiguousarray(mask, dtype=np.uint8)

@@ -78,3 +78,31 @@ def test_adjoint_gradient_central_differences():
         ad = float((g * d).sum())
         assert abs(fd - ad) <= 1e-5 * abs(ad), (fd, ad)
     prob.close()
+
+
+@pytest.mark.parametrize("inner", [capi.STOKES_F32])
+def test_adjoint_gradient_on_a_block_of_the_largest_slab(inner):
+    """The 512 x 512 x 8 slab's generators (random log(beta) field, SI units)
+    on a 4 x 4 x 8 column block: the GPU gradient through the multigrid
+    forward and adjoint solves against the oracle's adjoint gradient, with
+    u_obs = 0 (J = 1/2 |u_top|^2)."""
+    wl = synth.sub_block(synth.workload("slab_512x512x8_q2p1"), 100, 37, 4, 4)
+    o = OracleMesh(wl)
+    lb_ref = wl.phys.logbeta(*o.basal_coords()[:, :2].T)
+    top_o = oadjoint.top_nodes(o)
+    u_obs = np.zeros((top_o.size, 3))
+    J_o, g_o, gA_o, _ = oadjoint.gradient(o, wl.phys, lb_ref, u_obs, top_o, rtol=1e-12)
+    m = Mesh(wl, device=0)
+    prob = StokesProblem(m, wl.phys, inner_prec=inner, rtol=1e-11, adjoint_rtol=1e-11)
+    top = top_nodes(m)
+    assert np.array_equal(top.cpu().numpy(), top_o)
+    lb = torch.as_tensor(lb_ref, dtype=torch.float64, device="cuda").requires_grad_(True)
+    A = torch.tensor(wl.phys.A, dtype=torch.float64, device="cuda", requires_grad=True)
+    J = misfit(StokesForward.apply(lb, A, prob), torch.as_tensor(u_obs, device="cuda"), m, top)
+    J.backward()
+    assert prob.last_forward["mg_levels"] == 2 and prob.last_adjoint["mg_levels"] == 2
+    assert abs(J.item() - J_o) <= 1e-8 * J_o
+    g = lb.grad.cpu().numpy()
+    assert np.linalg.norm(g - g_o) <= 1e-7 * np.linalg.norm(g_o), np.linalg.norm(g - g_o) / np.linalg.norm(g_o)
+    assert abs(A.grad.item() - gA_o) <= 1e-7 * abs(gA_o)
+    prob.close()

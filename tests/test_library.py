@@ -192,3 +192,14 @@ def test_gridded_geometry(name):
         d, keep = mesh_desc(wl, device=-1, grid=(rbed, surf))
         d.surface_nodes = None
         capi.stokes_mesh_create(d)
+
+
+def test_offset_sub_block_geometry():
+    """A column block of a slab (origin x0, y0 != 0) builds the geometry of
+    its physical position: the node heights equal the oracle's."""
+    wl = synth.sub_block(synth.workload("slab_512x512x8_q2p1"), 100, 37, 3, 2)
+    m = Mesh(wl, device=-1)
+    o = OracleMesh(wl)
+    a, b = m.node_coords(), o.node_coords()
+    np.testing.assert_allclose(a[:, 0] + wl.x0, b[:, 0], rtol=0, atol=1e-9 * wl.Lx)
+    np.testing.assert_allclose(a[:, 2], b[:, 2], rtol=0, atol=1e-9 * np.abs(b[:, 2]).max())
