@@ -37,10 +37,10 @@ STATE_FIELDS = 11
 
 # Sources that define the stored-state apply kernels: a capture's DRAM
 # traffic is reported only while their hash equals the one recorded with it.
-KERNEL_SOURCES = ["include/stokes.h"] + [
+KERNEL_SOURCES = [
     "paper_1406_6573_gb300/csrc/" + f for f in
-    ("common.h", "kernels.h", "hanging.h", "tma.cuh", "elem_kernels.cuh", "elem_body.cuh", "cpl_apply.cuh",
-     "k2.cu", "k3.cu", "k4.cu", "capi.cu")]
+    ("kernels.h", "hanging.h", "tma.cuh", "elem_kernels.cuh", "elem_body.cuh", "cpl_apply.cuh",
+     "k2.cu", "k3.cu", "k4.cu")]
 
 
 def kernel_source_sha():
