@@ -117,6 +117,9 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-solve", action="store_true",
                     help="skip the time-to-1e-10 Newton solves (FP32-inner vs FP64)")
+    ap.add_argument("--pairing-study", action="store_true",
+                    help="Q2 x P1 against Q2 x Q0 pressure (Section 3.2.2): FP32-inner Newton solves to 1e-10 on "
+                         "16 x 16 x 4 slabs of element aspect ratio phi = 1 .. 100, Krylov iterations and time")
     ap.add_argument("--adjoint-check", type=int, default=0, metavar="N",
                     help="adjoint gradient of a surface misfit and N central-difference directional checks")
     ap.add_argument("--restart", type=int, default=30, help="FGMRES restart length of the solves")
@@ -271,6 +274,57 @@ def adjoint_check(args, wl, mesh, rank):
             "grad_norm": float(g.norm()), "directions": args.adjoint_check, "h": h,
             "fd_rel_diff_max": max(checks), "fd_rel_diff": [float("%.3g" % c) for c in checks],
             "forward_rtol": 1e-11, "adjoint_rtol": 1e-11}
+
+
+def pairing_study(args):
+    """Time to 1e-10 of both pressure pairings on thin slabs of growing element
+    aspect ratio phi = (L / nx) / (H / nz): the P_(k-1) pairing loses inf-sup
+    stability as phi grows, the Q_(k-2) pairing does not (Section 3.2.2)."""
+    import dataclasses
+    import math
+    import torch
+    import stokes_synth as synth
+    from stokes_synth.fields import bed_field, surface_field
+    from paper_1406_6573_gb300 import capi
+    from paper_1406_6573_gb300.mesh import Mesh, params
+    out = []
+    nx, nz, H = 16, 4, 1000.0
+    for phi in (1.0, 4.0, 16.0, 100.0):
+        L = phi * (H / nz) * nx
+        for ps in ("P", "Q"):
+            base = synth.workload("slab_8x8x2_q2p1")
+            wl = dataclasses.replace(base, name=f"phi{phi:g}_{ps}", nx=nx, ny=nx, nz=nz, pspace=ps, Lx=L, Ly=L,
+                                     bed=bed_field(base.seed, L, L, max_dev=0.05 * H),
+                                     surface=surface_field(base.seed, L, L, mean=H, max_dev=0.02 * H))
+            m = Mesh(wl, device=0)
+            xyz = m.node_coords()
+            bn = m.basal_nodes()
+            lb = torch.as_tensor(wl.phys.logbeta(xyz[bn, 0], xyz[bn, 1]), dtype=torch.float64, device="cuda")
+            p = params(wl.phys, lb)
+            row = {"phi": phi, "pressure": "P1" if ps == "P" else "Q0", "dofs": m.ndof}
+            for mg in (1, 0):
+                op = capi.stokes_solver_opts()
+                op.inner_prec = capi.STOKES_F32
+                op.restart = 30
+                op.max_krylov = 6000
+                op.max_newton = 60
+                op.rtol = 1e-10
+                op.eta_max = args.eta_max
+                op.velocity_mg = mg
+                sv = capi.stokes_solver_create(m.handle, op)
+                up = torch.zeros(m.ndof, dtype=torch.float64, device="cuda")
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                rc, rep = capi.stokes_newton_solve(sv, p, up, check=False)
+                torch.cuda.synchronize()
+                dt = time.perf_counter() - t0
+                capi.stokes_solver_destroy(sv)
+                key = "multigrid" if mg else "column_blocks"
+                row[key] = {"converged": bool(rep["converged"]), "seconds": round(dt, 3),
+                            "newton_its": rep["newton_its"], "krylov_its": rep["krylov_its"]}
+            out.append(row)
+            m.close()
+    return out
 
 
 def run_reference(args):
@@ -565,6 +619,7 @@ def run_ours(args):
             solve["speedup_fp32_inner"] = round(solve["fp64"]["seconds"] / solve["fp32_inner"]["seconds"], 3)
 
     adjoint = adjoint_check(args, wl, mesh, rank) if args.adjoint_check > 0 else None
+    pairing = pairing_study(args) if args.pairing_study and rank == 0 else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -602,6 +657,8 @@ def run_ours(args):
             "cpu_baseline": cpu,
             "adjoint_check": adjoint,
         }
+        if pairing is not None:
+            out["pairing_study"] = pairing
         print(json.dumps(out))
     if world > 1:
         dist.destroy_process_group()
