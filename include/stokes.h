@@ -192,7 +192,10 @@ int stokes_residual(const stokes_mesh* mesh, const stokes_params* params,
                     const void* up, void* r, int prec, void* stream);
 
 /* y = J_c(up_lin) x, the Newton Jacobian of Eqs. 2.6-2.7 at up_lin, fused:
- * the linearisation is recomputed at every quadrature point. */
+ * the linearisation is recomputed at every quadrature point.  On meshes of
+ * degree k >= 5 (block-per-element kernels) the call linearises into a
+ * per-mesh FP64 workspace and applies from it: two such calls on one mesh
+ * must not overlap on the GPU (they race on the workspace). */
 int stokes_jacobian_apply(const stokes_mesh* mesh, const stokes_params* params,
                           const void* up_lin, const void* x, void* y,
                           int prec, void* stream);

@@ -14,7 +14,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "lib")
 LIB = os.path.join(OUT, "libstokes_gb300.so")
 
-SOURCES = ["k2.cu", "k3.cu", "k4.cu", "misc.cu", "vec.cu", "precond.cu", "solver.cu", "mg.cu", "noalloc.cu", "capi.cu", "mesh.cpp", "basis.cpp"]
+SOURCES = ["k2.cu", "k3.cu", "k4.cu", "misc.cu", "vec.cu", "precond.cu", "khigh.cu", "solver.cu", "mg.cu", "noalloc.cu", "capi.cu", "mesh.cpp", "basis.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-fopenmp", "--expt-relaxed-constexpr"]
 

@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 
 #include "handles.h"
+#include "khigh.h"
 
 using namespace stokes;
 
@@ -33,7 +34,10 @@ int ensure_tables(int dev, int k) {
         case 2: e = upload_tables_k2(t); break;
         case 3: e = upload_tables_k3(t); break;
         case 4: e = upload_tables_k4(t); break;
-        default: return fail(STOKES_E_INVAL, "the GPU kernels are built for degrees k = 2, 3, 4");
+        default:
+            if (k < 5 || k > KMAX) return fail(STOKES_E_INVAL, "the GPU kernels are built for degrees k = 2 .. 9");
+            g_tables_done[dev][k] = true;     // k >= 5: tables in device memory (high_tables)
+            return STOKES_OK;
     }
     if (e != 0) return cuda_fail(cudaError_t(e), "uploading basis tables");
     g_tables_done[dev][k] = true;
@@ -57,7 +61,7 @@ void free_mesh_device(stokes_mesh* m) {
     m->prof.pool.clear();
     void* ptrs[] = {m->d_nodes, m->d_hang, m->d_geo, m->d_pidx, m->d_pel, m->d_pel_f, m->d_face_elem, m->d_fidx,
                     m->d_fgeo, m->d_fmap, m->d_basal_nodes, m->d_basal_P, m->d_err, m->d_col_of,
-                    m->d_pos_of, m->d_col_nodes, m->d_col_len, m->d_col_basal};
+                    m->d_pos_of, m->d_col_nodes, m->d_col_len, m->d_col_basal, m->d_hwork};
     for (void* p : ptrs) if (p) cudaFree(p);
 }
 
@@ -95,6 +99,7 @@ int launch_elem(int k, int mode, int prec, int state_prec, bool trans, const Ele
         case 3: return launch_elem_k3(mode, prec, state_prec, trans, a, s);
         case 4: return launch_elem_k4(mode, prec, state_prec, trans, a, s);
     }
+    if (k >= 5 && k <= KMAX) return launch_elem_high(mode, prec, state_prec, a, s);
     return int(cudaErrorInvalidValue);
 }
 
@@ -104,6 +109,7 @@ int64_t state_stride(int k) {
         case 3: return state_stride_k3();
         case 4: return state_stride_k4();
     }
+    if (k >= 5 && k <= KMAX) return high_state_stride(k);
     return 0;
 }
 
@@ -113,6 +119,7 @@ int64_t grad_a_partials(int k, int64_t E) {
         case 3: return grad_a_partials_k3(E);
         case 4: return grad_a_partials_k4(E);
     }
+    if (k >= 5 && k <= KMAX) return high_grad_a_partials(E);
     return 0;
 }
 
@@ -122,6 +129,7 @@ int launch_face(int k, int mode, int prec, const FaceArgs& a, cudaStream_t s) {
         case 3: return launch_face_k3(mode, prec, a, s);
         case 4: return launch_face_k4(mode, prec, a, s);
     }
+    if (k >= 5 && k <= KMAX) return launch_face_high(mode, prec, a, s);
     return int(cudaErrorInvalidValue);
 }
 
@@ -131,6 +139,7 @@ int launch_precond_assembly(int k, int prec, const ColArgs& a, cudaStream_t s) {
         case 3: return launch_precond_assembly_k3(prec, a, s);
         case 4: return launch_precond_assembly_k4(prec, a, s);
     }
+    if (k >= 5 && k <= KMAX) return launch_precond_assembly_high(prec, a, s);
     return int(cudaErrorInvalidValue);
 }
 
@@ -162,6 +171,9 @@ ElemArgs elem_args(const stokes_mesh* m, const stokes_params* p) {
     a.pel_f = m->d_pel_f;
     a.err = m->d_err;
     a.wait_polls = m->wait_polls;
+    a.htab = m->htab;
+    a.htab_k = m->h.k;
+    a.state_stride = state_stride(m->h.k);
     if (m->h.lattice) {
         a.lat_nx = m->h.nx; a.lat_ny = m->h.ny; a.lat_NX = m->h.latNX; a.lat_NY = m->h.latNY;
     }
@@ -182,6 +194,7 @@ FaceArgs face_args(const stokes_mesh* m, const stokes_params* p) {
     f.face_elem = m->d_face_elem; f.nodes = m->d_nodes; f.hang = m->d_hang;
     f.pidx = m->d_pidx; f.pel = m->d_pel; f.fgeo = m->d_fgeo; f.fmap = m->d_fmap;
     f.logbeta = p ? p->logbeta : nullptr;
+    f.htab = m->htab;
     if (sliding_nonlinear(p)) {
         f.slide = 1;
         f.slide_m = p->sliding_m;
@@ -204,7 +217,21 @@ int operator_sequence(const stokes_mesh* m, const stokes_params* p, int mode, in
     a.x = x; a.y = y; a.u = u; a.cstate = cstate;
     a.state_cpl = state_cpl;
     const bool robin = p->robin && m->h.nF > 0;
-    if (mode == MODE_STATE_APPLY) {
+    const bool high = m->h.k >= 5;
+    if (high && mode == MODE_APPLY) {
+        // k >= 5: fused Jacobian = linearisation at u into the mesh's FP64
+        // workspace, then the stored-state element apply; the basal face term
+        // below recomputes its sliding linearisation from u
+        ElemArgs al = a;
+        al.u = u;
+        al.state = m->d_hwork;
+        al.state_cpl = 0;
+        e = timed(m, 1, s, [&] { return launch_elem(m->h.k, MODE_LINEARIZE, prec, STOKES_F64, false, al, s); });
+        if (e) return cuda_fail(cudaError_t(e), "linearisation kernel launch");
+        a.cstate = m->d_hwork;
+        e = timed(m, 1, s, [&] { return launch_elem(m->h.k, MODE_STATE_APPLY, prec, STOKES_F64, trans, a, s); });
+        if (e) return cuda_fail(cudaError_t(e), "element kernel launch");
+    } else if (mode == MODE_STATE_APPLY && !high) {
         // the stored-state kernel also does the basal Robin term and the
         // constraint rows (one launch per apply)
         a.face = face_args(m, p);
@@ -223,14 +250,17 @@ int operator_sequence(const stokes_mesh* m, const stokes_params* p, int mode, in
         a.Nb = m->h.Nb; a.basal_nodes = m->d_basal_nodes; a.basal_P = m->d_basal_P;
         a.cscale = p->constraint_scale;
     }
-    e = timed(m, 1, s, [&] { return launch_elem(m->h.k, mode, prec, state_prec, trans, a, s); });
-    if (e) return cuda_fail(cudaError_t(e), "element kernel launch");
+    if (!(high && mode == MODE_APPLY)) {
+        e = timed(m, 1, s, [&] { return launch_elem(m->h.k, mode, prec, state_prec, trans, a, s); });
+        if (e) return cuda_fail(cudaError_t(e), "element kernel launch");
+    }
     if (mode == MODE_STATE_GRADP) return STOKES_OK;   // zero velocity input: no Robin or (I - P) term
-    if (mode == MODE_STATE_APPLY) return STOKES_OK;
+    if (mode == MODE_STATE_APPLY && !high) return STOKES_OK;
     if (robin) {
         FaceArgs f = face_args(m, p);
         f.x = x; f.y = y;
         f.ulin = u;               // fused Jacobian: the linearisation point; residual: NULL (u = x)
+        if (mode == MODE_STATE_APPLY) f.fstate = fstate;   // k >= 5 stored state: its sliding state
         e = timed(m, 2, s, [&] { return launch_face(m->h.k, FACE_APPLY, prec, f, s); });
         if (e) return cuda_fail(cudaError_t(e), "basal face kernel launch");
     }
@@ -267,9 +297,9 @@ int stokes_mesh_create(const stokes_mesh_desc* desc, stokes_mesh** out) {
     if (rc != STOKES_OK) { delete m; return fail(rc, err); }
     m->device = desc->device;
     if (desc->device >= 0) {
-        if (m->h.k < 2 || m->h.k > 4) {
+        if (m->h.k < 2 || m->h.k > KMAX) {
             delete m;
-            return fail(STOKES_E_INVAL, "the GPU kernels are built for degrees k = 2, 3, 4");
+            return fail(STOKES_E_INVAL, "the GPU kernels are built for degrees k = 2 .. 9");
         }
         DeviceGuard g(desc->device);
         if (g.err != cudaSuccess) { delete m; return cuda_fail(g.err, "selecting the device"); }
@@ -298,6 +328,17 @@ int stokes_mesh_create(const stokes_mesh_desc* desc, stokes_mesh** out) {
                 if (m->h.pos_of[g] == 0) cb[m->h.col_of[g]] = int32_t(b);
             }
             rc = upload(&m->d_col_basal, cb);
+        }
+        if (rc == STOKES_OK && m->h.k >= 5) {
+            // degree tables of the block-per-element kernels, and the FP64
+            // linearisation workspace of their fused Jacobian apply
+            rc = high_tables(desc->device, m->h.k, &m->htab);
+            if (rc == STOKES_OK &&
+                dev_alloc(reinterpret_cast<void**>(&m->d_hwork), size_t(m->h.E) * size_t(high_state_stride(m->h.k)) * 8) !=
+                    cudaSuccess) {
+                m->d_hwork = nullptr;
+                rc = fail(STOKES_E_NOMEM, "cudaMalloc of the linearisation workspace failed");
+            }
         }
         if (rc != STOKES_OK) { free_mesh_device(m); delete m; return rc; }
         m->on_device = true;

@@ -88,6 +88,10 @@ struct stokes_mesh {
     int32_t* d_col_nodes = nullptr;
     int32_t* d_col_len = nullptr;
     int32_t* d_col_basal = nullptr;
+    // k >= 5: degree tables (device, shared per device and degree) and the
+    // FP64 linearisation workspace [E][state stride] of the fused apply
+    const void* htab = nullptr;
+    double* d_hwork = nullptr;
 };
 
 namespace stokes {

@@ -61,6 +61,7 @@ struct FaceArgs {
     const void* fstate;        // apply: stored sliding state [nF][7][q^2] (type of x), used when set
     void* fstate_out;          // linearisation output (fstate_f32: float, else double)
     int fstate_f32;
+    const void* htab;          // degree tables of the k >= 5 kernels (device)
 };
 // stored basal state per basal Gauss point: beta w s, then
 // v = 2 beta w s' T u (3) and T u (3): the Jacobian's face term on w is
@@ -109,6 +110,10 @@ struct ElemArgs {
     // of the face tail; fidx: basal face of each element (-1 if none)
     int face_in_elements;
     const int32_t* fidx;
+    // k >= 5 kernels: degree tables (device), the degree, the state stride
+    const void* htab;
+    int htab_k;
+    int64_t state_stride;
     FaceArgs face;
     int64_t Nb;
     const int32_t* basal_nodes;

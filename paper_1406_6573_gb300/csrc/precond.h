@@ -43,6 +43,9 @@ struct ColArgs {
     int state_cpl;             // the state is in the group layout of k = 2 FP32 states
     void* A;                   // [3 colmax][2 bw + 1][ncol] banded column matrices
     double* mblk;              // [E][npr][npr] M(1/mu) element blocks (FP64, assembly output)
+    const void* htab;          // k >= 5: degree tables (device), degree, state stride
+    int htab_k;
+    int64_t state_stride;
 };
 
 int launch_precond_assembly_k2(int prec, const ColArgs& a, cudaStream_t s);

@@ -141,6 +141,7 @@ int precond_setup(stokes_solver* S, const stokes_params* p, const double* up, cu
     a.nodes = m->d_nodes; a.hang = m->d_hang; a.col_of = m->d_col_of; a.pos_of = m->d_pos_of;
     a.fidx = m->d_fidx; a.fmap = m->d_fmap; a.fgeo = m->d_fgeo; a.logbeta = p->logbeta;
     a.state = S->st_in->d_state; a.state_cpl = S->st_in->cpl; a.A = S->A; a.mblk = S->mblk; a.schur_full = schur_full(m);
+    a.htab = m->htab; a.htab_k = m->h.k; a.state_stride = state_stride(m->h.k);
     TU(PROF_SETUP, launch_precond_assembly(m->h.k, S->inner, a, st), "preconditioner assembly");
     TU(PROF_SETUP, launch_schur_invert(S->inner, m->h.E, m->h.npr, schur_full(m), S->mblk, S->md, st), "Schur inversion");
     double scale = p->constraint_scale;
