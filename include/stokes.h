@@ -303,8 +303,9 @@ typedef struct {
     int velocity_mg;     /* 1: the velocity block of the preconditioner is a geometric
                             multigrid V-cycle (horizontal semi-coarsening that keeps the
                             node columns, as the paper's column-preserving aggregation
-                            of Section 5; column-block smoother) on conforming Q2 meshes
-                            with nx, ny even and >= 4 (the default when opts is NULL);
+                            of Section 5; column-block smoother) on conforming meshes of
+                            degree 2, 3, 4 with nx, ny even and >= 4 (the default
+                            when opts is NULL);
                             other meshes, and 0, use the column blocks alone       */
 } stokes_solver_opts;
 

@@ -16,122 +16,117 @@ constexpr int TPB = 256;
 
 inline unsigned blocks_for(int64_t n) { return unsigned((n + TPB - 1) / TPB); }
 
-// coarse FP64 velocity at node (Xc, Yc, Z) <- fine velocity at (2 Xc, 2 Yc, Z)
-__global__ void inject_u_kernel(int64_t NXc, int64_t NYc, int64_t NZ, int64_t NX, int64_t NY, const double* __restrict__ uf,
-                                double* __restrict__ uc) {
+// Transfers between a level (fine lattice NX x NY x NZ) and the next
+// (coarse NXc x NYc x NZ) are tensor products of 1-D tables in x and y,
+// identity in z; each table row lists (lattice index, weight) pairs:
+//   P  [fine X]:   coarse nodal values -> fine node (coarse degree-k
+//                  Lagrange interpolation; KP = k + 1 entries)
+//   R  [coarse X]: the transpose of P (at most RM entries)
+//   J  [coarse X]: fine nodal values -> coarse node (fine degree-k
+//                  interpolation at the coarse node's position; KP entries)
+constexpr int KP = 5;     // k + 1 for k <= 4
+constexpr int RM = 17;    // 4 k + 1
+
+struct Tab1 {
+    const int32_t* idx;   // [n][m]
+    const double* w;      // [n][m]
+    const int32_t* cnt;   // [n]
+    int m;
+};
+
+// out (3 components at every node of the target lattice) = tensor transfer of
+// in: out[X, Y, Z] = sum_a sum_b tx[X][a] ty[Y][b] in[ix, iy, Z]
+template <typename TI, typename TO>
+__global__ void transfer_kernel(int64_t NXo, int64_t NYo, int64_t NZ, int64_t NXi, int64_t NYi, Tab1 tx, Tab1 ty,
+                                int ncomp, const TI* __restrict__ in, TO* __restrict__ out) {
     const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (t >= NXc * NYc * NZ) return;
-    const int64_t Xc = t % NXc, r = t / NXc, Yc = r % NYc, Z = r / NYc;
-    const int64_t gf = 2 * Xc + NX * (2 * Yc + NY * Z);
-    uc[3 * t] = uf[3 * gf];
-    uc[3 * t + 1] = uf[3 * gf + 1];
-    uc[3 * t + 2] = uf[3 * gf + 2];
-}
-
-// coarse log(beta) at basal node (Xc, Yc) <- fine at (2 Xc, 2 Yc)
-__global__ void inject_lb_kernel(int64_t NXc, int64_t NYc, int64_t NX, const double* __restrict__ lf, double* __restrict__ lc) {
-    const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (t >= NXc * NYc) return;
-    const int64_t Xc = t % NXc, Yc = t / NXc;
-    lc[t] = lf[2 * Xc + NX * 2 * Yc];
-}
-
-// 1-D Q2 interpolation weights: fine lattice index X from the coarse nodes
-// (coarse element cx = X div 4 spans fine X = 4 cx .. 4 cx + 4 and coarse
-// nodes 2 cx, 2 cx + 1, 2 cx + 2; local coordinate (X mod 4) / 2 - 1)
-__device__ __forceinline__ int interp_1d(int64_t X, int64_t NXc, bool periodic, int64_t (&ic)[3], float (&w)[3]) {
-    if ((X & 1) == 0) {
-        ic[0] = X / 2;
-        w[0] = 1.f;
-        return 1;
-    }
-    const int64_t cx = X / 4;
-    const bool r1 = (X % 4) == 1;    // xi = -1/2 (r1) or +1/2
-    w[0] = r1 ? 0.375f : -0.125f;
-    w[1] = 0.75f;
-    w[2] = r1 ? -0.125f : 0.375f;
-    for (int m = 0; m < 3; ++m) {
-        int64_t c = 2 * cx + m;
-        if (periodic && c >= NXc) c -= NXc;
-        ic[m] = c;
-    }
-    return 3;
-}
-
-// out_f = P x_c (velocity part): Q2 interpolation in x and y, identity in z
-template <typename T>
-__global__ void prolong_kernel(int64_t NX, int64_t NY, int64_t NZ, int64_t NXc, int64_t NYc, int periodic,
-                               const T* __restrict__ xc, T* __restrict__ out) {
-    const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (t >= NX * NY * NZ) return;
-    const int64_t X = t % NX, r = t / NX, Y = r % NY, Z = r / NY;
-    int64_t ix[3], iy[3];
-    float wx[3], wy[3];
-    const int nxp = interp_1d(X, NXc, periodic != 0, ix, wx);
-    const int nyp = interp_1d(Y, NYc, periodic != 0, iy, wy);
-    T s0 = 0, s1 = 0, s2 = 0;
-    for (int b = 0; b < nyp; ++b)
-        for (int a = 0; a < nxp; ++a) {
-            const int64_t gc = ix[a] + NXc * (iy[b] + NYc * Z);
-            const T w = T(wx[a] * wy[b]);
-            s0 += w * xc[3 * gc];
-            s1 += w * xc[3 * gc + 1];
-            s2 += w * xc[3 * gc + 2];
-        }
-    out[3 * t] = s0;
-    out[3 * t + 1] = s1;
-    out[3 * t + 2] = s2;
-}
-
-// fine lattice offsets d and weights of the coarse node Xc in P^T (the
-// transpose of interp_1d): vertex nodes (Xc even) reach X = 2 Xc + {0, +-1,
-// +-3}, midpoint nodes (Xc odd) X = 2 Xc + {0, +-1}
-__device__ __forceinline__ int restrict_1d(int64_t Xc, int64_t NX, bool periodic, int64_t (&ix)[5], float (&w)[5]) {
-    const int64_t X0 = 2 * Xc;
-    int n = 0;
-    auto add = [&](int d, float wt) {
-        int64_t X = X0 + d;
-        if (periodic) {
-            if (X < 0) X += NX;
-            if (X >= NX) X -= NX;
-        } else if (X < 0 || X >= NX) {
-            return;
-        }
-        ix[n] = X;
-        w[n] = wt;
-        ++n;
-    };
-    if ((Xc & 1) == 0) {
-        add(-3, -0.125f); add(-1, 0.375f); add(0, 1.f); add(1, 0.375f); add(3, -0.125f);
-    } else {
-        add(-1, 0.75f); add(0, 1.f); add(1, 0.75f);
-    }
-    return n;
-}
-
-// b_c = P^T r_f (velocity part)
-template <typename T>
-__global__ void restrict_kernel(int64_t NX, int64_t NY, int64_t NZ, int64_t NXc, int64_t NYc, int periodic,
-                                const T* __restrict__ rf, T* __restrict__ bc) {
-    const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (t >= NXc * NYc * NZ) return;
-    const int64_t Xc = t % NXc, r = t / NXc, Yc = r % NYc, Z = r / NYc;
-    int64_t ix[5], iy[5];
-    float wx[5], wy[5];
-    const int nx = restrict_1d(Xc, NX, periodic != 0, ix, wx);
-    const int ny = restrict_1d(Yc, NY, periodic != 0, iy, wy);
-    T s0 = 0, s1 = 0, s2 = 0;
-    for (int b = 0; b < ny; ++b)
+    if (t >= NXo * NYo * NZ) return;
+    const int64_t X = t % NXo, r = t / NXo, Y = r % NYo, Z = r / NYo;
+    const int nx = tx.cnt[X], ny = ty.cnt[Y];
+    double s[3] = {0.0, 0.0, 0.0};
+    for (int b = 0; b < ny; ++b) {
+        const int64_t iy = ty.idx[Y * ty.m + b];
+        const double wy = ty.w[Y * ty.m + b];
         for (int a = 0; a < nx; ++a) {
-            const int64_t gf = ix[a] + NX * (iy[b] + NY * Z);
-            const T w = T(wx[a] * wy[b]);
-            s0 += w * rf[3 * gf];
-            s1 += w * rf[3 * gf + 1];
-            s2 += w * rf[3 * gf + 2];
+            const int64_t gi = tx.idx[X * tx.m + a] + NXi * (iy + NYi * Z);
+            const double wgt = tx.w[X * tx.m + a] * wy;
+            for (int c = 0; c < ncomp; ++c) s[c] += wgt * double(in[ncomp * gi + c]);
         }
-    bc[3 * t] = s0;
-    bc[3 * t + 1] = s1;
-    bc[3 * t + 2] = s2;
+    }
+    for (int c = 0; c < ncomp; ++c) out[ncomp * t + c] = TO(s[c]);
+}
+
+// Lagrange polynomials of the nodes x[0..n) at t
+void lagrange_at(int n, const double* x, double t, double* out) {
+    for (int i = 0; i < n; ++i) {
+        double v = 1.0;
+        for (int j = 0; j < n; ++j)
+            if (j != i) v *= (t - x[j]) / (x[i] - x[j]);
+        out[i] = v;
+    }
+}
+
+// host tables of one direction: fine lattice of nf elements, coarse of nf / 2
+struct HostTab1 {
+    std::vector<int32_t> idx, cnt;
+    std::vector<double> w;
+    int m = 0;
+};
+
+void build_dir(int nf, int k, bool periodic, const double* gll, HostTab1& P, HostTab1& R, HostTab1& J) {
+    const int nc = nf / 2;
+    const int NXf = periodic ? nf * k : nf * k + 1, NXc = periodic ? nc * k : nc * k + 1;
+    auto wrapf = [&](int64_t X) { return periodic ? int32_t(X % NXf) : int32_t(X); };
+    auto wrapc = [&](int64_t X) { return periodic ? int32_t(X % NXc) : int32_t(X); };
+    double L[N1MAX];
+    // P: fine X = ex k + i lies in coarse element ex / 2 at local coordinate
+    // (ex - 2 cx) + t_i - 1 (t_i = (gll_i + 1) / 2)
+    P.m = KP; P.idx.assign(size_t(NXf) * KP, 0); P.w.assign(size_t(NXf) * KP, 0.0); P.cnt.assign(NXf, 0);
+    for (int X = 0; X < NXf; ++X) {
+        int ex = X / k, i = X % k;
+        if (ex == nf) { ex = nf - 1; i = k; }          // last node of a non-periodic lattice
+        const int cx = ex / 2;
+        lagrange_at(k + 1, gll, double(ex - 2 * cx) + 0.5 * (gll[i] + 1.0) - 1.0, L);
+        int n = 0;
+        for (int m = 0; m <= k; ++m) {
+            if (std::fabs(L[m]) < 1e-14) continue;
+            P.idx[size_t(X) * KP + n] = wrapc(int64_t(cx) * k + m);
+            P.w[size_t(X) * KP + n] = L[m];
+            ++n;
+        }
+        P.cnt[X] = n;
+    }
+    // R = P^T
+    std::vector<std::vector<std::pair<int32_t, double>>> rows(NXc);
+    for (int X = 0; X < NXf; ++X)
+        for (int a = 0; a < P.cnt[X]; ++a) rows[P.idx[size_t(X) * KP + a]].push_back({X, P.w[size_t(X) * KP + a]});
+    R.m = RM; R.idx.assign(size_t(NXc) * RM, 0); R.w.assign(size_t(NXc) * RM, 0.0); R.cnt.assign(NXc, 0);
+    for (int Xc = 0; Xc < NXc; ++Xc) {
+        const int n = int(std::min<size_t>(rows[Xc].size(), RM));
+        for (int a = 0; a < n; ++a) {
+            R.idx[size_t(Xc) * RM + a] = rows[Xc][a].first;
+            R.w[size_t(Xc) * RM + a] = rows[Xc][a].second;
+        }
+        R.cnt[Xc] = n;
+    }
+    // J: coarse Xc = cx k + i at fine-element coordinate 2 cx + 2 t_i
+    J.m = KP; J.idx.assign(size_t(NXc) * KP, 0); J.w.assign(size_t(NXc) * KP, 0.0); J.cnt.assign(NXc, 0);
+    for (int Xc = 0; Xc < NXc; ++Xc) {
+        int cx = Xc / k, i = Xc % k;
+        if (cx == nc) { cx = nc - 1; i = k; }
+        const double pos = 2.0 * cx + (gll[i] + 1.0);  // in fine elements
+        int ex = int(std::floor(pos + 1e-12));
+        if (ex > 2 * cx + 1) ex = 2 * cx + 1;
+        lagrange_at(k + 1, gll, 2.0 * (pos - ex) - 1.0, L);
+        int n = 0;
+        for (int m = 0; m <= k; ++m) {
+            if (std::fabs(L[m]) < 1e-14) continue;
+            J.idx[size_t(Xc) * KP + n] = wrapf(int64_t(ex) * k + m);
+            J.w[size_t(Xc) * KP + n] = L[m];
+            ++n;
+        }
+        J.cnt[Xc] = n;
+    }
 }
 
 // v_g <- P_b v_g at the basal nodes (the slip projector; zero for no-slip)
@@ -191,25 +186,28 @@ int project(const MgLevel& Lv, int prec, void* v, cudaStream_t s) {
     return STOKES_OK;
 }
 
-int transfer(const MgLevel& F, const MgLevel& Cl, int prec, bool periodic, bool up, const void* in, void* out,
-             cudaStream_t s) {
-    if (up) {
-        const int64_t n = F.NX * F.NY * F.NZ;
-        if (prec == STOKES_F32)
-            prolong_kernel<float><<<blocks_for(n), TPB, 0, s>>>(F.NX, F.NY, F.NZ, Cl.NX, Cl.NY, periodic,
-                                                                static_cast<const float*>(in), static_cast<float*>(out));
-        else
-            prolong_kernel<double><<<blocks_for(n), TPB, 0, s>>>(F.NX, F.NY, F.NZ, Cl.NX, Cl.NY, periodic,
-                                                                 static_cast<const double*>(in), static_cast<double*>(out));
-    } else {
-        const int64_t n = Cl.NX * Cl.NY * Cl.NZ;
-        if (prec == STOKES_F32)
-            restrict_kernel<float><<<blocks_for(n), TPB, 0, s>>>(F.NX, F.NY, F.NZ, Cl.NX, Cl.NY, periodic,
-                                                                 static_cast<const float*>(in), static_cast<float*>(out));
-        else
-            restrict_kernel<double><<<blocks_for(n), TPB, 0, s>>>(F.NX, F.NY, F.NZ, Cl.NX, Cl.NY, periodic,
-                                                                  static_cast<const double*>(in), static_cast<double*>(out));
-    }
+Tab1 dev_tab(const MgLevel& Cl, int which) {
+    // which: 0 P_x, 1 P_y, 2 R_x, 3 R_y, 4 J_x, 5 J_y
+    Tab1 t{};
+    t.idx = Cl.t_idx + Cl.t_off[which];
+    t.w = Cl.t_w + Cl.t_off[which];
+    t.cnt = Cl.t_cnt + Cl.t_coff[which];
+    t.m = Cl.t_m[which];
+    return t;
+}
+
+// up: out_f = P in_c (coarse -> fine); down: out_c = P^T in_f (fine -> coarse)
+int transfer(const MgLevel& F, const MgLevel& Cl, int prec, bool up, const void* in, void* out, cudaStream_t s) {
+    const int64_t n = up ? F.NX * F.NY * F.NZ : Cl.NX * Cl.NY * Cl.NZ;
+    const Tab1 tx = dev_tab(Cl, up ? 0 : 2), ty = dev_tab(Cl, up ? 1 : 3);
+    const int64_t NXo = up ? F.NX : Cl.NX, NYo = up ? F.NY : Cl.NY;
+    const int64_t NXi = up ? Cl.NX : F.NX, NYi = up ? Cl.NY : F.NY;
+    if (prec == STOKES_F32)
+        transfer_kernel<float, float><<<blocks_for(n), TPB, 0, s>>>(NXo, NYo, F.NZ, NXi, NYi, tx, ty, 3,
+                                                                    static_cast<const float*>(in), static_cast<float*>(out));
+    else
+        transfer_kernel<double, double><<<blocks_for(n), TPB, 0, s>>>(NXo, NYo, F.NZ, NXi, NYi, tx, ty, 3,
+                                                                      static_cast<const double*>(in), static_cast<double*>(out));
     MG_CU(cudaGetLastError(), "multigrid transfer");
     return STOKES_OK;
 }
@@ -246,10 +244,10 @@ int vcycle(Multigrid& mg, size_t l, cudaStream_t s) {
     MgLevel& C = mg.L[l + 1];
     MG_CK(residual(mg, Lv, s));
     MG_CK(project(Lv, mg.prec, Lv.r, s));
-    MG_CK(transfer(Lv, C, mg.prec, mg.periodic, false, Lv.r, C.b, s));
+    MG_CK(transfer(Lv, C, mg.prec, false, Lv.r, C.b, s));
     MG_CK(project(C, mg.prec, C.b, s));
     MG_CK(vcycle(mg, l + 1, s));
-    MG_CK(transfer(Lv, C, mg.prec, mg.periodic, true, C.x, Lv.t, s));
+    MG_CK(transfer(Lv, C, mg.prec, true, C.x, Lv.t, s));
     MG_CK(project(Lv, mg.prec, Lv.t, s));
     MG_CU(vec_axpby(Lv.nu, 1.0, nullptr, mg.prec, Lv.t, 1.0, mg.prec, Lv.x, s), "coarse correction");
     MG_CK(smooth(mg, Lv, s));
@@ -259,7 +257,7 @@ int vcycle(Multigrid& mg, size_t l, cudaStream_t s) {
 }  // namespace
 
 bool mg_eligible(const stokes_mesh* m) {
-    return m && m->on_device && m->h.lattice && m->h.k == 2 && m->h.n_hang == 0 && m->h.nx % 2 == 0 &&
+    return m && m->on_device && m->h.lattice && m->h.k >= 2 && m->h.k <= 4 && m->h.n_hang == 0 && m->h.nx % 2 == 0 &&
            m->h.ny % 2 == 0 && m->h.nx >= 4 && m->h.ny >= 4;
 }
 
@@ -288,21 +286,31 @@ int mg_create(Multigrid& mg, const stokes_mesh* fine, stokes_state* st_fine, voi
         const MgLevel& P = mg.L.back();
         const HostMesh& h = P.mesh->h;
         if (h.nx % 2 || h.ny % 2 || h.nx / 2 < 2 || h.ny / 2 < 2) break;
-        // coarse mesh: the fine lattice heights at the coarse GLL points
-        // (the fine element vertices, lattice points 2 Xc, 2 Yc)
+        // 1-D transfer tables of this level pair (x and y)
+        HostTab1 PX, RX, JX, PY, RY, JY;
+        build_dir(h.nx, h.k, h.periodic, h.tab.gll, PX, RX, JX);
+        build_dir(h.ny, h.k, h.periodic, h.tab.gll, PY, RY, JY);
+        // coarse mesh: the fine isoparametric heights interpolated at the
+        // coarse GLL points (for k = 2 the fine element vertices)
         stokes_mesh_desc d{};
-        d.nx = h.nx / 2; d.ny = h.ny / 2; d.nz = h.nz; d.k = 2;
+        d.nx = h.nx / 2; d.ny = h.ny / 2; d.nz = h.nz; d.k = h.k;
         d.pressure_space = h.pspace; d.periodic_xy = h.periodic ? 1 : 0;
         d.Lx = h.Lx; d.Ly = h.Ly; d.basal_bc = h.basal_bc; d.device = fine->device;
-        const int64_t NXc = h.periodic ? int64_t(d.nx) * 2 : int64_t(d.nx) * 2 + 1;
-        const int64_t NYc = h.periodic ? int64_t(d.ny) * 2 : int64_t(d.ny) * 2 + 1;
+        const int64_t NXc = int64_t(JX.cnt.size()), NYc = int64_t(JY.cnt.size());
         std::vector<double> bed(size_t(NXc * NYc)), surf(size_t(NXc * NYc));
         for (int64_t Yc = 0; Yc < NYc; ++Yc)
             for (int64_t Xc = 0; Xc < NXc; ++Xc) {
-                const int64_t g0 = 2 * Xc + P.NX * (2 * Yc);
-                const int64_t g1 = g0 + P.NX * P.NY * (P.NZ - 1);
-                bed[size_t(Xc + NXc * Yc)] = h.node_xyz[size_t(3 * g0 + 2)];
-                surf[size_t(Xc + NXc * Yc)] = h.node_xyz[size_t(3 * g1 + 2)];
+                double sb = 0, ss = 0;
+                for (int b2 = 0; b2 < JY.cnt[Yc]; ++b2)
+                    for (int a2 = 0; a2 < JX.cnt[Xc]; ++a2) {
+                        const double w = JX.w[size_t(Xc) * KP + a2] * JY.w[size_t(Yc) * KP + b2];
+                        const int64_t g0 = JX.idx[size_t(Xc) * KP + a2] + P.NX * int64_t(JY.idx[size_t(Yc) * KP + b2]);
+                        const int64_t g1 = g0 + P.NX * P.NY * (P.NZ - 1);
+                        sb += w * h.node_xyz[size_t(3 * g0 + 2)];
+                        ss += w * h.node_xyz[size_t(3 * g1 + 2)];
+                    }
+                bed[size_t(Xc + NXc * Yc)] = sb;
+                surf[size_t(Xc + NXc * Yc)] = ss;
             }
         d.bed_nodes = bed.data();
         d.surface_nodes = surf.data();
@@ -325,6 +333,24 @@ int mg_create(Multigrid& mg, const stokes_mesh* fine, stokes_state* st_fine, voi
         MG_CK(dalloc(&Cl.t, size_t(Cl.n) * isz));
         MG_CK(dalloc(reinterpret_cast<void**>(&Cl.u64), size_t(Cl.n) * 8));
         MG_CK(dalloc(reinterpret_cast<void**>(&Cl.logbeta), size_t(std::max<int64_t>(hc.Nb, 1)) * 8));
+        // upload the six tables (P_x, P_y, R_x, R_y, J_x, J_y) in one buffer each
+        const HostTab1* T6[6] = {&PX, &PY, &RX, &RY, &JX, &JY};
+        std::vector<int32_t> idx, cnt;
+        std::vector<double> w;
+        for (int q6 = 0; q6 < 6; ++q6) {
+            Cl.t_off[q6] = int64_t(idx.size());
+            Cl.t_coff[q6] = int64_t(cnt.size());
+            Cl.t_m[q6] = T6[q6]->m;
+            idx.insert(idx.end(), T6[q6]->idx.begin(), T6[q6]->idx.end());
+            w.insert(w.end(), T6[q6]->w.begin(), T6[q6]->w.end());
+            cnt.insert(cnt.end(), T6[q6]->cnt.begin(), T6[q6]->cnt.end());
+        }
+        MG_CK(dalloc(reinterpret_cast<void**>(&Cl.t_idx), idx.size() * 4));
+        MG_CK(dalloc(reinterpret_cast<void**>(&Cl.t_w), w.size() * 8));
+        MG_CK(dalloc(reinterpret_cast<void**>(&Cl.t_cnt), cnt.size() * 4));
+        MG_CU(cudaMemcpy(Cl.t_idx, idx.data(), idx.size() * 4, cudaMemcpyHostToDevice), "tables");
+        MG_CU(cudaMemcpy(Cl.t_w, w.data(), w.size() * 8, cudaMemcpyHostToDevice), "tables");
+        MG_CU(cudaMemcpy(Cl.t_cnt, cnt.data(), cnt.size() * 4, cudaMemcpyHostToDevice), "tables");
     }
     if (mg.L.size() < 2) {
         mg_destroy(mg);
@@ -339,13 +365,16 @@ int mg_setup(Multigrid& mg, const stokes_params* p, const double* up_fine, doubl
         MgLevel& F = mg.L[l - 1];
         MgLevel& C = mg.L[l];
         const double* uf = l == 1 ? up_fine : F.u64;
-        inject_u_kernel<<<blocks_for(C.NX * C.NY * C.NZ), TPB, 0, s>>>(C.NX, C.NY, C.NZ, F.NX, F.NY, uf, C.u64);
-        MG_CU(cudaGetLastError(), "multigrid injection");
+        // the fine linearisation point interpolated at the coarse nodes
+        transfer_kernel<double, double><<<blocks_for(C.NX * C.NY * C.NZ), TPB, 0, s>>>(
+            C.NX, C.NY, C.NZ, F.NX, F.NY, dev_tab(C, 4), dev_tab(C, 5), 3, uf, C.u64);
+        MG_CU(cudaGetLastError(), "multigrid interpolation");
         stokes_params pc = *p;
         if (p->robin && p->logbeta) {
             const double* lf = l == 1 ? p->logbeta : F.logbeta;
-            inject_lb_kernel<<<blocks_for(C.NX * C.NY), TPB, 0, s>>>(C.NX, C.NY, F.NX, lf, C.logbeta);
-            MG_CU(cudaGetLastError(), "multigrid injection");
+            transfer_kernel<double, double><<<blocks_for(C.NX * C.NY), TPB, 0, s>>>(
+                C.NX, C.NY, 1, F.NX, F.NY, dev_tab(C, 4), dev_tab(C, 5), 1, lf, C.logbeta);
+            MG_CU(cudaGetLastError(), "multigrid interpolation");
             pc.logbeta = C.logbeta;
         }
         pc.constraint_scale = C.scale > 0 ? C.scale : 1.0;
@@ -392,6 +421,9 @@ void mg_destroy(Multigrid& mg) {
             if (Lv.A) cudaFree(Lv.A);
             if (Lv.u64) cudaFree(Lv.u64);
             if (Lv.logbeta) cudaFree(Lv.logbeta);
+            if (Lv.t_idx) cudaFree(Lv.t_idx);
+            if (Lv.t_w) cudaFree(Lv.t_w);
+            if (Lv.t_cnt) cudaFree(Lv.t_cnt);
             if (Lv.st) stokes_state_destroy(Lv.st);
             if (Lv.mesh) stokes_mesh_destroy(Lv.mesh);
         }

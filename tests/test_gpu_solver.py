@@ -209,7 +209,7 @@ def _mg_opts(inner, rtol=1e-11):
     return op
 
 
-@pytest.mark.parametrize("name", ["slab_8x8x2_q2p1", "box_4x4x2_q2p1"])
+@pytest.mark.parametrize("name", ["slab_8x8x2_q2p1", "box_4x4x2_q2p1", "slab_6x6x2_q3q1", "slab_4x4x2_q4p3"])
 @pytest.mark.parametrize("inner", [capi.STOKES_F64, capi.STOKES_F32])
 def test_multigrid_newton_reaches_oracle_solution(name, inner):
     """Velocity block by the column-preserving geometric multigrid: the same
