@@ -303,9 +303,10 @@ typedef struct {
     int velocity_mg;     /* 1: the velocity block of the preconditioner is a geometric
                             multigrid V-cycle (horizontal semi-coarsening that keeps the
                             node columns, as the paper's column-preserving aggregation
-                            of Section 5; column-block smoother) on conforming meshes of
-                            degree 2, 3, 4 with nx, ny even and >= 4 (the default
-                            when opts is NULL);
+                            of Section 5; column-block smoother) on meshes of degree
+                            2, 3, 4: conforming meshes with nx, ny even and >= 4, and
+                            2:1 forests with nx, ny >= 2, whose unrefined base mesh is
+                            the first coarse level (the default when opts is NULL);
                             other meshes, and 0, use the column blocks alone       */
 } stokes_solver_opts;
 
@@ -360,10 +361,21 @@ int stokes_linear_solve(stokes_solver* solver, const stokes_params* params, cons
  * succeed and the one after fails as if the device were out of memory (the
  * entry point making it returns STOKES_E_NOMEM and frees what it had
  * allocated); n < 0 switches the hook off (the default).  Process-wide;
- * returns the previous setting. */
+ * returns the previous setting.
+ *
+ * stokes_debug_forest_prolongation: builds, on the host, the prolongation of
+ * the velocity multigrid from base (the unrefined mesh of forest: same grid,
+ * degree, geometry and periodicity, no refinement) to forest, and checks that
+ * it reproduces the forest's node coordinates from the base's (heights, and
+ * x, y away from a periodic seam).  Both meshes host-only (device = -1).
+ * *nnz receives the prolongation's entries, *rowsum_err the largest
+ * |row sum - 1|.  STOKES_E_MESH if the meshes do not match or the check
+ * fails; STOKES_E_INVAL for device meshes. */
 #define STOKES_WAIT_POLLS_DEFAULT 4194304u
 int stokes_debug_wait_limit(stokes_mesh* mesh, uint32_t polls);
 int64_t stokes_debug_fail_alloc_after(int64_t n);
+int stokes_debug_forest_prolongation(const stokes_mesh* forest, const stokes_mesh* base, int64_t* nnz,
+                                     double* rowsum_err);
 
 /* Per-kernel timing (tracing).  Between stokes_profile_begin and
  * stokes_profile_end every operator call on this mesh, and every launch and

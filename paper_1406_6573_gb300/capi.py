@@ -127,6 +127,8 @@ _SIGS = {
     "stokes_last_error": (C.c_char_p, []),
     "stokes_debug_wait_limit": (C.c_int, [C.c_void_p, C.c_uint32]),
     "stokes_debug_fail_alloc_after": (C.c_int64, [C.c_int64]),
+    "stokes_debug_forest_prolongation": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_int64),
+                                                   C.POINTER(C.c_double)]),
 }
 
 _lib = None
@@ -196,6 +198,15 @@ def stokes_mesh_node_coords(h, out):
 
 def stokes_mesh_basal_nodes(h, out):
     _check(lib().stokes_mesh_basal_nodes(h, _ptr(out)))
+
+
+def stokes_debug_forest_prolongation(forest, base):
+    """(entries, largest |row sum - 1|) of the forest multigrid's prolongation
+    from base to forest (host-only meshes); raises on a mismatch."""
+    nnz = C.c_int64(0)
+    err = C.c_double(0.0)
+    _check(lib().stokes_debug_forest_prolongation(forest, base, C.byref(nnz), C.byref(err)))
+    return nnz.value, err.value
 
 
 def stokes_debug_wait_limit(h, polls):

@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 
 #include "handles.h"
+#include "mg.h"
 #include "khigh.h"
 
 using namespace stokes;
@@ -295,6 +296,24 @@ int stokes_mesh_create(const stokes_mesh_desc* desc, stokes_mesh** out) {
         rc = STOKES_E_NOMEM; err = "host allocation failed while building the mesh";
     }
     if (rc != STOKES_OK) { delete m; return fail(rc, err); }
+    {
+        // keep the mesh's sources for related meshes (multigrid levels)
+        const int64_t nc = int64_t(desc->nx) * desc->ny * desc->nz;
+        if (desc->refine) m->src.refine.assign(desc->refine, desc->refine + nc);
+        auto keep = [](const stokes_field& f, std::vector<double>* v, double& mean) {
+            mean = f.mean;
+            const double* arr[4] = {f.amp, f.kx, f.ky, f.phase};
+            for (int q4 = 0; q4 < 4; ++q4) v[q4].assign(arr[q4], arr[q4] + (f.n_modes > 0 ? f.n_modes : 0));
+        };
+        keep(desc->bed, m->src.bed, m->src.bed_mean);
+        keep(desc->surface, m->src.surf, m->src.surf_mean);
+        if (desc->bed_nodes) {
+            const int64_t NXg = int64_t(desc->nx) * desc->k + (desc->periodic_xy ? 0 : 1);
+            const int64_t NYg = int64_t(desc->ny) * desc->k + (desc->periodic_xy ? 0 : 1);
+            m->src.bed_nodes.assign(desc->bed_nodes, desc->bed_nodes + NXg * NYg);
+            m->src.surf_nodes.assign(desc->surface_nodes, desc->surface_nodes + NXg * NYg);
+        }
+    }
     m->device = desc->device;
     if (desc->device >= 0) {
         if (m->h.k < 2 || m->h.k > KMAX) {
@@ -405,6 +424,25 @@ int stokes_debug_wait_limit(stokes_mesh* mesh, uint32_t polls) {
 
 int64_t stokes_debug_fail_alloc_after(int64_t n) {
     return g_alloc_budget.exchange(n < 0 ? -1 : n);
+}
+
+int stokes_debug_forest_prolongation(const stokes_mesh* forest, const stokes_mesh* base, int64_t* nnz,
+                                     double* rowsum_err) {
+    using namespace stokes;
+    if (!forest || !base || !nnz || !rowsum_err) return fail(STOKES_E_INVAL, "null argument");
+    if (forest->on_device || base->on_device) return fail(STOKES_E_INVAL, "host-only meshes expected");
+    HostCsr P;
+    const int rc = forest_prolongation(forest->h, forest->h.elem_nodes, forest->src.refine, base->h, P);
+    if (rc != STOKES_OK) return rc;
+    double worst = 0;
+    for (size_t g = 0; g + 1 < P.ptr.size(); ++g) {
+        double sum = 0;
+        for (int32_t j = P.ptr[g]; j < P.ptr[g + 1]; ++j) sum += P.w[size_t(j)];
+        worst = std::max(worst, std::fabs(sum - 1.0));
+    }
+    *nnz = int64_t(P.col.size());
+    *rowsum_err = worst;
+    return STOKES_OK;
 }
 
 int stokes_mesh_destroy(stokes_mesh* mesh) {

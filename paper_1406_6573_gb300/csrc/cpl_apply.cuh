@@ -489,9 +489,7 @@ int launch_cpl_t(const ElemArgs& a, cudaStream_t s) {
         max_blocks = (per_sm > 0 ? per_sm : 1) * sms;
         configured_device = dev;
     }
-    const int64_t ngroups = (a.E + CPL_E - 1) / CPL_E;
-    int64_t blocks = (ngroups + C::W - 1) / C::W;
-    if (blocks > max_blocks) blocks = max_blocks;
+    const int64_t blocks = persistent_blocks((a.E + CPL_E - 1) / CPL_E, C::W, max_blocks);
     cpl_state_apply_kernel<PS, PONLY><<<unsigned(blocks), 32 * C::W, C::SMEM, s>>>(a);
     return int(cudaGetLastError());
 }

@@ -63,9 +63,19 @@ int64_t state_stride(int k);
 
 }  // namespace stokes
 
+// Host copy of what a mesh was built from (geometry and refinement), so that
+// related meshes (the multigrid's base and coarse levels) can be built.
+struct MeshSource {
+    std::vector<uint8_t> refine;                      // [ncoarse] or empty
+    std::vector<double> bed[4], surf[4];              // modal fields: amp, kx, ky, phase
+    double bed_mean = 0, surf_mean = 0;
+    std::vector<double> bed_nodes, surf_nodes;        // gridded heights, or empty
+};
+
 struct stokes_mesh {
     mutable stokes::Profiler prof;
     stokes::HostMesh h;
+    MeshSource src;
     int device = -1;
     bool on_device = false;
     int32_t* d_nodes = nullptr;

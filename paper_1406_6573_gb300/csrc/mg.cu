@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include "mg.h"
+#include "hanging.h"
 #include "precond.h"
 #include "vec.h"
 
@@ -54,6 +55,20 @@ __global__ void transfer_kernel(int64_t NXo, int64_t NYo, int64_t NZ, int64_t NX
         }
     }
     for (int c = 0; c < ncomp; ++c) out[ncomp * t + c] = TO(s[c]);
+}
+
+// out[row * nc + c] = sum_j w[j] in[col[j] * nc + c]  (CSR, nc components)
+template <typename TI, typename TO>
+__global__ void csr_kernel(int64_t rows, const int32_t* __restrict__ ptr, const int32_t* __restrict__ col,
+                           const double* __restrict__ w, int nc, const TI* __restrict__ in, TO* __restrict__ out) {
+    const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (r >= rows) return;
+    double s[3] = {0.0, 0.0, 0.0};
+    for (int j = ptr[r]; j < ptr[r + 1]; ++j) {
+        const int64_t c = col[j];
+        for (int q = 0; q < nc; ++q) s[q] += w[j] * double(in[nc * c + q]);
+    }
+    for (int q = 0; q < nc; ++q) out[nc * r + q] = TO(s[q]);
 }
 
 // Lagrange polynomials of the nodes x[0..n) at t
@@ -198,6 +213,20 @@ Tab1 dev_tab(const MgLevel& Cl, int which) {
 
 // up: out_f = P in_c (coarse -> fine); down: out_c = P^T in_f (fine -> coarse)
 int transfer(const MgLevel& F, const MgLevel& Cl, int prec, bool up, const void* in, void* out, cudaStream_t s) {
+    if (Cl.csr) {
+        const int64_t rows = up ? F.mesh->h.Nv : Cl.mesh->h.Nv;
+        const int32_t* ptr = up ? Cl.P_ptr : Cl.R_ptr;
+        const int32_t* col = up ? Cl.P_col : Cl.R_col;
+        const double* w = up ? Cl.P_w : Cl.R_w;
+        if (prec == STOKES_F32)
+            csr_kernel<float, float><<<blocks_for(rows), TPB, 0, s>>>(rows, ptr, col, w, 3, static_cast<const float*>(in),
+                                                                      static_cast<float*>(out));
+        else
+            csr_kernel<double, double><<<blocks_for(rows), TPB, 0, s>>>(rows, ptr, col, w, 3, static_cast<const double*>(in),
+                                                                        static_cast<double*>(out));
+        MG_CU(cudaGetLastError(), "multigrid transfer");
+        return STOKES_OK;
+    }
     const int64_t n = up ? F.NX * F.NY * F.NZ : Cl.NX * Cl.NY * Cl.NZ;
     const Tab1 tx = dev_tab(Cl, up ? 0 : 2), ty = dev_tab(Cl, up ? 1 : 3);
     const int64_t NXo = up ? F.NX : Cl.NX, NYo = up ? F.NY : Cl.NY;
@@ -212,10 +241,24 @@ int transfer(const MgLevel& F, const MgLevel& Cl, int prec, bool up, const void*
     return STOKES_OK;
 }
 
+double level_omega(const Multigrid& mg, const MgLevel& Lv) { return Lv.omega > 0 ? Lv.omega : mg.omega; }
+
+// deterministic start vector of the power iteration: hashed values in [-1, 1)
+template <typename T>
+__global__ void hash_fill_kernel(int64_t n, T* v) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint64_t z = uint64_t(i) * 0x9E3779B97F4A7C15ull + 0x632BE59BD9B4E019ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    v[i] = T(double(z >> 11) * (2.0 / 9007199254740992.0) - 1.0);
+}
+
 // x = omega C^-1 b  (first smoothing step from x = 0)
 int smooth_first(Multigrid& mg, MgLevel& Lv, cudaStream_t s) {
     MG_CU(launch_col_solve(mg.prec, level_cs(Lv, Lv.scale), Lv.b, Lv.t, s), "column solve");
-    MG_CU(vec_axpby(Lv.nu, mg.omega, nullptr, mg.prec, Lv.t, 0.0, mg.prec, Lv.x, s), "smoothing");
+    MG_CU(vec_axpby(Lv.nu, level_omega(mg, Lv), nullptr, mg.prec, Lv.t, 0.0, mg.prec, Lv.x, s), "smoothing");
     return STOKES_OK;
 }
 
@@ -230,12 +273,26 @@ int residual(Multigrid& mg, MgLevel& Lv, cudaStream_t s) {
 int smooth(Multigrid& mg, MgLevel& Lv, cudaStream_t s) {
     MG_CK(residual(mg, Lv, s));
     MG_CU(launch_col_solve(mg.prec, level_cs(Lv, Lv.scale), Lv.r, Lv.t, s), "column solve");
-    MG_CU(vec_axpby(Lv.nu, mg.omega, nullptr, mg.prec, Lv.t, 1.0, mg.prec, Lv.x, s), "smoothing");
+    MG_CU(vec_axpby(Lv.nu, level_omega(mg, Lv), nullptr, mg.prec, Lv.t, 1.0, mg.prec, Lv.x, s), "smoothing");
     return STOKES_OK;
 }
 
 int vcycle(Multigrid& mg, size_t l, cudaStream_t s) {
     MgLevel& Lv = mg.L[l];
+    if (l + 1 < mg.L.size() && mg.L[l + 1].csr && mg.forest_additive) {
+        // forest level: column blocks and the base-level cycle side by side
+        MgLevel& C = mg.L[l + 1];
+        MG_CU(launch_col_solve(mg.prec, level_cs(Lv, Lv.scale), Lv.b, Lv.x, s), "column solve");
+        MG_CU(vec_axpby(Lv.nu, 1.0, nullptr, mg.prec, Lv.b, 0.0, mg.prec, Lv.r, s), "residual copy");
+        MG_CK(project(Lv, mg.prec, Lv.r, s));
+        MG_CK(transfer(Lv, C, mg.prec, false, Lv.r, C.b, s));
+        MG_CK(project(C, mg.prec, C.b, s));
+        MG_CK(vcycle(mg, l + 1, s));
+        MG_CK(transfer(Lv, C, mg.prec, true, C.x, Lv.t, s));
+        MG_CK(project(Lv, mg.prec, Lv.t, s));
+        MG_CU(vec_axpby(Lv.nu, 1.0, nullptr, mg.prec, Lv.t, 1.0, mg.prec, Lv.x, s), "coarse correction");
+        return STOKES_OK;
+    }
     MG_CK(smooth_first(mg, Lv, s));
     if (l + 1 == mg.L.size()) {
         for (int it = 1; it < mg.coarse_sweeps; ++it) MG_CK(smooth(mg, Lv, s));
@@ -254,18 +311,243 @@ int vcycle(Multigrid& mg, size_t l, cudaStream_t s) {
     return STOKES_OK;
 }
 
+// Largest eigenvalue of C^-1 A on level Lv (C: its factored column blocks,
+// A: its velocity block with the constraint rows) by power iteration from a
+// hashed start vector; uses Lv.x and Lv.t.
+int estimate_lmax(Multigrid& mg, MgLevel& Lv, int its, double& lmax, cudaStream_t s) {
+    if (mg.prec == STOKES_F32) hash_fill_kernel<float><<<blocks_for(Lv.nu), TPB, 0, s>>>(Lv.nu, static_cast<float*>(Lv.x));
+    else hash_fill_kernel<double><<<blocks_for(Lv.nu), TPB, 0, s>>>(Lv.nu, static_cast<double*>(Lv.x));
+    MG_CU(cudaGetLastError(), "power iteration start");
+    MG_CK(project(Lv, mg.prec, Lv.x, s));
+    MG_CU(vec_multidot(Lv.nu, mg.prec, nullptr, 0, 0, mg.prec, Lv.x, mg.dsc, 1, s), "norm");
+    MG_CU(vec_normalize(Lv.nu, mg.prec, Lv.x, mg.dsc, s), "normalise");
+    for (int it = 0; it < its; ++it) {
+        MG_CK(stokes_state_apply(Lv.st, Lv.x, Lv.r, s));
+        MG_CU(launch_col_solve(mg.prec, level_cs(Lv, Lv.scale), Lv.r, Lv.t, s), "column solve");
+        MG_CU(vec_multidot(Lv.nu, mg.prec, nullptr, 0, 0, mg.prec, Lv.t, mg.dsc, 1, s), "norm");
+        MG_CU(vec_axpby(Lv.nu, 1.0, nullptr, mg.prec, Lv.t, 0.0, mg.prec, Lv.x, s), "copy");
+        MG_CU(vec_normalize(Lv.nu, mg.prec, Lv.x, mg.dsc, s), "normalise");
+    }
+    double n2 = 0;
+    MG_CU(cudaMemcpyAsync(&n2, mg.dsc, sizeof(double), cudaMemcpyDeviceToHost, s), "readback");
+    MG_CU(cudaStreamSynchronize(s), "sync");
+    lmax = std::sqrt(n2);
+    // the work vectors start the cycle from zero again
+    MG_CU(cudaMemsetAsync(Lv.x, 0, size_t(Lv.n) * (mg.prec == STOKES_F32 ? 4 : 8), s), "clear");
+    MG_CU(cudaMemsetAsync(Lv.t, 0, size_t(Lv.n) * (mg.prec == STOKES_F32 ? 4 : 8), s), "clear");
+    return STOKES_OK;
+}
+
 }  // namespace
 
 bool mg_eligible(const stokes_mesh* m) {
-    return m && m->on_device && m->h.lattice && m->h.k >= 2 && m->h.k <= 4 && m->h.n_hang == 0 && m->h.nx % 2 == 0 &&
-           m->h.ny % 2 == 0 && m->h.nx >= 4 && m->h.ny >= 4;
+    if (!m || !m->on_device || m->h.k < 2 || m->h.k > 4) return false;
+    if (!m->h.lattice) return m->h.nx >= 2 && m->h.ny >= 2;       // forest: the base mesh is the next level
+    return m->h.n_hang == 0 && m->h.nx % 2 == 0 && m->h.ny % 2 == 0 && m->h.nx >= 4 && m->h.ny >= 4;
 }
+
+int forest_prolongation(const HostMesh& h, const std::vector<int32_t>& nodes, const std::vector<uint8_t>& refine,
+                        const HostMesh& hb, HostCsr& P) {
+    const int k = h.k, n1 = k + 1, N3 = n1 * n1 * n1;
+    const int64_t NXb = hb.latNX, NYb = hb.latNY;
+    const int64_t nc = int64_t(h.nx) * h.ny * h.nz;
+    if (!hb.lattice || hb.k != k || hb.nx != h.nx || hb.ny != h.ny || hb.nz != h.nz || nodes.size() != size_t(h.E) * N3 ||
+        h.elem_hang.size() != size_t(h.E) || h.node_xyz.size() != size_t(3 * h.Nv) ||
+        hb.node_xyz.size() != size_t(3 * hb.Nv) || (!refine.empty() && refine.size() != size_t(nc)))
+        return fail(STOKES_E_MESH, "the forest and its base mesh do not match");
+    // element -> coarse cell (children of a refined cell are consecutive)
+    std::vector<int64_t> cell(size_t(h.E));
+    {
+        int64_t e = 0;
+        for (int64_t c = 0; c < nc; ++c) {
+            const int nch = (!refine.empty() && refine[size_t(c)]) ? 8 : 1;
+            for (int ch = 0; ch < nch; ++ch) {
+                if (e >= h.E) return fail(STOKES_E_MESH, "forest element count does not match its refinement mask");
+                cell[size_t(e++)] = c;
+            }
+        }
+        if (e != h.E) return fail(STOKES_E_MESH, "forest element count does not match its refinement mask");
+    }
+    // rows: forest global nodes, each from the first non-hanging slot naming it
+    std::vector<std::vector<std::pair<int32_t, double>>> rows(size_t(h.Nv));
+    std::vector<char> done(size_t(h.Nv), 0);
+    double L[3][N1MAX];
+    for (int64_t e = 0; e < h.E; ++e) {
+        const uint32_t hc = h.elem_hang[size_t(e)];
+        const int64_t c = cell[size_t(e)];
+        const bool child = !refine.empty() && refine[size_t(c)];
+        const int64_t cx = c % h.nx, cy = (c / h.nx) % h.ny, cz = c / (int64_t(h.nx) * h.ny);
+        for (int n = 0; n < N3; ++n) {
+            const int idx[3] = {n % n1, (n / n1) % n1, n / (n1 * n1)};
+            if (slot_on_hanging_entity(hc, idx, k)) continue;
+            const int64_t g = nodes[size_t(e) * N3 + n];
+            if (g < 0 || g >= h.Nv) return fail(STOKES_E_MESH, "forest element map out of range");
+            if (done[size_t(g)]) continue;
+            done[size_t(g)] = 1;
+            // the slot's coordinates in the base cell's reference element
+            for (int dd = 0; dd < 3; ++dd) {
+                const double xi = child ? double(child_bit(hc, dd)) + 0.5 * (h.tab.gll[idx[dd]] + 1.0) - 1.0
+                                        : h.tab.gll[idx[dd]];
+                lagrange_at(n1, h.tab.gll, xi, L[dd]);
+            }
+            for (int c2 = 0; c2 < n1; ++c2)
+                for (int b2 = 0; b2 < n1; ++b2)
+                    for (int a2 = 0; a2 < n1; ++a2) {
+                        const double wgt = L[0][a2] * L[1][b2] * L[2][c2];
+                        if (std::fabs(wgt) < 1e-14) continue;
+                        int64_t X = cx * k + a2, Y = cy * k + b2;
+                        if (h.periodic) { X %= NXb; Y %= NYb; }
+                        const int64_t gb = X + NXb * (Y + NYb * (cz * k + c2));
+                        if (gb < 0 || gb >= hb.Nv) return fail(STOKES_E_MESH, "base lattice node out of range");
+                        rows[size_t(g)].push_back({int32_t(gb), wgt});
+                    }
+        }
+    }
+    P.ptr.assign(size_t(h.Nv) + 1, 0);
+    P.col.clear();
+    P.w.clear();
+    for (int64_t g = 0; g < h.Nv; ++g) {
+        if (!done[size_t(g)]) return fail(STOKES_E_MESH, "a forest node has no element slot of its own");
+        P.ptr[size_t(g) + 1] = P.ptr[size_t(g)] + int32_t(rows[size_t(g)].size());
+        for (auto& pr : rows[size_t(g)]) { P.col.push_back(pr.first); P.w.push_back(pr.second); }
+    }
+    // the base map interpolated at the forest nodes is the forest map (the
+    // children inherit their parent's map): heights, and the horizontal
+    // positions away from a periodic seam
+    for (int64_t g = 0; g < h.Nv; ++g) {
+        double x[3] = {0, 0, 0};
+        for (int32_t j = P.ptr[size_t(g)]; j < P.ptr[size_t(g) + 1]; ++j)
+            for (int dd = 0; dd < 3; ++dd) x[dd] += P.w[size_t(j)] * hb.node_xyz[size_t(3 * P.col[size_t(j)] + dd)];
+        const double* xf = &h.node_xyz[size_t(3 * g)];
+        const double tol = 1e-8 * (std::fabs(xf[2]) + std::max(h.Lx, h.Ly));
+        bool bad = std::fabs(x[2] - xf[2]) > tol;
+        if (!h.periodic) bad = bad || std::fabs(x[0] - xf[0]) > tol || std::fabs(x[1] - xf[1]) > tol;
+        if (bad) return fail(STOKES_E_MESH, "the forest's base level does not reproduce its geometry");
+    }
+    return STOKES_OK;
+}
+
+namespace {
+
+HostCsr transpose(const HostCsr& A, int64_t ncols) {
+    HostCsr T;
+    T.ptr.assign(size_t(ncols) + 1, 0);
+    for (int32_t c : A.col) T.ptr[size_t(c) + 1]++;
+    for (int64_t i = 0; i < ncols; ++i) T.ptr[size_t(i) + 1] += T.ptr[size_t(i)];
+    T.col.resize(A.col.size());
+    T.w.resize(A.w.size());
+    std::vector<int32_t> fill(T.ptr.begin(), T.ptr.end() - 1);
+    const int64_t rows = int64_t(A.ptr.size()) - 1;
+    for (int64_t r = 0; r < rows; ++r)
+        for (int32_t j = A.ptr[size_t(r)]; j < A.ptr[size_t(r) + 1]; ++j) {
+            const int32_t c = A.col[size_t(j)];
+            T.col[size_t(fill[size_t(c)])] = int32_t(r);
+            T.w[size_t(fill[size_t(c)])] = A.w[size_t(j)];
+            fill[size_t(c)]++;
+        }
+    return T;
+}
+
+// rows scaled to unit sum (an averaging restriction); empty rows stay empty
+void normalise_rows(HostCsr& A) {
+    const int64_t rows = int64_t(A.ptr.size()) - 1;
+    for (int64_t r = 0; r < rows; ++r) {
+        double s = 0;
+        for (int32_t j = A.ptr[size_t(r)]; j < A.ptr[size_t(r) + 1]; ++j) s += A.w[size_t(j)];
+        if (std::fabs(s) > 1e-12)
+            for (int32_t j = A.ptr[size_t(r)]; j < A.ptr[size_t(r) + 1]; ++j) A.w[size_t(j)] /= s;
+    }
+}
+
+int upload_csr(const HostCsr& A, int32_t** ptr, int32_t** col, double** w) {
+    MG_CK(dalloc(reinterpret_cast<void**>(ptr), A.ptr.size() * 4));
+    MG_CK(dalloc(reinterpret_cast<void**>(col), std::max<size_t>(A.col.size(), 1) * 4));
+    MG_CK(dalloc(reinterpret_cast<void**>(w), std::max<size_t>(A.w.size(), 1) * 8));
+    MG_CU(cudaMemcpy(*ptr, A.ptr.data(), A.ptr.size() * 4, cudaMemcpyHostToDevice), "tables");
+    if (!A.col.empty()) {
+        MG_CU(cudaMemcpy(*col, A.col.data(), A.col.size() * 4, cudaMemcpyHostToDevice), "tables");
+        MG_CU(cudaMemcpy(*w, A.w.data(), A.w.size() * 8, cudaMemcpyHostToDevice), "tables");
+    }
+    return STOKES_OK;
+}
+
+// sizes, stored state, column blocks and work vectors of a coarse level whose
+// mesh is built
+int alloc_level(MgLevel& Cl, int prec) {
+    const size_t isz = prec == STOKES_F32 ? 4 : 8;
+    const HostMesh& hc = Cl.mesh->h;
+    Cl.n = 3 * hc.Nv + hc.Np;
+    Cl.nu = 3 * hc.Nv;
+    Cl.NX = hc.latNX; Cl.NY = hc.latNY; Cl.NZ = int64_t(hc.nz) * hc.k + 1;
+    Cl.bw = 3 * hc.bnode + 2;
+    Cl.band_elems = size_t(3) * hc.colmax * size_t(2 * Cl.bw + 1) * size_t(band_cols(hc.ncol));
+    MG_CK(stokes_state_create(Cl.mesh, prec, &Cl.st));
+    MG_CK(dalloc(&Cl.A, Cl.band_elems * isz));
+    MG_CK(dalloc(&Cl.b, size_t(Cl.n) * isz));
+    MG_CK(dalloc(&Cl.x, size_t(Cl.n) * isz));
+    MG_CK(dalloc(&Cl.r, size_t(Cl.n) * isz));
+    MG_CK(dalloc(&Cl.t, size_t(Cl.n) * isz));
+    MG_CK(dalloc(reinterpret_cast<void**>(&Cl.u64), size_t(Cl.n) * 8));
+    MG_CK(dalloc(reinterpret_cast<void**>(&Cl.logbeta), size_t(std::max<int64_t>(hc.Nb, 1)) * 8));
+    return STOKES_OK;
+}
+
+// The unrefined base mesh of the forest fine and the transfers between them.
+int build_base_level(const stokes_mesh* fine, MgLevel& C) {
+    const HostMesh& h = fine->h;
+    const int k = h.k, N3 = (k + 1) * (k + 1) * (k + 1);
+    stokes_mesh_desc d{};
+    d.nx = h.nx; d.ny = h.ny; d.nz = h.nz; d.k = k; d.pressure_space = h.pspace;
+    d.periodic_xy = h.periodic ? 1 : 0; d.Lx = h.Lx; d.Ly = h.Ly; d.basal_bc = h.basal_bc; d.device = fine->device;
+    const MeshSource& sc = fine->src;
+    d.bed = stokes_field{sc.bed_mean, int(sc.bed[0].size()), sc.bed[0].data(), sc.bed[1].data(), sc.bed[2].data(),
+                         sc.bed[3].data()};
+    d.surface = stokes_field{sc.surf_mean, int(sc.surf[0].size()), sc.surf[0].data(), sc.surf[1].data(),
+                             sc.surf[2].data(), sc.surf[3].data()};
+    if (!sc.bed_nodes.empty()) { d.bed_nodes = sc.bed_nodes.data(); d.surface_nodes = sc.surf_nodes.data(); }
+    C.owned = true;
+    C.csr = true;
+    MG_CK(stokes_mesh_create(&d, &C.mesh));
+    const HostMesh& hb = C.mesh->h;
+    const int64_t NXb = hb.latNX, NYb = hb.latNY;
+    // forest element map (the device copy: a device mesh keeps no host copy)
+    std::vector<int32_t> nodes(size_t(h.E) * N3);
+    MG_CU(cudaMemcpy(nodes.data(), fine->d_nodes, nodes.size() * 4, cudaMemcpyDeviceToHost), "element map");
+    HostCsr P;
+    MG_CK(forest_prolongation(h, nodes, sc.refine, hb, P));
+    HostCsr R = transpose(P, hb.Nv);
+    HostCsr J = R;
+    normalise_rows(J);
+    // basal rows: forest basal node bf -> base basal nodes (the Z = 0 lattice plane)
+    if (h.basal_nodes.size() != size_t(h.Nb)) return fail(STOKES_E_MESH, "the forest's basal node list is incomplete");
+    HostCsr Pb;
+    Pb.ptr.assign(size_t(h.Nb) + 1, 0);
+    for (int64_t bf = 0; bf < h.Nb; ++bf) {
+        const int64_t g = h.basal_nodes[size_t(bf)];
+        if (g < 0 || g >= h.Nv) return fail(STOKES_E_MESH, "forest basal node out of range");
+        for (int32_t j = P.ptr[size_t(g)]; j < P.ptr[size_t(g) + 1]; ++j)
+            if (P.col[size_t(j)] < NXb * NYb) { Pb.col.push_back(P.col[size_t(j)]); Pb.w.push_back(P.w[size_t(j)]); }
+        Pb.ptr[size_t(bf) + 1] = int32_t(Pb.col.size());
+    }
+    HostCsr Jb = transpose(Pb, hb.Nb);
+    normalise_rows(Jb);
+    MG_CK(upload_csr(P, &C.P_ptr, &C.P_col, &C.P_w));
+    MG_CK(upload_csr(R, &C.R_ptr, &C.R_col, &C.R_w));
+    MG_CK(upload_csr(J, &C.J_ptr, &C.J_col, &C.J_w));
+    MG_CK(upload_csr(Jb, &C.Jb_ptr, &C.Jb_col, &C.Jb_w));
+    return STOKES_OK;
+}
+
+}  // namespace
 
 int mg_create(Multigrid& mg, const stokes_mesh* fine, stokes_state* st_fine, void* A_fine, int bw_fine, int prec) {
     mg_destroy(mg);
     if (!mg_eligible(fine)) return fail(STOKES_E_INVAL, "the mesh does not carry the velocity multigrid");
     mg.prec = prec;
     mg.periodic = fine->h.periodic;
+#ifdef STOKES_MG_FOREST_ADDITIVE
+    mg.forest_additive = STOKES_MG_FOREST_ADDITIVE;
+#endif
     const size_t isz = prec == STOKES_F32 ? 4 : 8;
     MgLevel L0;
     L0.mesh = const_cast<stokes_mesh*>(fine);
@@ -282,6 +564,13 @@ int mg_create(Multigrid& mg, const stokes_mesh* fine, stokes_state* st_fine, voi
     MG_CK(dalloc(&F0.r, size_t(F0.n) * isz));
     MG_CK(dalloc(&F0.t, size_t(F0.n) * isz));
     MG_CK(dalloc(reinterpret_cast<void**>(&mg.dsc), sizeof(double)));
+    if (!fine->h.lattice) {
+        // a 2:1 forest: its unrefined base mesh is the first coarse level
+        mg.L.push_back(MgLevel{});
+        MgLevel& B = mg.L.back();
+        MG_CK(build_base_level(fine, B));
+        MG_CK(alloc_level(B, prec));
+    }
     while (true) {
         const MgLevel& P = mg.L.back();
         const HostMesh& h = P.mesh->h;
@@ -316,23 +605,10 @@ int mg_create(Multigrid& mg, const stokes_mesh* fine, stokes_state* st_fine, voi
         d.surface_nodes = surf.data();
         MgLevel C;
         C.owned = true;
-        MG_CK(stokes_mesh_create(&d, &C.mesh));
-        const HostMesh& hc = C.mesh->h;
-        C.n = 3 * hc.Nv + hc.Np;
-        C.nu = 3 * hc.Nv;
-        C.NX = hc.latNX; C.NY = hc.latNY; C.NZ = int64_t(hc.nz) * hc.k + 1;
-        C.bw = 3 * hc.bnode + 2;
-        C.band_elems = size_t(3) * hc.colmax * size_t(2 * C.bw + 1) * size_t(band_cols(hc.ncol));
         mg.L.push_back(C);
         MgLevel& Cl = mg.L.back();
-        MG_CK(stokes_state_create(Cl.mesh, prec, &Cl.st));
-        MG_CK(dalloc(&Cl.A, Cl.band_elems * isz));
-        MG_CK(dalloc(&Cl.b, size_t(Cl.n) * isz));
-        MG_CK(dalloc(&Cl.x, size_t(Cl.n) * isz));
-        MG_CK(dalloc(&Cl.r, size_t(Cl.n) * isz));
-        MG_CK(dalloc(&Cl.t, size_t(Cl.n) * isz));
-        MG_CK(dalloc(reinterpret_cast<void**>(&Cl.u64), size_t(Cl.n) * 8));
-        MG_CK(dalloc(reinterpret_cast<void**>(&Cl.logbeta), size_t(std::max<int64_t>(hc.Nb, 1)) * 8));
+        MG_CK(stokes_mesh_create(&d, &Cl.mesh));
+        MG_CK(alloc_level(Cl, prec));
         // upload the six tables (P_x, P_y, R_x, R_y, J_x, J_y) in one buffer each
         const HostTab1* T6[6] = {&PX, &PY, &RX, &RY, &JX, &JY};
         std::vector<int32_t> idx, cnt;
@@ -365,15 +641,25 @@ int mg_setup(Multigrid& mg, const stokes_params* p, const double* up_fine, doubl
         MgLevel& F = mg.L[l - 1];
         MgLevel& C = mg.L[l];
         const double* uf = l == 1 ? up_fine : F.u64;
-        // the fine linearisation point interpolated at the coarse nodes
-        transfer_kernel<double, double><<<blocks_for(C.NX * C.NY * C.NZ), TPB, 0, s>>>(
-            C.NX, C.NY, C.NZ, F.NX, F.NY, dev_tab(C, 4), dev_tab(C, 5), 3, uf, C.u64);
+        // the fine linearisation point interpolated at the coarse nodes (on a
+        // forest's base level: averaged over the forest nodes each base node
+        // interpolates to)
+        const int64_t Nvc = C.mesh->h.Nv, Nbc = C.mesh->h.Nb;
+        if (C.csr)
+            csr_kernel<double, double><<<blocks_for(Nvc), TPB, 0, s>>>(Nvc, C.J_ptr, C.J_col, C.J_w, 3, uf, C.u64);
+        else
+            transfer_kernel<double, double><<<blocks_for(C.NX * C.NY * C.NZ), TPB, 0, s>>>(
+                C.NX, C.NY, C.NZ, F.NX, F.NY, dev_tab(C, 4), dev_tab(C, 5), 3, uf, C.u64);
         MG_CU(cudaGetLastError(), "multigrid interpolation");
         stokes_params pc = *p;
         if (p->robin && p->logbeta) {
             const double* lf = l == 1 ? p->logbeta : F.logbeta;
-            transfer_kernel<double, double><<<blocks_for(C.NX * C.NY), TPB, 0, s>>>(
-                C.NX, C.NY, 1, F.NX, F.NY, dev_tab(C, 4), dev_tab(C, 5), 1, lf, C.logbeta);
+            if (C.csr)
+                csr_kernel<double, double><<<blocks_for(Nbc), TPB, 0, s>>>(Nbc, C.Jb_ptr, C.Jb_col, C.Jb_w, 1, lf,
+                                                                          C.logbeta);
+            else
+                transfer_kernel<double, double><<<blocks_for(C.NX * C.NY), TPB, 0, s>>>(
+                    C.NX, C.NY, 1, F.NX, F.NY, dev_tab(C, 4), dev_tab(C, 5), 1, lf, C.logbeta);
             MG_CU(cudaGetLastError(), "multigrid interpolation");
             pc.logbeta = C.logbeta;
         }
@@ -402,6 +688,13 @@ int mg_setup(Multigrid& mg, const stokes_params* p, const double* up_fine, doubl
         }
         C.st->params.constraint_scale = C.scale;
         MG_CU(launch_col_factor(mg.prec, level_cs(C, C.scale), s), "coarse column factorisation");
+        if (l + 1 == mg.L.size()) {
+            // coarsest level: damping of its sweeps from the spectrum of C^-1 A
+            double lm = 0;
+            MG_CK(estimate_lmax(mg, C, 10, lm, s));
+            C.lmax = lm;
+            C.omega = (std::isfinite(lm) && lm > 0) ? std::min(mg.omega, 1.6 / lm) : mg.omega;
+        }
     }
     return STOKES_OK;
 }
@@ -424,6 +717,10 @@ void mg_destroy(Multigrid& mg) {
             if (Lv.t_idx) cudaFree(Lv.t_idx);
             if (Lv.t_w) cudaFree(Lv.t_w);
             if (Lv.t_cnt) cudaFree(Lv.t_cnt);
+            for (void* p : {(void*)Lv.P_ptr, (void*)Lv.P_col, (void*)Lv.P_w, (void*)Lv.R_ptr, (void*)Lv.R_col,
+                            (void*)Lv.R_w, (void*)Lv.J_ptr, (void*)Lv.J_col, (void*)Lv.J_w, (void*)Lv.Jb_ptr,
+                            (void*)Lv.Jb_col, (void*)Lv.Jb_w})
+                if (p) cudaFree(p);
             if (Lv.st) stokes_state_destroy(Lv.st);
             if (Lv.mesh) stokes_mesh_destroy(Lv.mesh);
         }

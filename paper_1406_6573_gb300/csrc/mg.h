@@ -17,7 +17,19 @@
 //    restriction its transpose; the basal slip projector applied around
 //    both, so that corrections stay in the constrained space;
 //  * V(1,1) cycle; on the coarsest level (a few columns) several damped
-//    column-Jacobi sweeps.
+//    column-Jacobi sweeps, the damping capped at 1.6 / lambda_max(C^-1 A)
+//    (power iteration per linearisation): on isotropic high-order coarse
+//    meshes the column blocks miss strong horizontal couplings and the
+//    cycle's damping alone would amplify some error components.
+// On a 2:1 forest (one refinement level, hanging faces and edges) the first
+// coarse level is the unrefined base mesh: the base Q_k functions are exact
+// on the forest (children inherit the parent map and the hanging nodes
+// interpolate the coarse trace), so the prolongation evaluates them at the
+// forest's independent nodes; restriction is its transpose, and the base
+// level's linearisation point and log(beta) are averaging restrictions of
+// the forest's fields.  The forest level adds its column-block solve and the
+// prolongated base-level cycle (additive two-level form); the base mesh then
+// coarsens as above.
 #pragma once
 
 #include <cstdint>
@@ -37,6 +49,8 @@ struct MgLevel {
     size_t band_elems = 0;
     int bw = 0;
     double scale = 0.0;                   // constraint-row scale of this level (0: not chosen yet)
+    double omega = 0.0;                   // smoother damping of this level (0: the cycle's omega)
+    double lmax = 0.0;                    // coarsest level: estimate of the largest eigenvalue of C^-1 A
     int64_t n = 0, nu = 0;                // full state length, velocity length
     int64_t NX = 0, NY = 0, NZ = 0;       // node lattice (NX, NY: columns per direction)
     void *b = nullptr, *x = nullptr, *r = nullptr, *t = nullptr;   // work vectors (pressure parts zero)
@@ -49,7 +63,27 @@ struct MgLevel {
     int32_t* t_cnt = nullptr;
     int64_t t_off[6] = {}, t_coff[6] = {};
     int t_m[6] = {};
+    // a base level under a 2:1 forest: sparse transfers instead of the tables
+    // (rows of P: the forest's nodes; of R = P^T and of the averaging
+    // restriction J = D^-1 P^T: this level's nodes; Jb: J on the basal nodes)
+    bool csr = false;
+    int32_t *P_ptr = nullptr, *P_col = nullptr, *R_ptr = nullptr, *R_col = nullptr;
+    int32_t *J_ptr = nullptr, *J_col = nullptr, *Jb_ptr = nullptr, *Jb_col = nullptr;
+    double *P_w = nullptr, *R_w = nullptr, *J_w = nullptr, *Jb_w = nullptr;
 };
+
+// compressed sparse rows (host)
+struct HostCsr {
+    std::vector<int32_t> ptr, col;
+    std::vector<double> w;
+};
+
+// P: the base mesh hb's nodal values -> the nodes of the 2:1 forest h whose
+// unrefined mesh it is (element map nodes [E][n1^3], refinement mask of the
+// coarse cells, empty for none); checks that P reproduces the forest's node
+// coordinates from the base mesh's.  Host only.
+int forest_prolongation(const HostMesh& h, const std::vector<int32_t>& nodes, const std::vector<uint8_t>& refine,
+                        const HostMesh& hb, HostCsr& P);
 
 struct Multigrid {
     std::vector<MgLevel> L;
@@ -57,11 +91,20 @@ struct Multigrid {
     bool periodic = false;
     double omega = 0.8;                   // damping of the column-Jacobi smoother
     int coarse_sweeps = 12;
+    // a forest level (next level on sparse transfers): additive correction
+    // x = C^-1 b + P V(P^T b) instead of the smoothed cycle.  The forest's
+    // column blocks stand in for the hanging slots by single nodes, so they
+    // are not the exact diagonal blocks, and damped block Jacobi with them
+    // can amplify error components: measured, the smoothed cycle diverged on
+    // a Q2 forest (FGMRES stagnated) and saved 10-15 % of the iterations on
+    // the Q3 forests; the additive form converged on all of them.
+    bool forest_additive = true;
     double* dsc = nullptr;                // device scalar (diagonal sums)
 };
 
-// the mesh can carry the multigrid: conforming lattice mesh of degree 2, 3 or
-// 4, nx and ny even and >= 4
+// the mesh can carry the multigrid: degree 2, 3 or 4, and either a
+// conforming lattice mesh with nx and ny even and >= 4, or a 2:1 forest (its
+// unrefined base mesh is the first coarse level)
 bool mg_eligible(const stokes_mesh* m);
 // levels and work vectors; level 0 uses the given state and column blocks
 int mg_create(Multigrid& mg, const stokes_mesh* fine, stokes_state* st_fine, void* A_fine, int bw_fine,

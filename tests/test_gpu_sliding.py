@@ -147,6 +147,33 @@ def test_sliding_newton_reaches_oracle_solution(name, inner):
         capi.stokes_solver_destroy(s)
 
 
+@pytest.mark.parametrize("name", ["slab_8x8x2_q2p1", "forest_6x6x2_q3p2"])
+@pytest.mark.parametrize("inner", [capi.STOKES_F64, capi.STOKES_F32])
+def test_sliding_newton_multigrid(name, inner):
+    """Nonlinear sliding with the multigrid velocity block: on the Q3 forest,
+    where the column blocks alone stall, the base-level correction carries the
+    horizontal couplings and Newton reaches the oracle's solution."""
+    wl, o, m, lb = setup(name)
+    op = capi.stokes_solver_opts()
+    op.inner_prec = inner
+    op.restart = 30
+    op.max_krylov = 3000
+    op.max_newton = 60
+    op.rtol = 1e-11
+    op.eta_max = 1e-4
+    op.velocity_mg = 1
+    s = capi.stokes_solver_create(m.handle, op)
+    try:
+        up = torch.zeros(o.ndof, dtype=torch.float64, device="cuda")
+        rc, rep = capi.stokes_newton_solve(s, params(wl.phys, dev(lb)), up)
+        assert rc == 0 and rep["converged"] and rep["mg_levels"] >= 2, rep
+        r0 = np.linalg.norm(ostokes.residual(o, wl.phys, np.zeros(o.ndof), lb))
+        r = np.linalg.norm(ostokes.residual(o, wl.phys, up.cpu().numpy(), lb))
+        assert r <= 1e-10 * r0, (r / r0, rep)
+    finally:
+        capi.stokes_solver_destroy(s)
+
+
 def test_sliding_parameters_are_checked():
     wl, o, m, lb = setup("slab_5x3x3_q2p1")
     bad = dataclasses.replace(wl.phys, sliding_eps=0.0)

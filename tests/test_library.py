@@ -2,6 +2,7 @@
 include/stokes.h, rejects bad arguments, and its host mesh builder agrees
 with the oracle's independent construction (node count and coordinates,
 basal node set, element count)."""
+import dataclasses
 import re
 
 import numpy as np
@@ -199,3 +200,21 @@ def test_offset_sub_block_geometry():
     a, b = m.node_coords(), o.node_coords()
     np.testing.assert_allclose(a[:, 0] + wl.x0, b[:, 0], rtol=0, atol=1e-9 * wl.Lx)
     np.testing.assert_allclose(a[:, 2], b[:, 2], rtol=0, atol=1e-9 * np.abs(b[:, 2]).max())
+
+
+@pytest.mark.parametrize("name", ["forest_4x4x2_q2p1", "forest_6x6x2_q3p2", "cforest_3x3x2_q2p1",
+                                  "cforest_4x3x2_q4p3", "forest_4x4x2_q2q0"])
+def test_forest_multigrid_prolongation(name):
+    """The forest multigrid's first coarse level is the unrefined base mesh;
+    its prolongation (base Q_k functions evaluated at the forest's
+    independent nodes) reproduces the forest's node coordinates from the
+    base's (the children inherit the parent map), and has unit row sums."""
+    wl = synth.workload(name)
+    f = Mesh(wl, device=-1)
+    b = Mesh(dataclasses.replace(wl, refine_frac=0.0), device=-1)
+    nnz, err = capi.stokes_debug_forest_prolongation(f.handle, b.handle)
+    assert nnz >= f.Nv and err < 1e-12, (nnz, err)
+    # a base mesh that is not the forest's: refused
+    other = Mesh(dataclasses.replace(wl, refine_frac=0.0, nz=wl.nz + 1), device=-1)
+    with pytest.raises(capi.StokesError):
+        capi.stokes_debug_forest_prolongation(f.handle, other.handle)
