@@ -36,7 +36,9 @@ struct Tab1 {
 };
 
 // out (3 components at every node of the target lattice) = tensor transfer of
-// in: out[X, Y, Z] = sum_a sum_b tx[X][a] ty[Y][b] in[ix, iy, Z]
+// in: out[X, Y, Z] = sum_a sum_b tx[X][a] ty[Y][b] in[ix, iy, Z], accumulated
+// in the input's type (the FP32 cycle's transfers in FP32: FP64 arithmetic
+// made the fine-level transfer of the 128x128x8 slab take 0.1 ms)
 template <typename TI, typename TO>
 __global__ void transfer_kernel(int64_t NXo, int64_t NYo, int64_t NZ, int64_t NXi, int64_t NYi, Tab1 tx, Tab1 ty,
                                 int ncomp, const TI* __restrict__ in, TO* __restrict__ out) {
@@ -44,29 +46,31 @@ __global__ void transfer_kernel(int64_t NXo, int64_t NYo, int64_t NZ, int64_t NX
     if (t >= NXo * NYo * NZ) return;
     const int64_t X = t % NXo, r = t / NXo, Y = r % NYo, Z = r / NYo;
     const int nx = tx.cnt[X], ny = ty.cnt[Y];
-    double s[3] = {0.0, 0.0, 0.0};
+    TI s[3] = {TI(0), TI(0), TI(0)};
     for (int b = 0; b < ny; ++b) {
         const int64_t iy = ty.idx[Y * ty.m + b];
-        const double wy = ty.w[Y * ty.m + b];
+        const TI wy = TI(ty.w[Y * ty.m + b]);
         for (int a = 0; a < nx; ++a) {
             const int64_t gi = tx.idx[X * tx.m + a] + NXi * (iy + NYi * Z);
-            const double wgt = tx.w[X * tx.m + a] * wy;
-            for (int c = 0; c < ncomp; ++c) s[c] += wgt * double(in[ncomp * gi + c]);
+            const TI wgt = TI(tx.w[X * tx.m + a]) * wy;
+            for (int c = 0; c < ncomp; ++c) s[c] += wgt * in[ncomp * gi + c];
         }
     }
     for (int c = 0; c < ncomp; ++c) out[ncomp * t + c] = TO(s[c]);
 }
 
-// out[row * nc + c] = sum_j w[j] in[col[j] * nc + c]  (CSR, nc components)
+// out[row * nc + c] = sum_j w[j] in[col[j] * nc + c]  (CSR, nc components;
+// accumulated in the input's type)
 template <typename TI, typename TO>
 __global__ void csr_kernel(int64_t rows, const int32_t* __restrict__ ptr, const int32_t* __restrict__ col,
                            const double* __restrict__ w, int nc, const TI* __restrict__ in, TO* __restrict__ out) {
     const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (r >= rows) return;
-    double s[3] = {0.0, 0.0, 0.0};
+    TI s[3] = {TI(0), TI(0), TI(0)};
     for (int j = ptr[r]; j < ptr[r + 1]; ++j) {
         const int64_t c = col[j];
-        for (int q = 0; q < nc; ++q) s[q] += w[j] * double(in[nc * c + q]);
+        const TI wj = TI(w[j]);
+        for (int q = 0; q < nc; ++q) s[q] += wj * in[nc * c + q];
     }
     for (int q = 0; q < nc; ++q) out[nc * r + q] = TO(s[q]);
 }
@@ -173,7 +177,7 @@ ColSolveArgs level_cs(const MgLevel& Lv, double scale) {
     ColSolveArgs c{};
     c.ncol = m->h.ncol; c.Nv = m->h.Nv; c.colmax = m->h.colmax; c.bw = Lv.bw;
     c.col_nodes = m->d_col_nodes; c.col_len = m->d_col_len; c.col_basal = m->d_col_basal;
-    c.basal_P = m->d_basal_P; c.scale = scale; c.A = Lv.A;
+    c.basal_P = m->d_basal_P; c.scale = scale; c.A = Lv.A; c.err = m->d_err;
     return c;
 }
 

@@ -11,7 +11,9 @@
 
 #include <cuda_runtime.h>
 
+#include "kernels.h"
 #include "precond.h"
+#include "tma.cuh"
 
 namespace stokes {
 namespace {
@@ -176,6 +178,167 @@ __global__ void col_solve_band_kernel(ColSolveArgs a, const T* __restrict__ rhs,
     }
 }
 
+// Shared-memory variants for one band block (BAND_CB columns, one warp, one
+// thread per column): the whole block (rows x W x BAND_CB values, contiguous
+// in the band layout) is staged by bulk asynchronous copies (TMA,
+// cp.async.bulk) on an mbarrier.  The factorisation then updates shared
+// memory instead of global memory (the global version's dependent
+// read-modify-writes took about 0.4 ms per launch at every size) and writes
+// the block back; the solve has every band entry in shared memory before its
+// sequential sweeps (the global version, latency-bound on its band loads,
+// took about 52 us per launch on the small levels of the multigrid).  The
+// arithmetic is that of col_factor_kernel and col_solve_band_kernel, in the
+// same order.
+constexpr uint32_t STAGE_CHUNK = 32768;
+
+// lane 0 stages nbytes from src into dst; false (status word set, the copies
+// drained) if the copy does not arrive within the poll limit
+__device__ __forceinline__ bool stage_band_block(void* dst, const void* src, uint32_t nbytes, uint64_t* bar,
+                                                 int* err) {
+    using namespace dev;
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        fence_mbar_init();
+        mbar_arrive_expect_tx(bar, nbytes);
+        for (uint32_t o = 0; o < nbytes; o += STAGE_CHUNK) {
+            const uint32_t len = nbytes - o < STAGE_CHUNK ? nbytes - o : STAGE_CHUNK;
+            bulk_g2s(static_cast<unsigned char*>(dst) + o, static_cast<const unsigned char*>(src) + o, len, bar);
+        }
+    }
+    __syncwarp();
+    if (mbar_wait_polls(bar, 0, WAIT_POLLS_DEFAULT)) return true;
+    if (threadIdx.x == 0 && err) atomicOr(err, 1);
+    mbar_wait_bounded(bar, 0);
+    return false;
+}
+
+template <typename T, int BW>
+__global__ void __launch_bounds__(BAND_CB) col_factor_smem_kernel(ColSolveArgs a) {
+    extern __shared__ __align__(128) unsigned char smraw[];
+    constexpr int W = 2 * BW + 1;
+    const int rows = 3 * a.colmax, lane = threadIdx.x;
+    const int64_t nval = int64_t(rows) * W * BAND_CB;
+    T* S = reinterpret_cast<T*>(smraw);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smraw + nval * sizeof(T));
+    T* G = static_cast<T*>(a.A) + int64_t(blockIdx.x) * nval;
+    if (!stage_band_block(S, G, uint32_t(nval * sizeof(T)), bar, a.err)) return;
+    const int64_t c = int64_t(blockIdx.x) * BAND_CB + lane;
+    auto at = [&](int r, int q) -> T& { return S[(r * W + (q - r + BW)) * BAND_CB + lane]; };
+    if (c < a.ncol) {
+        const int n = 3 * a.col_len[c];
+        const int b = a.col_basal[c];
+        if (b >= 0) {
+            const double* p6 = a.basal_P + 6 * int64_t(b);
+            const T P[3][3] = {{T(p6[0]), T(p6[3]), T(p6[4])}, {T(p6[3]), T(p6[1]), T(p6[5])}, {T(p6[4]), T(p6[5]), T(p6[2])}};
+            const int qmax = min(n - 1, 2 + BW);
+            for (int q = 0; q <= qmax; ++q) {          // rows 0..2: P K
+                T v[3];
+                for (int r = 0; r < 3; ++r) v[r] = (q - r <= BW) ? at(r, q) : T(0);
+                for (int r = 0; r < 3; ++r)
+                    if (q - r <= BW) at(r, q) = P[r][0] * v[0] + P[r][1] * v[1] + P[r][2] * v[2];
+            }
+            for (int r = 0; r <= qmax; ++r) {          // columns 0..2: K P
+                T v[3];
+                for (int q = 0; q < 3; ++q) v[q] = (r - q <= BW) ? at(r, q) : T(0);
+                for (int q = 0; q < 3; ++q)
+                    if (r - q <= BW) at(r, q) = v[0] * P[0][q] + v[1] * P[1][q] + v[2] * P[2][q];
+            }
+            const T sc = T(a.scale);
+            for (int r = 0; r < 3; ++r)
+                for (int q = 0; q < 3; ++q) at(r, q) += sc * ((r == q ? T(1) : T(0)) - P[r][q]);
+        }
+        for (int p = 0; p < n; ++p) {
+            const T ipiv = T(1) / at(p, p);
+            T prow[BW];                                 // U[p][p + 1 .. p + BW]
+            #pragma unroll
+            for (int d = 1; d <= BW; ++d) prow[d - 1] = p + d < n ? at(p, p + d) : T(0);
+            #pragma unroll
+            for (int dr = 1; dr <= BW; ++dr) {
+                const int r = p + dr;
+                if (r >= n) break;
+                T& lrp = at(r, p);
+                const T l = lrp * ipiv;
+                lrp = l;
+                if (l != T(0)) {
+                    #pragma unroll
+                    for (int dq = 1; dq <= BW; ++dq)
+                        if (p + dq < n) at(r, p + dq) -= l * prow[dq - 1];
+                }
+            }
+        }
+    }
+    __syncwarp();
+    const int64_t n16 = nval * int64_t(sizeof(T)) / 16;
+    const uint4* s16 = reinterpret_cast<const uint4*>(S);
+    uint4* g16 = reinterpret_cast<uint4*>(G);
+    for (int64_t i = lane; i < n16; i += BAND_CB) g16[i] = s16[i];
+}
+
+template <typename T, int BW>
+__global__ void __launch_bounds__(BAND_CB) col_solve_smem_kernel(ColSolveArgs a, const T* __restrict__ rhs,
+                                                                 T* __restrict__ z) {
+    extern __shared__ __align__(128) unsigned char smraw[];
+    constexpr int W = 2 * BW + 1;
+    const int rows = 3 * a.colmax, lane = threadIdx.x;
+    const int64_t nval = int64_t(rows) * W * BAND_CB;
+    T* S = reinterpret_cast<T*>(smraw);
+    T* zc = S + nval;                                   // [rows][BAND_CB]
+    uint64_t* bar = reinterpret_cast<uint64_t*>(zc + int64_t(rows) * BAND_CB);
+    const T* G = static_cast<const T*>(a.A) + int64_t(blockIdx.x) * nval;
+    const int64_t c = int64_t(blockIdx.x) * BAND_CB + lane;
+    const int64_t ncol = a.ncol;
+    // the band copy is issued first; the right-hand side is gathered while it lands
+    {
+        using namespace dev;
+        if (lane == 0) {
+            mbar_init(bar, 1);
+            fence_mbar_init();
+            const uint32_t nbytes = uint32_t(nval * sizeof(T));
+            mbar_arrive_expect_tx(bar, nbytes);
+            for (uint32_t o = 0; o < nbytes; o += STAGE_CHUNK) {
+                const uint32_t len = nbytes - o < STAGE_CHUNK ? nbytes - o : STAGE_CHUNK;
+                bulk_g2s(reinterpret_cast<unsigned char*>(S) + o, reinterpret_cast<const unsigned char*>(G) + o, len,
+                         bar);
+            }
+        }
+    }
+    const int len = c < ncol ? a.col_len[c] : 0, n = 3 * len;
+    #pragma unroll 4
+    for (int p = 0; p < len; ++p) {
+        const int64_t g = a.col_nodes[int64_t(p) * ncol + c];
+        #pragma unroll
+        for (int k = 0; k < 3; ++k) zc[(3 * p + k) * BAND_CB + lane] = rhs[3 * g + k];
+    }
+    __syncwarp();
+    if (!dev::mbar_wait_polls(bar, 0, WAIT_POLLS_DEFAULT)) {
+        if (lane == 0 && a.err) atomicOr(a.err, 1);
+        dev::mbar_wait_bounded(bar, 0);
+        return;
+    }
+    auto A = [&](int r, int slot) { return S[(r * W + slot) * BAND_CB + lane]; };
+    // L y = r (unit lower): L[r][r - d] at band slot BW - d
+    for (int r = 1; r < n; ++r) {
+        T s = zc[r * BAND_CB + lane];
+        #pragma unroll
+        for (int d = 1; d <= BW; ++d)
+            if (r - d >= 0) s -= A(r, BW - d) * zc[(r - d) * BAND_CB + lane];
+        zc[r * BAND_CB + lane] = s;
+    }
+    // U x = y: U[r][r] at slot BW, U[r][r + d] at slot BW + d
+    for (int r = n - 1; r >= 0; --r) {
+        T s = zc[r * BAND_CB + lane];
+        #pragma unroll
+        for (int d = 1; d <= BW; ++d)
+            if (r + d < n) s -= A(r, BW + d) * zc[(r + d) * BAND_CB + lane];
+        zc[r * BAND_CB + lane] = s / A(r, BW);
+    }
+    for (int p = 0; p < len; ++p) {
+        const int64_t g = a.col_nodes[int64_t(p) * ncol + c];
+        #pragma unroll
+        for (int k = 0; k < 3; ++k) z[3 * g + k] = zc[(3 * p + k) * BAND_CB + lane];
+    }
+}
+
 // z_p(e) = -minv(e) r_p(e): one thread per pressure dof (e, b); with full
 // blocks minv holds npr x npr per element, otherwise one inverse diagonal
 // entry per dof
@@ -260,12 +423,108 @@ int solve_threads(int colmax, int bytes) {
 
 }  // namespace
 
+namespace {
+
+// largest dynamic shared memory a block may opt in to on the current device
+int smem_optin() {
+    static int cached_dev = -1, val = 0;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (dev != cached_dev) {
+        if (cudaDeviceGetAttribute(&val, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) val = 0;
+        cached_dev = dev;
+    }
+    return val;
+}
+
+// raise a kernel's dynamic shared-memory limit to the opt-in maximum (once per device)
+template <typename K>
+cudaError_t allow_smem(K kernel) {
+    static int done_dev = -1;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev == done_dev) return e;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin());
+    if (e == cudaSuccess) done_dev = dev;
+    return e;
+}
+
+template <typename T>
+size_t band_block_bytes(const ColSolveArgs& a) {
+    return size_t(3) * a.colmax * size_t(2 * a.bw + 1) * BAND_CB * sizeof(T);
+}
+
+// the shared-memory solve runs where the levels are latency-bound (few band
+// blocks); above this many columns the register-ring kernel streams the band
+// at a higher rate (one 32-thread block per SM at these block sizes)
+constexpr int64_t SMEM_SOLVE_MAX_COLS = 32768;
+
+template <typename T, int BW>
+cudaError_t factor_smem(const ColSolveArgs& a, size_t bytes, cudaStream_t s) {
+    cudaError_t e = allow_smem(col_factor_smem_kernel<T, BW>);
+    if (e != cudaSuccess) return e;
+    col_factor_smem_kernel<T, BW><<<unsigned(band_cols(a.ncol) / BAND_CB), BAND_CB, bytes, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename T, int BW>
+cudaError_t solve_smem(const ColSolveArgs& a, size_t bytes, const void* r, void* z, cudaStream_t s) {
+    cudaError_t e = allow_smem(col_solve_smem_kernel<T, BW>);
+    if (e != cudaSuccess) return e;
+    col_solve_smem_kernel<T, BW><<<unsigned(band_cols(a.ncol) / BAND_CB), BAND_CB, bytes, s>>>(
+        a, static_cast<const T*>(r), static_cast<T*>(z));
+    return cudaGetLastError();
+}
+
+// a shared-memory launch that the device refuses (its limit, less a margin
+// for the block's reserved shared memory, is checked first) falls back to the
+// global-memory kernels
+constexpr size_t SMEM_MARGIN = 1024;
+
+template <typename T>
+int col_factor_t(const ColSolveArgs& a, cudaStream_t s) {
+    const size_t bytes = band_block_bytes<T>(a) + 16;
+    if (bytes + SMEM_MARGIN <= size_t(smem_optin())) {
+        cudaError_t e = cudaErrorInvalidValue;
+        switch (a.bw) {
+            case 8: e = factor_smem<T, 8>(a, bytes, s); break;
+            case 11: e = factor_smem<T, 11>(a, bytes, s); break;
+            case 14: e = factor_smem<T, 14>(a, bytes, s); break;
+            default: break;
+        }
+        if (e == cudaSuccess) return 0;
+        (void)cudaGetLastError();
+    }
+    const unsigned blocks = unsigned((a.ncol + 127) / 128);
+    col_factor_kernel<T><<<blocks, 128, 0, s>>>(a);
+    return int(cudaGetLastError());
+}
+
+template <typename T>
+int col_solve_smem_t(const ColSolveArgs& a, const void* r, void* z, cudaStream_t s, bool& done) {
+    done = false;
+    const size_t bytes = band_block_bytes<T>(a) + size_t(3) * a.colmax * BAND_CB * sizeof(T) + 16;
+    if (a.ncol > SMEM_SOLVE_MAX_COLS || bytes + SMEM_MARGIN > size_t(smem_optin())) return 0;
+    cudaError_t e = cudaSuccess;
+    switch (a.bw) {
+        case 8: e = solve_smem<T, 8>(a, bytes, r, z, s); break;
+        case 11: e = solve_smem<T, 11>(a, bytes, r, z, s); break;
+        case 14: e = solve_smem<T, 14>(a, bytes, r, z, s); break;
+        default: return 0;
+    }
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return 0;
+    }
+    done = true;
+    return 0;
+}
+
+}  // namespace
+
 int launch_col_factor(int prec, const ColSolveArgs& a, cudaStream_t s) {
     if (a.ncol == 0) return 0;
-    const unsigned blocks = unsigned((a.ncol + 127) / 128);
-    if (prec == 1) col_factor_kernel<float><<<blocks, 128, 0, s>>>(a);
-    else col_factor_kernel<double><<<blocks, 128, 0, s>>>(a);
-    return int(cudaGetLastError());
+    return prec == 1 ? col_factor_t<float>(a, s) : col_factor_t<double>(a, s);
 }
 
 int launch_col_diag_sum(int prec, const ColSolveArgs& a, double* out, cudaStream_t s) {
@@ -280,6 +539,11 @@ int launch_col_diag_sum(int prec, const ColSolveArgs& a, double* out, cudaStream
 
 int launch_col_solve(int prec, const ColSolveArgs& a, const void* r, void* z, cudaStream_t s) {
     if (a.ncol == 0) return 0;
+    {
+        bool done = false;
+        const int rc = prec == 1 ? col_solve_smem_t<float>(a, r, z, s, done) : col_solve_smem_t<double>(a, r, z, s, done);
+        if (done || rc) return rc;
+    }
     const int bytes = prec == 1 ? 4 : 8;
     const int nt = solve_threads(a.colmax, bytes);
     const size_t sm = size_t(3) * a.colmax * nt * bytes;

@@ -61,6 +61,7 @@ struct ColSolveArgs {
     const double* basal_P;     // [Nb][6]
     double scale;              // constraint-row scale s of P F P + s (I - P)
     void* A;                   // banded matrices (factored in place)
+    int* err;                  // status word for bounded waits that expired (may be NULL)
 };
 
 // constraints (P F P + I - P on the basal node block) + banded LU per column

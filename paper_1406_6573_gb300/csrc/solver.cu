@@ -122,7 +122,7 @@ ColSolveArgs colsolve_args(stokes_solver* S, double scale) {
     ColSolveArgs c{};
     c.ncol = m->h.ncol; c.Nv = m->h.Nv; c.colmax = m->h.colmax; c.bw = S->bw;
     c.col_nodes = m->d_col_nodes; c.col_len = m->d_col_len; c.col_basal = m->d_col_basal;
-    c.basal_P = m->d_basal_P; c.scale = scale; c.A = S->A;
+    c.basal_P = m->d_basal_P; c.scale = scale; c.A = S->A; c.err = m->d_err;
     return c;
 }
 

@@ -73,15 +73,16 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Wait for the phase with the given parity to complete, giving up after a
-// bounded number of polls (each poll may suspend the thread for a
-// hardware-chosen interval).  The result is made uniform across the warp.
 // hint: bring the line holding p into L1 (no register written, no wait)
 __device__ __forceinline__ void prefetch_l1(const void* p) {
     asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
 }
 
 constexpr uint32_t MBAR_POLL_LIMIT = WAIT_POLLS_DEFAULT;
+
+// Wait for the phase with the given parity to complete, giving up after a
+// bounded number of polls (each poll may suspend the thread for a
+// hardware-chosen interval).  The result is made uniform across the warp.
 
 __device__ __forceinline__ bool mbar_wait_polls(uint64_t* bar, uint32_t parity, uint32_t limit) {
     bool ok = false;
