@@ -652,3 +652,51 @@ int stokes_state_apply_pressure_block(const stokes_state* state, const void* x, 
 }
 
 }  // extern "C"
+
+namespace stokes {
+// Both states of the mixed-precision solver (FP32 inner, FP64 outer) at one
+// linearisation point: one FP64 pass of the element kernel writes both
+// (k <= 4), the basal states one launch each; otherwise two linearisations.
+int linearize_pair(stokes_state* s32, stokes_state* s64, const stokes_params* params, const double* up_lin,
+                   void* stream) {
+    if (!s32 || !s64 || s32->mesh != s64->mesh || s32->prec != STOKES_F32 || s64->prec != STOKES_F64 ||
+        s32->mesh->h.k > 4) {
+        int rc = stokes_linearize(s32, params, up_lin, stream);
+        if (rc) return rc;
+        return s64 && s64 != s32 ? stokes_linearize(s64, params, up_lin, stream) : STOKES_OK;
+    }
+    const stokes_mesh* mesh = s32->mesh;
+    int rc = check_common(mesh, STOKES_F32);
+    if (rc) return rc;
+    if ((rc = check_params(mesh, params))) return rc;
+    if (!up_lin) return fail(STOKES_E_INVAL, "up_lin is NULL");
+    DeviceGuard g(mesh->device);
+    if (g.err != cudaSuccess) return cuda_fail(g.err, "selecting the device");
+    ElemArgs a = elem_args(mesh, params);
+    a.ud = up_lin;
+    a.state = s32->d_state;
+    a.state_cpl = s32->cpl;
+    a.state2 = static_cast<double*>(s64->d_state);
+    a.state2_cpl = s64->cpl;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int e = timed(mesh, PROF_ELEMENT, s, [&] {
+        return launch_elem(mesh->h.k, MODE_LINEARIZE, STOKES_F64, STOKES_F32, false, a, s);
+    });
+    if (e) return cuda_fail(cudaError_t(e), "linearize kernel launch");
+    for (stokes_state* st : {s32, s64}) {
+        st->slide = sliding_nonlinear(params) && mesh->h.nF > 0;
+        st->face_lin = params->robin && mesh->h.nF > 0;
+        if (st->face_lin) {
+            FaceArgs f = face_args(mesh, params);
+            f.u = up_lin;
+            f.fstate_out = st->d_fstate;
+            f.fstate_f32 = st->prec == STOKES_F32;
+            e = timed(mesh, PROF_FACE, s, [&] { return launch_face(mesh->h.k, FACE_LINEARIZE, STOKES_F64, f, s); });
+            if (e) return cuda_fail(cudaError_t(e), "basal linearisation kernel launch");
+        }
+        st->params = *params;
+        st->linearized = true;
+    }
+    return STOKES_OK;
+}
+}  // namespace stokes

@@ -219,6 +219,25 @@ __global__ void __launch_bounds__(32 * GW<T>) elem_kernel(ElemArgs a) {
                 F[8 * fs] = S(sq * E01);
                 F[9 * fs] = S(sq * E02);
                 F[10 * fs] = S(sq * E12);
+                if (a.state2) {
+                    // the FP64 state of the same linearisation point
+                    double* st2 = a.state2;
+                    const StateRef sr2(e, a.state2_cpl);
+                    double* F2 = st2 + sr2.f(0, lq, i + N1 * j);
+                    const int fs2 = sr2.fstride;
+                    if (qp == 0) { st2[sr2.c(0)] = double(Ji[0]); st2[sr2.c(1)] = double(Ji[4]); }
+                    F2[0] = double(Ji[6]);
+                    F2[fs2] = double(Ji[7]);
+                    F2[2 * fs2] = double(Ji[8]);
+                    F2[3 * fs2] = double(wdj);
+                    F2[4 * fs2] = double(mu * wdj);
+                    F2[5 * fs2] = double(sq * E00);
+                    F2[6 * fs2] = double(sq * E11);
+                    F2[7 * fs2] = double(sq * E22);
+                    F2[8 * fs2] = double(sq * E01);
+                    F2[9 * fs2] = double(sq * E02);
+                    F2[10 * fs2] = double(sq * E12);
+                }
             }
         }
     } else if constexpr (MODE == MODE_GRAD_A || MODE == MODE_GRAD_A_PARTIAL) {

@@ -33,6 +33,10 @@ struct Profiler {
 int fail(int code, const std::string& msg);
 // cudaMalloc through the allocation-failure test hook (stokes_debug_fail_alloc_after)
 cudaError_t dev_alloc(void** p, size_t bytes);
+// stokes_linearize of an FP32 and an FP64 state of one mesh at one point
+// (one element pass writes both where the kernels allow)
+int linearize_pair(stokes_state* s32, stokes_state* s64, const stokes_params* params, const double* up_lin,
+                   void* stream);
 int cuda_fail(cudaError_t e, const char* where);
 
 // Make `dev` current for the duration of a call, restoring the caller's device.

@@ -97,6 +97,8 @@ struct ElemArgs {
     void* state;               // [E][state stride] (linearize output)
     const void* cstate;        // same (state apply input)
     int state_cpl;             // state in the group layout (k = 2, FP32, conforming mesh)
+    double* state2;            // linearize, k <= 4: a second (FP64) state written by the same
+    int state2_cpl;            // pass (NULL: none), and its layout flag
     double C, gamma, delta, pexp;
     int n_is_3;
     int picard;                // linearisation: 0 Newton (Eq. 2.7), 1 Picard (viscosity frozen)

@@ -261,8 +261,9 @@ __global__ void hash_fill_kernel(int64_t n, T* v) {
 
 // x = omega C^-1 b  (first smoothing step from x = 0)
 int smooth_first(Multigrid& mg, MgLevel& Lv, cudaStream_t s) {
-    MG_CU(launch_col_solve(mg.prec, level_cs(Lv, Lv.scale), Lv.b, Lv.t, s), "column solve");
-    MG_CU(vec_axpby(Lv.nu, level_omega(mg, Lv), nullptr, mg.prec, Lv.t, 0.0, mg.prec, Lv.x, s), "smoothing");
+    ColSolveArgs cs = level_cs(Lv, Lv.scale);
+    cs.out_alpha = level_omega(mg, Lv);
+    MG_CU(launch_col_solve(mg.prec, cs, Lv.b, Lv.x, s), "column solve");
     return STOKES_OK;
 }
 
@@ -276,8 +277,10 @@ int residual(Multigrid& mg, MgLevel& Lv, cudaStream_t s) {
 // x += omega C^-1 (b - A x)
 int smooth(Multigrid& mg, MgLevel& Lv, cudaStream_t s) {
     MG_CK(residual(mg, Lv, s));
-    MG_CU(launch_col_solve(mg.prec, level_cs(Lv, Lv.scale), Lv.r, Lv.t, s), "column solve");
-    MG_CU(vec_axpby(Lv.nu, level_omega(mg, Lv), nullptr, mg.prec, Lv.t, 1.0, mg.prec, Lv.x, s), "smoothing");
+    ColSolveArgs cs = level_cs(Lv, Lv.scale);
+    cs.out_alpha = level_omega(mg, Lv);
+    cs.out_beta = 1.0;
+    MG_CU(launch_col_solve(mg.prec, cs, Lv.r, Lv.x, s), "column solve");
     return STOKES_OK;
 }
 

@@ -16,7 +16,7 @@
 //    nodes in x and y (tensor products of 1-D tables), identity in z;
 //    restriction its transpose; the basal slip projector applied around
 //    both, so that corrections stay in the constrained space;
-//  * V(1,1) cycle; on the coarsest level (a few columns) several damped
+//  * V(1,1) cycle; on the coarsest level (a few columns) four damped
 //    column-Jacobi sweeps, the damping capped at 1.6 / lambda_max(C^-1 A)
 //    (power iteration per linearisation): on isotropic high-order coarse
 //    meshes the column blocks miss strong horizontal couplings and the
@@ -90,7 +90,13 @@ struct Multigrid {
     int prec = 1;
     bool periodic = false;
     double omega = 0.8;                   // damping of the column-Jacobi smoother
-    int coarse_sweeps = 12;
+// sweeps on the coarsest level: the Krylov counts did not change between 12
+// and 4 (128x128x8 Q2, 64x64x4 Q3 and Q4 slabs, Q3 forest), and 4 saved 8-12 %
+// of the solve time (2 sweeps: the forest needed 10 % more iterations)
+#ifndef STOKES_MG_COARSE_SWEEPS
+#define STOKES_MG_COARSE_SWEEPS 4
+#endif
+    int coarse_sweeps = STOKES_MG_COARSE_SWEEPS;
     // a forest level (next level on sparse transfers): additive correction
     // x = C^-1 b + P V(P^T b) instead of the smoothed cycle.  The forest's
     // column blocks stand in for the hanging slots by single nodes, so they

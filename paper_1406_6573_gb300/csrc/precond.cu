@@ -64,6 +64,7 @@ __global__ void col_factor_kernel(ColSolveArgs a) {
             if (l != T(0))
                 for (int q = p + 1; q <= rmax; ++q) band(A, 3 * a.colmax, W, bw, r, q, c) -= l * band(A, 3 * a.colmax, W, bw, p, q, c);
         }
+        band(A, 3 * a.colmax, W, bw, p, p, c) = ipiv;   // the solves multiply by 1 / U[p][p]
     }
 }
 
@@ -90,11 +91,15 @@ __global__ void col_solve_kernel(ColSolveArgs a, const T* __restrict__ rhs, T* _
         T s = zc[r * nt + t];
         const int qmax = min(n - 1, r + bw);
         for (int q = r + 1; q <= qmax; ++q) s -= A[band_at(c, r, q - r + bw, W, 3 * a.colmax)] * zc[q * nt + t];
-        zc[r * nt + t] = s / A[band_at(c, r, bw, W, 3 * a.colmax)];
+        zc[r * nt + t] = s * A[band_at(c, r, bw, W, 3 * a.colmax)];
     }
+    const T oa = T(a.out_alpha), ob = T(a.out_beta);
     for (int p = 0; p < len; ++p) {
         const int64_t g = a.col_nodes[int64_t(p) * a.ncol + c];
-        for (int k = 0; k < 3; ++k) z[3 * g + k] = zc[(3 * p + k) * nt + t];
+        for (int k = 0; k < 3; ++k) {
+            const T v = oa * zc[(3 * p + k) * nt + t];
+            z[3 * g + k] = ob != T(0) ? ob * z[3 * g + k] + v : v;
+        }
     }
 }
 
@@ -149,7 +154,7 @@ __global__ void col_solve_band_kernel(ColSolveArgs a, const T* __restrict__ rhs,
             }
         }
     }
-    // U x = y: row r holds U[r][r] at slot BW and U[r][r + d] at slot BW + d;
+    // U x = y: row r holds 1 / U[r][r] at slot BW and U[r][r + d] at slot BW + d;
     // row n - 1 - i lives in ring slot i mod R
     T U[R][BW + 1];
     auto loadU = [&](int r, T (&dst)[BW + 1]) {
@@ -168,13 +173,17 @@ __global__ void col_solve_band_kernel(ColSolveArgs a, const T* __restrict__ rhs,
                 #pragma unroll
                 for (int d = 1; d <= BW; ++d)
                     if (r + d < n) s -= U[u][d] * zc[(r + d) * nt + t];
-                zc[r * nt + t] = s / U[u][0];
+                zc[r * nt + t] = s * U[u][0];
             }
         }
     }
+    const T oa = T(a.out_alpha), ob = T(a.out_beta);
     for (int p = 0; p < len; ++p) {
         const int64_t g = a.col_nodes[int64_t(p) * ncol + c];
-        for (int k = 0; k < 3; ++k) z[3 * g + k] = zc[(3 * p + k) * nt + t];
+        for (int k = 0; k < 3; ++k) {
+            const T v = oa * zc[(3 * p + k) * nt + t];
+            z[3 * g + k] = ob != T(0) ? ob * z[3 * g + k] + v : v;
+        }
     }
 }
 
@@ -187,8 +196,8 @@ __global__ void col_solve_band_kernel(ColSolveArgs a, const T* __restrict__ rhs,
 // the block back; the solve has every band entry in shared memory before its
 // sequential sweeps (the global version, latency-bound on its band loads,
 // took about 52 us per launch on the small levels of the multigrid).  The
-// arithmetic is that of col_factor_kernel and col_solve_band_kernel, in the
-// same order.
+// factorisation's arithmetic is that of col_factor_kernel, in the same order;
+// the solve sums each row's band terms from the farthest to the nearest row.
 constexpr uint32_t STAGE_CHUNK = 32768;
 
 // lane 0 stages nbytes from src into dst; false (status word set, the copies
@@ -265,6 +274,7 @@ __global__ void __launch_bounds__(BAND_CB) col_factor_smem_kernel(ColSolveArgs a
                         if (p + dq < n) at(r, p + dq) -= l * prow[dq - 1];
                 }
             }
+            at(p, p) = ipiv;                            // the solves multiply by 1 / U[p][p]
         }
     }
     __syncwarp();
@@ -303,9 +313,13 @@ __global__ void __launch_bounds__(BAND_CB) col_solve_smem_kernel(ColSolveArgs a,
         }
     }
     const int len = c < ncol ? a.col_len[c] : 0, n = 3 * len;
+    // node indices, then the right-hand side: two rounds of independent loads
+    int32_t* gidx = reinterpret_cast<int32_t*>(bar + 2);   // [colmax][BAND_CB]
+    #pragma unroll 8
+    for (int p = 0; p < len; ++p) gidx[p * BAND_CB + lane] = a.col_nodes[int64_t(p) * ncol + c];
     #pragma unroll 4
     for (int p = 0; p < len; ++p) {
-        const int64_t g = a.col_nodes[int64_t(p) * ncol + c];
+        const int64_t g = gidx[p * BAND_CB + lane];
         #pragma unroll
         for (int k = 0; k < 3; ++k) zc[(3 * p + k) * BAND_CB + lane] = rhs[3 * g + k];
     }
@@ -316,26 +330,51 @@ __global__ void __launch_bounds__(BAND_CB) col_solve_smem_kernel(ColSolveArgs a,
         return;
     }
     auto A = [&](int r, int slot) { return S[(r * W + slot) * BAND_CB + lane]; };
+    // the last BW + 1 solution values in a register ring (slot: row mod RING);
+    // the term of the previous row is subtracted last, so that one FMA per row
+    // waits on it
+    constexpr int RING = BW + 1;
+    T zr[RING];
     // L y = r (unit lower): L[r][r - d] at band slot BW - d
-    for (int r = 1; r < n; ++r) {
-        T s = zc[r * BAND_CB + lane];
+    for (int r0 = 0; r0 < n; r0 += RING) {
         #pragma unroll
-        for (int d = 1; d <= BW; ++d)
-            if (r - d >= 0) s -= A(r, BW - d) * zc[(r - d) * BAND_CB + lane];
-        zc[r * BAND_CB + lane] = s;
+        for (int u = 0; u < RING; ++u) {
+            const int r = r0 + u;
+            if (r < n) {
+                T s = zc[r * BAND_CB + lane];
+                #pragma unroll
+                for (int d = BW; d >= 1; --d)
+                    if (r - d >= 0) s -= A(r, BW - d) * zr[(u - d + RING) % RING];
+                zr[u] = s;
+                zc[r * BAND_CB + lane] = s;
+            }
+        }
     }
-    // U x = y: U[r][r] at slot BW, U[r][r + d] at slot BW + d
-    for (int r = n - 1; r >= 0; --r) {
-        T s = zc[r * BAND_CB + lane];
+    // U x = y: 1 / U[r][r] at slot BW, U[r][r + d] at slot BW + d (ring slot:
+    // (n - 1 - r) mod RING)
+    for (int i0 = 0; i0 < n; i0 += RING) {
         #pragma unroll
-        for (int d = 1; d <= BW; ++d)
-            if (r + d < n) s -= A(r, BW + d) * zc[(r + d) * BAND_CB + lane];
-        zc[r * BAND_CB + lane] = s / A(r, BW);
+        for (int u = 0; u < RING; ++u) {
+            const int r = n - 1 - (i0 + u);
+            if (r >= 0) {
+                T s = zc[r * BAND_CB + lane];
+                #pragma unroll
+                for (int d = BW; d >= 1; --d)
+                    if (r + d < n) s -= A(r, BW + d) * zr[(u - d + RING) % RING];
+                s *= A(r, BW);
+                zr[u] = s;
+                zc[r * BAND_CB + lane] = s;
+            }
+        }
     }
+    const T oa = T(a.out_alpha), ob = T(a.out_beta);
     for (int p = 0; p < len; ++p) {
-        const int64_t g = a.col_nodes[int64_t(p) * ncol + c];
+        const int64_t g = gidx[p * BAND_CB + lane];
         #pragma unroll
-        for (int k = 0; k < 3; ++k) z[3 * g + k] = zc[(3 * p + k) * BAND_CB + lane];
+        for (int k = 0; k < 3; ++k) {
+            const T v = oa * zc[(3 * p + k) * BAND_CB + lane];
+            z[3 * g + k] = ob != T(0) ? ob * z[3 * g + k] + v : v;
+        }
     }
 }
 
@@ -454,10 +493,20 @@ size_t band_block_bytes(const ColSolveArgs& a) {
     return size_t(3) * a.colmax * size_t(2 * a.bw + 1) * BAND_CB * sizeof(T);
 }
 
-// the shared-memory solve runs where the levels are latency-bound (few band
-// blocks); above this many columns the register-ring kernel streams the band
-// at a higher rate (one 32-thread block per SM at these block sizes)
-constexpr int64_t SMEM_SOLVE_MAX_COLS = 32768;
+// the shared-memory solve runs where the levels are latency-bound (at most one
+// wave of band blocks, one 32-thread block per SM at these block sizes);
+// above that the register-ring kernel streams the band at a higher rate
+// (16384 columns of the Q2 slab: 78 us in 3.4 waves against 55 us)
+int64_t smem_solve_max_cols() {
+    static int cached_dev = -1, sms = 0;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (dev != cached_dev) {
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) sms = 0;
+        cached_dev = dev;
+    }
+    return int64_t(sms) * BAND_CB;
+}
 
 template <typename T, int BW>
 cudaError_t factor_smem(const ColSolveArgs& a, size_t bytes, cudaStream_t s) {
@@ -503,8 +552,9 @@ int col_factor_t(const ColSolveArgs& a, cudaStream_t s) {
 template <typename T>
 int col_solve_smem_t(const ColSolveArgs& a, const void* r, void* z, cudaStream_t s, bool& done) {
     done = false;
-    const size_t bytes = band_block_bytes<T>(a) + size_t(3) * a.colmax * BAND_CB * sizeof(T) + 16;
-    if (a.ncol > SMEM_SOLVE_MAX_COLS || bytes + SMEM_MARGIN > size_t(smem_optin())) return 0;
+    const size_t bytes = band_block_bytes<T>(a) + size_t(3) * a.colmax * BAND_CB * sizeof(T) + 16 +
+                         size_t(a.colmax) * BAND_CB * 4;
+    if (a.ncol > smem_solve_max_cols() || bytes + SMEM_MARGIN > size_t(smem_optin())) return 0;
     cudaError_t e = cudaSuccess;
     switch (a.bw) {
         case 8: e = solve_smem<T, 8>(a, bytes, r, z, s); break;

@@ -62,13 +62,16 @@ struct ColSolveArgs {
     double scale;              // constraint-row scale s of P F P + s (I - P)
     void* A;                   // banded matrices (factored in place)
     int* err;                  // status word for bounded waits that expired (may be NULL)
+    double out_alpha = 1.0;    // the solve stores z = out_beta z + out_alpha C^-1 r
+    double out_beta = 0.0;     // (velocity part; out_beta 0 does not read z)
 };
 
 // constraints (P F P + I - P on the basal node block) + banded LU per column
 int launch_col_factor(int prec, const ColSolveArgs& a, cudaStream_t s);
 // out[0] = sum over all columns of |diag| of the assembled blocks
 int launch_col_diag_sum(int prec, const ColSolveArgs& a, double* out, cudaStream_t s);
-// z_u = F~^{-1} r_u on the velocity part (z, r: state vectors of type prec)
+// z_u = out_beta z_u + out_alpha F~^{-1} r_u on the velocity part (z, r: state
+// vectors of type prec; z_u = F~^{-1} r_u with the defaults)
 int launch_col_solve(int prec, const ColSolveArgs& a, const void* r, void* z, cudaStream_t s);
 // full: minv[e] = inverse of the element block mblk[e] (npr x npr, SPD);
 // otherwise minv[e npr + b] = 1 / mblk[e][b][b] (inverse diagonal); in prec

@@ -411,8 +411,8 @@ int stokes_newton_solve(stokes_solver* S, const stokes_params* params, double* u
             eta = std::min(e2, S->o.eta_max);
             eta = std::max(eta, 0.5 * S->o.rtol * nr0 / nr);
         }
-        CK(stokes_linearize(S->st_in, params, up, st));
-        if (S->st64 != S->st_in) CK(stokes_linearize(S->st64, params, up, st));
+        if (S->st64 != S->st_in) CK(linearize_pair(S->st_in, S->st64, params, up, st));
+        else CK(stokes_linearize(S->st_in, params, up, st));
         CK(precond_setup(S, params, up, st));
         // rhs = -r
         TU(PROF_VECTOR, vec_axpby(n, -1.0, nullptr, STOKES_F64, S->r, 0.0, STOKES_F64, S->trial, st), "rhs");
@@ -473,8 +473,8 @@ int stokes_linear_solve(stokes_solver* S, const stokes_params* params, const dou
     const int64_t n = S->n;
     stokes_solve_report R{};
     auto t0 = std::chrono::steady_clock::now();
-    CK(stokes_linearize(S->st_in, params, up_lin, st));
-    if (S->st64 != S->st_in) CK(stokes_linearize(S->st64, params, up_lin, st));
+    if (S->st64 != S->st_in) CK(linearize_pair(S->st_in, S->st64, params, up_lin, st));
+    else CK(stokes_linearize(S->st_in, params, up_lin, st));
     CK(precond_setup(S, params, up_lin, st));
     double nb = 0;
     CK(norm64(S, b, n, nb, st));
