@@ -695,7 +695,10 @@ int mg_setup(Multigrid& mg, const stokes_params* p, const double* up_fine, doubl
         }
         C.st->params.constraint_scale = C.scale;
         MG_CU(launch_col_factor(mg.prec, level_cs(C, C.scale), s), "coarse column factorisation");
-        if (l + 1 == mg.L.size()) {
+#ifndef STOKES_MG_COARSE_DAMP
+#define STOKES_MG_COARSE_DAMP 1
+#endif
+        if (STOKES_MG_COARSE_DAMP && l + 1 == mg.L.size()) {
             // coarsest level: damping of its sweeps from the spectrum of C^-1 A
             double lm = 0;
             MG_CK(estimate_lmax(mg, C, 10, lm, s));
