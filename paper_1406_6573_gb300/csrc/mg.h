@@ -5,7 +5,8 @@
 // coarse spaces coarsen only horizontally.  Here the same idea is built
 // geometrically on conforming slab meshes of degree 2, 3, 4:
 //  * levels: the mesh semi-coarsened by 2 in x and y (columns and the vertical
-//    node lattice kept), each level a mesh of its own (the fine isoparametric
+//    node lattice kept) down to 4 cells per direction (2 for the first
+//    coarse level of a small mesh), each level a mesh of its own (the fine isoparametric
 //    heights at the coarse GLL points), with its own stored FP32 (or FP64)
 //    state linearised at the fine velocity interpolated to its nodes (the
 //    coarse operator is the rediscretised Newton Jacobian) and log(beta)
