@@ -42,19 +42,18 @@ struct Tab1 {
 template <typename TI, typename TO>
 __global__ void transfer_kernel(int64_t NXo, int64_t NYo, int64_t NZ, int64_t NXi, int64_t NYi, Tab1 tx, Tab1 ty,
                                 int ncomp, const TI* __restrict__ in, TO* __restrict__ out) {
-    using A = TI;
     const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (t >= NXo * NYo * NZ) return;
     const int64_t X = t % NXo, r = t / NXo, Y = r % NYo, Z = r / NYo;
     const int nx = tx.cnt[X], ny = ty.cnt[Y];
-    A s[3] = {A(0), A(0), A(0)};
+    TI s[3] = {TI(0), TI(0), TI(0)};
     for (int b = 0; b < ny; ++b) {
         const int64_t iy = ty.idx[Y * ty.m + b];
-        const A wy = A(ty.w[Y * ty.m + b]);
+        const TI wy = TI(ty.w[Y * ty.m + b]);
         for (int a = 0; a < nx; ++a) {
             const int64_t gi = tx.idx[X * tx.m + a] + NXi * (iy + NYi * Z);
-            const A wgt = A(tx.w[X * tx.m + a]) * wy;
-            for (int c = 0; c < ncomp; ++c) s[c] += wgt * A(in[ncomp * gi + c]);
+            const TI wgt = TI(tx.w[X * tx.m + a]) * wy;
+            for (int c = 0; c < ncomp; ++c) s[c] += wgt * in[ncomp * gi + c];
         }
     }
     for (int c = 0; c < ncomp; ++c) out[ncomp * t + c] = TO(s[c]);
