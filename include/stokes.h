@@ -370,12 +370,23 @@ int stokes_linear_solve(stokes_solver* solver, const stokes_params* params, cons
  * x, y away from a periodic seam).  Both meshes host-only (device = -1).
  * *nnz receives the prolongation's entries, *rowsum_err the largest
  * |row sum - 1|.  STOKES_E_MESH if the meshes do not match or the check
- * fails; STOKES_E_INVAL for device meshes. */
+ * fails; STOKES_E_INVAL for device meshes.
+ *
+ * stokes_debug_mg_transfer: a dense host copy of one 1-D transfer table of
+ * the velocity multigrid between a lattice of nf elements of degree k
+ * (1 <= k <= 4, nf even) and its semi-coarsening of nf / 2 elements, with
+ * NXf = k nf (+ 1 unless periodic) and NXc = k nf / 2 (+ 1 unless periodic)
+ * nodes: which = 0 the prolongation P [NXf][NXc] (degree-k interpolation of
+ * coarse nodal values at the fine nodes), 1 the restriction R = P^T
+ * [NXc][NXf], 2 the interpolation J [NXc][NXf] of fine nodal values at the
+ * coarse nodes.  out: host, rows x cols row-major.  STOKES_E_INVAL on a wrong
+ * shape or degree. */
 #define STOKES_WAIT_POLLS_DEFAULT 4194304u
 int stokes_debug_wait_limit(stokes_mesh* mesh, uint32_t polls);
 int64_t stokes_debug_fail_alloc_after(int64_t n);
 int stokes_debug_forest_prolongation(const stokes_mesh* forest, const stokes_mesh* base, int64_t* nnz,
                                      double* rowsum_err);
+int stokes_debug_mg_transfer(int nf, int k, int periodic, int which, double* out, int64_t rows, int64_t cols);
 
 /* Per-kernel timing (tracing).  Between stokes_profile_begin and
  * stokes_profile_end every operator call on this mesh, and every launch and

@@ -129,6 +129,8 @@ _SIGS = {
     "stokes_debug_fail_alloc_after": (C.c_int64, [C.c_int64]),
     "stokes_debug_forest_prolongation": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_int64),
                                                    C.POINTER(C.c_double)]),
+    "stokes_debug_mg_transfer": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_int64,
+                                           C.c_int64]),
 }
 
 _lib = None
@@ -207,6 +209,17 @@ def stokes_debug_forest_prolongation(forest, base):
     err = C.c_double(0.0)
     _check(lib().stokes_debug_forest_prolongation(forest, base, C.byref(nnz), C.byref(err)))
     return nnz.value, err.value
+
+
+def stokes_debug_mg_transfer(nf, k, periodic, which):
+    """Dense 1-D multigrid transfer table (0 = P, 1 = R, 2 = J) as a numpy array."""
+    import numpy as np
+    NXf = k * nf + (0 if periodic else 1)
+    NXc = k * (nf // 2) + (0 if periodic else 1)
+    shape = (NXf, NXc) if which == 0 else (NXc, NXf)
+    out = np.zeros(shape, dtype=np.float64)
+    _check(lib().stokes_debug_mg_transfer(nf, k, int(periodic), which, out.ctypes.data, shape[0], shape[1]))
+    return out
 
 
 def stokes_debug_wait_limit(h, polls):

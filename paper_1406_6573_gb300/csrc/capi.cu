@@ -445,6 +445,10 @@ int stokes_debug_forest_prolongation(const stokes_mesh* forest, const stokes_mes
     return STOKES_OK;
 }
 
+int stokes_debug_mg_transfer(int nf, int k, int periodic, int which, double* out, int64_t rows, int64_t cols) {
+    return stokes::mg_transfer_dense(nf, k, periodic, which, out, rows, cols);
+}
+
 int stokes_mesh_destroy(stokes_mesh* mesh) {
     if (!mesh) return STOKES_OK;
     if (mesh->on_device) {

@@ -92,7 +92,10 @@ struct HostTab1 {
     int m = 0;
 };
 
-void build_dir(int nf, int k, bool periodic, const double* gll, HostTab1& P, HostTab1& R, HostTab1& J) {
+// false if a table row would need more entries than its width (KP for P and
+// J, RM for R: 4k + 1 fine nodes per coarse node, 17 at k = 4)
+bool build_dir(int nf, int k, bool periodic, const double* gll, HostTab1& P, HostTab1& R, HostTab1& J) {
+    if (k < 1 || k + 1 > KP || 4 * k + 1 > RM || nf < 2 || nf % 2) return false;
     const int nc = nf / 2;
     const int NXf = periodic ? nf * k : nf * k + 1, NXc = periodic ? nc * k : nc * k + 1;
     auto wrapf = [&](int64_t X) { return periodic ? int32_t(X % NXf) : int32_t(X); };
@@ -121,7 +124,8 @@ void build_dir(int nf, int k, bool periodic, const double* gll, HostTab1& P, Hos
         for (int a = 0; a < P.cnt[X]; ++a) rows[P.idx[size_t(X) * KP + a]].push_back({X, P.w[size_t(X) * KP + a]});
     R.m = RM; R.idx.assign(size_t(NXc) * RM, 0); R.w.assign(size_t(NXc) * RM, 0.0); R.cnt.assign(NXc, 0);
     for (int Xc = 0; Xc < NXc; ++Xc) {
-        const int n = int(std::min<size_t>(rows[Xc].size(), RM));
+        if (rows[Xc].size() > size_t(RM)) return false;
+        const int n = int(rows[Xc].size());
         for (int a = 0; a < n; ++a) {
             R.idx[size_t(Xc) * RM + a] = rows[Xc][a].first;
             R.w[size_t(Xc) * RM + a] = rows[Xc][a].second;
@@ -146,6 +150,7 @@ void build_dir(int nf, int k, bool periodic, const double* gll, HostTab1& P, Hos
         }
         J.cnt[Xc] = n;
     }
+    return true;
 }
 
 // v_g <- P_b v_g at the basal nodes (the slip projector; zero for no-slip)
@@ -346,6 +351,25 @@ int estimate_lmax(Multigrid& mg, MgLevel& Lv, int its, double& lmax, cudaStream_
 }
 
 }  // namespace
+
+int mg_transfer_dense(int nf, int k, int periodic, int which, double* out, int64_t rows, int64_t cols) {
+    Tables1D t{};
+    if (k < 1 || k > 4) return fail(STOKES_E_INVAL, "degree outside 1..4");
+    build_tables(k, 0, t);
+    HostTab1 P, R, J;
+    if (!build_dir(nf, k, periodic != 0, t.gll, P, R, J)) return fail(STOKES_E_INVAL, "transfer tables not built");
+    const HostTab1& T = which == 0 ? P : (which == 1 ? R : J);
+    const int64_t nr = int64_t(T.cnt.size());
+    const int64_t NXf = periodic ? int64_t(nf) * k : int64_t(nf) * k + 1;
+    const int64_t NXc = periodic ? int64_t(nf / 2) * k : int64_t(nf / 2) * k + 1;
+    const int64_t nc = which == 0 ? NXc : NXf;
+    if (which < 0 || which > 2 || rows != nr || cols != nc || !out) return fail(STOKES_E_INVAL, "wrong table shape");
+    std::fill(out, out + rows * cols, 0.0);
+    for (int64_t r = 0; r < nr; ++r)
+        for (int a = 0; a < T.cnt[size_t(r)]; ++a)
+            out[r * cols + T.idx[size_t(r) * T.m + a]] += T.w[size_t(r) * T.m + a];
+    return STOKES_OK;
+}
 
 bool mg_eligible(const stokes_mesh* m) {
     if (!m || !m->on_device || m->h.k < 2 || m->h.k > 4) return false;
@@ -593,8 +617,9 @@ int mg_create(Multigrid& mg, const stokes_mesh* fine, stokes_state* st_fine, voi
         if (h.nx % 2 || h.ny % 2 || h.nx / 2 < min_cells || h.ny / 2 < min_cells) break;
         // 1-D transfer tables of this level pair (x and y)
         HostTab1 PX, RX, JX, PY, RY, JY;
-        build_dir(h.nx, h.k, h.periodic, h.tab.gll, PX, RX, JX);
-        build_dir(h.ny, h.k, h.periodic, h.tab.gll, PY, RY, JY);
+        if (!build_dir(h.nx, h.k, h.periodic, h.tab.gll, PX, RX, JX) ||
+            !build_dir(h.ny, h.k, h.periodic, h.tab.gll, PY, RY, JY))
+            return fail(STOKES_E_INVAL, "multigrid transfer tables exceed their row width");
         // coarse mesh: the fine isoparametric heights interpolated at the
         // coarse GLL points (for k = 2 the fine element vertices)
         stokes_mesh_desc d{};
@@ -648,6 +673,11 @@ int mg_create(Multigrid& mg, const stokes_mesh* fine, stokes_state* st_fine, voi
         mg_destroy(mg);
         return fail(STOKES_E_INVAL, "the mesh is too small for the velocity multigrid");
     }
+    // two levels: the coarsest level carries the whole coarse correction and
+    // is not small (a forest's base mesh, a small slab's first coarsening);
+    // with 4 sweeps (or with 1.2 / lambda_max damping) the isotropic Q4
+    // curved forest did not converge in some runs, with 12 it did
+    if (mg.L.size() == 2) mg.coarse_sweeps = std::max(mg.coarse_sweeps, 12);
     return STOKES_OK;
 }
 

@@ -17,8 +17,9 @@
 //    nodes in x and y (tensor products of 1-D tables), identity in z;
 //    restriction its transpose; the basal slip projector applied around
 //    both, so that corrections stay in the constrained space;
-//  * V(1,1) cycle; on the coarsest level (a few columns) four damped
-//    column-Jacobi sweeps, the damping capped at 1.6 / lambda_max(C^-1 A)
+//  * V(1,1) cycle; on the coarsest level four damped
+//    column-Jacobi sweeps (twelve when there are only two levels), the
+//    damping capped at 1.6 / lambda_max(C^-1 A)
 //    (power iteration per linearisation): on isotropic high-order coarse
 //    meshes the column blocks miss strong horizontal couplings and the
 //    cycle's damping alone would amplify some error components.
@@ -85,6 +86,12 @@ struct HostCsr {
 // coordinates from the base mesh's.  Host only.
 int forest_prolongation(const HostMesh& h, const std::vector<int32_t>& nodes, const std::vector<uint8_t>& refine,
                         const HostMesh& hb, HostCsr& P);
+
+// dense copy of a 1-D transfer table between a lattice of nf elements and
+// its semi-coarsening (nf / 2 elements), degree k: which 0 = P (coarse ->
+// fine, [NXf][NXc]), 1 = R = P^T ([NXc][NXf]), 2 = J (fine -> coarse
+// interpolation, [NXc][NXf]).  Host only.
+int mg_transfer_dense(int nf, int k, int periodic, int which, double* out, int64_t rows, int64_t cols);
 
 struct Multigrid {
     std::vector<MgLevel> L;

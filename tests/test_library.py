@@ -218,3 +218,53 @@ def test_forest_multigrid_prolongation(name):
     other = Mesh(dataclasses.replace(wl, refine_frac=0.0, nz=wl.nz + 1), device=-1)
     with pytest.raises(capi.StokesError):
         capi.stokes_debug_forest_prolongation(f.handle, other.handle)
+
+
+def _gll(k):
+    """GLL nodes of degree k on [-1, 1]: the end points and the roots of P_k'."""
+    from numpy.polynomial import legendre as L
+    inner = np.sort(L.legroots(L.legder([0] * k + [1]))) if k > 1 else np.array([])
+    return np.concatenate([[-1.0], inner, [1.0]])
+
+
+def _lattice_x(n_el, k, scale):
+    """Node positions of a non-periodic degree-k lattice of n_el elements of
+    length `scale` (element e, local node i at e + (g_i + 1) / 2)."""
+    g = _gll(k)
+    x = [scale * (e + 0.5 * (g[i] + 1.0)) for e in range(n_el) for i in range(k)]
+    return np.array(x + [scale * n_el])
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4])
+@pytest.mark.parametrize("nf", [4, 6])
+def test_multigrid_transfer_tables(k, nf):
+    """The velocity multigrid's 1-D transfers: P interpolates degree-k data
+    of the coarse lattice (nf / 2 elements of length 2) at the fine nodes
+    exactly, R is exactly P^T, J interpolates degree-k data of the fine
+    lattice at the coarse nodes exactly; the periodic P is the non-periodic
+    one with the end nodes identified."""
+    xf = _lattice_x(nf, k, 1.0)
+    xc = _lattice_x(nf // 2, k, 2.0)
+    P = capi.stokes_debug_mg_transfer(nf, k, False, 0)
+    R = capi.stokes_debug_mg_transfer(nf, k, False, 1)
+    J = capi.stokes_debug_mg_transfer(nf, k, False, 2)
+    assert P.shape == (len(xf), len(xc)) and R.shape == J.shape == (len(xc), len(xf))
+    for j in range(k + 1):
+        fc, ff = (xc / nf) ** j, (xf / nf) ** j
+        assert np.max(np.abs(P @ fc - ff)) < 1e-13, (k, nf, j)
+        assert np.max(np.abs(J @ ff - fc)) < 1e-13, (k, nf, j)
+    assert np.array_equal(R, P.T)
+    # a degree-(k + 1) function is not reproduced: the tables are of degree k
+    assert np.max(np.abs(P @ (xc / nf) ** (k + 1) - (xf / nf) ** (k + 1))) > 1e-6
+    Pp = capi.stokes_debug_mg_transfer(nf, k, True, 0)
+    fold = P[:-1].copy()
+    fold[:, 0] += fold[:, -1]
+    assert np.allclose(Pp, fold[:, :-1], rtol=0, atol=1e-15)
+    assert np.array_equal(capi.stokes_debug_mg_transfer(nf, k, True, 1), Pp.T)
+
+
+def test_multigrid_transfer_tables_reject_bad_shapes():
+    with pytest.raises(capi.StokesError):
+        capi.stokes_debug_mg_transfer(5, 2, False, 0)       # odd element count
+    with pytest.raises(capi.StokesError):
+        capi.stokes_debug_mg_transfer(4, 5, False, 0)       # degree above 4
