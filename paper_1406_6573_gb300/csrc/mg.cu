@@ -325,7 +325,7 @@ int vcycle(Multigrid& mg, size_t l, cudaStream_t s) {
 
 // Largest eigenvalue of C^-1 A on level Lv (C: its factored column blocks,
 // A: its velocity block with the constraint rows) by power iteration from a
-// hashed start vector; uses Lv.x and Lv.t.
+// hashed start vector; uses Lv.x, Lv.r and Lv.t (x and t cleared afterwards).
 int estimate_lmax(Multigrid& mg, MgLevel& Lv, int its, double& lmax, cudaStream_t s) {
     if (mg.prec == STOKES_F32) hash_fill_kernel<float><<<blocks_for(Lv.nu), TPB, 0, s>>>(Lv.nu, static_cast<float*>(Lv.x));
     else hash_fill_kernel<double><<<blocks_for(Lv.nu), TPB, 0, s>>>(Lv.nu, static_cast<double*>(Lv.x));

@@ -98,13 +98,12 @@ struct Multigrid {
     int prec = 1;
     bool periodic = false;
     double omega = 0.8;                   // damping of the column-Jacobi smoother
-// sweeps on the coarsest level: the Krylov counts did not change between 12
-// and 4 (128x128x8 Q2, 64x64x4 Q3 and Q4 slabs, Q3 forest), and 4 saved 8-12 %
-// of the solve time (2 sweeps: the forest needed 10 % more iterations)
-#ifndef STOKES_MG_COARSE_SWEEPS
-#define STOKES_MG_COARSE_SWEEPS 4
-#endif
-    int coarse_sweeps = STOKES_MG_COARSE_SWEEPS;
+    // sweeps on the coarsest level of hierarchies of three or more levels:
+    // the Krylov counts did not change between 12 and 4 (128x128x8 Q2,
+    // 64x64x4 Q3 and Q4 slabs, Q3 forest), and 4 saved 8-12 % of the solve
+    // time (2 sweeps: the forest needed 10 % more iterations); two-level
+    // hierarchies use 12 (mg_create)
+    int coarse_sweeps = 4;
     // a forest level (next level on sparse transfers): additive correction
     // x = C^-1 b + P V(P^T b) instead of the smoothed cycle.  The forest's
     // column blocks stand in for the hanging slots by single nodes, so they
