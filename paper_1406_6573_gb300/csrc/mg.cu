@@ -736,8 +736,12 @@ int mg_setup(Multigrid& mg, const stokes_params* p, const double* up_fine, doubl
         MG_CU(launch_col_factor(mg.prec, level_cs(C, C.scale), s), "coarse column factorisation");
         if (l + 1 == mg.L.size()) {
             // coarsest level: damping of its sweeps from the spectrum of C^-1 A
+            // the norm ratio of the power iteration approaches lambda_max from
+            // below; a two-level hierarchy's coarsest level (the base mesh of a
+            // forest, the first coarsening of a small slab) gets more
+            // iterations, since its damping decides the whole coarse correction
             double lm = 0;
-            MG_CK(estimate_lmax(mg, C, 10, lm, s));
+            MG_CK(estimate_lmax(mg, C, mg.L.size() == 2 ? 25 : 10, lm, s));
             C.lmax = lm;
             C.omega = (std::isfinite(lm) && lm > 0) ? std::min(mg.omega, 1.6 / lm) : mg.omega;
         }
