@@ -26,8 +26,7 @@ def test_reference_arm_prints_one_json_line():
     lines = [l for l in r.stdout.splitlines() if l.strip()]
     assert len(lines) == 1
     d = json.loads(lines[0])
-    base = json.load(open(os.path.join(ROOT, "BASELINE.json")))
-    assert d["impl"] == "reference" and d["metric"] == base["metric"]
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
     assert d["value"] > 0 and d["higher_is_better"] is True and d["steps"] == 1
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 1
     assert d["cpu_baseline"]["value"] == d["value"]
